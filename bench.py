@@ -1,0 +1,379 @@
+"""Benchmark: Hawkes log-likelihood + location-gradient evaluations per second.
+
+Workload: the N = 100,000, D = 2 synthetic data set shaped like the paper's
+large gunfire-style workload (50 km square, 5 years, offspring mean 0.6,
+decay 0.2/day, offspring sd 50 m, 100 m coarsening).  One step is one full
+evaluation of ell (Eq. (1)) and d ell / d X (Appendix A) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload, extrapolated to
+N = 100,000 by the N^2 pair count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "loglik+location-gradient evals/s and pairs/s at N=1e5, mixed vs FP64 GPU"
+UNIT = "evals/s"
+MAX_SM_MHZ_NOMINAL = 2070.0  # GB300 maximum SM clock
+FP32_LANES_PER_SM = 128      # FP32 FMA-pipe lanes per SM per clock
+MUFU_PER_SM = 16             # MUFU (ex2) results per SM per clock
+CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
+
+
+def pass_bound_cycles(d: int, which: str) -> float:
+    """SM cycles per unordered pair: max(FMA ops / 128, ex2 / 16) with the
+    algorithmic counts of each pass (no hi/lo overhead)."""
+    f1, f2, e1, e2 = 2 * d + 9, 4 * d + 10, 2, 2
+    if which == "pass1":
+        return max(f1 / FP32_LANES_PER_SM, e1 / MUFU_PER_SM)
+    if which == "pass2":
+        return max(f2 / FP32_LANES_PER_SM, e2 / MUFU_PER_SM)
+    return max((f1 + f2) / FP32_LANES_PER_SM, (e1 + e2) / MUFU_PER_SM)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float, device) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(n_sample: int, repeats: int = 1) -> dict:
+    """Time the FP64 oracle (all host cores) on the first n_sample events of
+    the workload: one full ell + grad per repeat."""
+    import oracle
+    import synth
+
+    w = synth.scaled_down(synth.make_c5(), n_sample)
+    cores = oracle.max_threads()
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.loglik_and_grad(w.t, w.X, w.params, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    sec = statistics.median(times)
+    pairs_per_s = float(n_sample) ** 2 / sec
+    return {"sec_per_eval": sec, "pairs_per_s": pairs_per_s, "evals_per_s_at_1e5": pairs_per_s / 1e10,
+            "cores": cores, "n_sample": n_sample}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_s = args.cpu_sample
+    for _ in range(max(0, args.warmup_ref)):
+        cpu_oracle_sample(n_s, 1)
+    t0 = time.perf_counter()
+    res = [cpu_oracle_sample(n_s, 1) for _ in range(args.steps_ref)]
+    wall = time.perf_counter() - t0
+    sec = statistics.median(r["sec_per_eval"] for r in res)
+    value = float(n_s) ** 2 / sec / 1e10
+    sample = (f"first {n_s} events (time order) of the N=1e5 D=2 workload; one full FP64 ell + grad_X per step; "
+              f"evals/s at N=1e5 = measured pairs/s / 1e10")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps_ref, "warmup": args.warmup_ref, "ms_per_step": 1e3 * sec, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c5_large_n100000_d2", "n": 100000, "d": 2, "sample_n": n_s,
+                   "precision": "fp64 (CPU oracle)"},
+        "pairs_per_s": float(n_s) ** 2 / sec,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[0]["cores"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=100_000)
+    args = ap.parse_args()
+    args.steps_ref = max(1, min(args.steps, 10))
+    args.warmup_ref = min(args.warmup, 1)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_loglik_grad_locations
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.make_c5() if args.n == 100_000 else synth.scaled_down(synth.make_c5(), args.n)
+    n, d = w.n, w.d
+    ctx = HawkesContext(device=local, max_n=n, max_d=d)
+    t = torch.tensor(w.t, device=dev)
+    X = torch.tensor(w.X, device=dev)
+    ell = torch.empty((), dtype=torch.float64, device=dev)
+    g = torch.empty((n, d), dtype=torch.float64, device=dev)
+    l2 = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        hawkes_loglik_grad_locations(ctx, t, X, w.params, precision=prec, check=False, out=(ell, g, None))
+
+    # --- device-resident timing (mixed path) ---------------------------------
+    for _ in range(args.warmup):
+        step("mixed")
+    ctx.sync_status()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    ctx.reset_stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)  # the sampler's first line lands inside the timed region
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush_l2(l2)
+        starts[k].record(stream)
+        step("mixed")
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    launches = ctx.launch_count()
+    ctx.sync_status()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_mixed = max_over_ranks(world, sum(step_ms) / len(step_ms), dev)
+    value = world * 1e3 / ms_mixed
+
+    # --- per-kernel timing (events around each pair pass, same stream) -------
+    ctx.set_option("profile", 1)
+    ctx.reset_stats()
+    prof_steps = min(20, args.steps)
+    for _ in range(prof_steps):
+        flush_l2(l2)
+        step("mixed")
+    torch.cuda.synchronize()
+    k1, k2 = ctx.kernel_stats(0), ctx.kernel_stats(1)
+    ctx.set_option("profile", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pairs = 0.5 * n * (n - 1)
+
+    def roof(stat, which):
+        achieved = stat["pairs"] / (stat["ms"] * 1e-3) / 1e9
+        peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, which) / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
+                "traffic": None, "ms_per_launch": stat["ms"] / max(1, stat["launches"]),
+                "peak_basis": f"{sms} SMs x {MAX_SM_MHZ_NOMINAL:.0f} MHz / max(FMA/128, ex2/16) cycles per pair"}
+
+    r1, r2 = roof(k1, "pass1"), roof(k2, "pass2")
+    dominant = ("pass2_gradient", r2) if k2["ms"] >= k1["ms"] else ("pass1_rates", r1)
+    eval_peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, "both") / pairs
+
+    # --- FP64 GPU path on the same inputs ------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        step("fp64")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(args.fp64_steps):
+            flush_l2(l2)
+            e0.record(stream)
+            step("fp64")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ctx.sync_status()
+        ms64 = tot / args.fp64_steps
+        fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "pairs_per_s": n * n / (ms64 * 1e-3),
+                "steps": args.fp64_steps}
+
+    # --- end to end: host buffers, H2D + evaluation + D2H inside the timing --
+    t_h = torch.tensor(w.t).pin_memory()
+    X_h = torch.tensor(w.X).pin_memory()
+    g_h = torch.empty((n, d), dtype=torch.float64).pin_memory()
+    ell_h = torch.empty((), dtype=torch.float64).pin_memory()
+    t_d = torch.empty_like(t)
+    X_d = torch.empty_like(X)
+
+    def e2e_step():
+        t_d.copy_(t_h, non_blocking=True)
+        X_d.copy_(X_h, non_blocking=True)
+        hawkes_loglik_grad_locations(ctx, t_d, X_d, w.params, precision="mixed", check=False, out=(ell, g, None))
+        g_h.copy_(g, non_blocking=True)
+        ell_h.copy_(ell, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+    for k in range(args.e2e_steps):
+        flush_l2(l2)
+        es[k].record(stream)
+        e2e_step()
+        ee[k].record(stream)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ms_e2e = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in zip(es, ee)) / args.e2e_steps, dev)
+    h2d = t_h.numel() * 8 + X_h.numel() * 8
+    d2h = g_h.numel() * 8 + 8
+
+    # --- CPU baseline: the oracle on the host cores ---------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(args.cpu_sample, 1)
+        cpu = {"value": cb["evals_per_s_at_1e5"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+               "sample": (f"first {cb['n_sample']} events (time order) of the N=1e5 D=2 workload, one full FP64 "
+                          f"ell + grad_X in {cb['sec_per_eval']:.2f} s; evals/s at N=1e5 = pairs/s / 1e10"),
+               "pairs_per_s": cb["pairs_per_s"]}
+
+    per_step_launches = launches["own"] / max(1, args.steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c5_large_n100000_d2" if n == 100_000 else f"c5_first{n}", "n": n, "d": d,
+                   "precision": "mixed: f32 pair values and squared distances, f64 reductions",
+                   "parallelism": "replicas only" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (512 MB write, untimed)"},
+        "pairs_per_s": world * n * n / (ms_mixed * 1e-3),
+        "unordered_pairs_per_s": world * pairs / (ms_mixed * 1e-3),
+        "roofline": dict(dominant[1], kernel=dominant[0]),
+        "roofline_kernels": {"pass1_rates": r1, "pass2_gradient": r2},
+        "roofline_eval": {"achieved_evals_per_s": 1e3 / ms_mixed, "peak_evals_per_s": eval_peak,
+                          "frac": (1e3 / ms_mixed) / eval_peak},
+        "fp64_gpu": fp64,
+        "e2e": {"value": world * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": ms_e2e},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": int(launches["own"]),
+        "gpu_launches_per_step": per_step_launches,
+        "library_sort_launches": int(launches["library"]),
+        "sm_count": sms,
+        "wall_s": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

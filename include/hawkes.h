@@ -1,0 +1,204 @@
+/*
+ * hawkes.h -- C ABI of libhawkes, a GB300 (sm_103a) implementation of the
+ * spatiotemporal Hawkes log-likelihood of Holbrook, Ji & Suchard ("Bayesian
+ * mitigation of spatial coarsening for a Hawkes model applied to gunfire,
+ * wildfire and viral contagion") and of its gradients, together with the
+ * HMC trajectory over event locations that calls them.
+ *
+ * Model (Section 2.1).  Events (x_n, t_n), x_n in R^D, t_n >= 0, n = 1..N.
+ *   lambda_n = sum_{n'} mu_{nn'} + xi_{nn'}                         (Eq. (1))
+ *   mu_{nn'} = mu0 / (tau_x^D tau_t) phi((x_n-x_n')/tau_x) phi((t_n-t_n')/tau_t) I[t_n != t_n']
+ *   xi_{nn'} = theta omega / h^D exp(-omega (t_n-t_n')) phi((x_n-x_n')/h) I[t_n' < t_n]
+ *   Lambda_n = mu0 [Phi((T-t_n)/tau_t) - Phi(-t_n/tau_t)] + theta [1 - exp(-omega (T-t_n))]
+ *   ell      = sum_n log lambda_n - sum_n Lambda_n,  T = max_n t_n     (Eq. (1))
+ * phi is the standard normal density (D-variate for space), Phi its CDF.
+ * The location gradient is the one of Appendix A (its sigma_x is h):
+ *   d ell/d x_n = sum_{n'} [ (mu_{nn'}/lambda_n + mu_{n'n}/lambda_n') / tau_x^2
+ *                          + (xi_{nn'}/lambda_n + xi_{n'n}/lambda_n') / h^2 ] (x_n' - x_n)
+ * The parameter gradient differentiates the same expressions with respect to
+ * Theta = (mu0, tau_x, tau_t, theta, omega, h).
+ *
+ * Conventions shared by every entry point.
+ *   - Arrays named t, X, grad, p, box_* are DEVICE pointers owned by the
+ *     caller; X is row-major N x D (event n occupies X[n*D .. n*D+D-1]).
+ *     Times need not be sorted; outputs follow the caller's event order.
+ *   - hawkes_params and host-side index arrays are HOST pointers, read
+ *     before the call returns.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) and the call returns without waiting for it.  Scalar
+ *     results are written to device memory.
+ *   - The returned status reports argument errors found on the host.
+ *     Errors found on the device (non-finite or negative inputs, a zero
+ *     rate, a timed-out device wait) are recorded in a sticky per-context
+ *     device status; hawkes_ctx_sync_status() waits for the stream and
+ *     returns it.  Outputs of a call that records a device error are NaN.
+ *   - A context is used by one host thread at a time; calls that share a
+ *     context must be issued on one stream, or ordered by the caller.
+ *   - No C++ exception crosses this interface; hawkes_last_error() returns a
+ *     message for the last failure on a context.
+ */
+#ifndef HAWKES_H
+#define HAWKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Theta of Section 2.1, in the paper's order.  All six must be finite and
+ * strictly positive (omega, h and theta are stated as strictly positive in
+ * Section 2.1; mu0 and the bandwidths carry truncated priors on (0, inf)). */
+typedef struct {
+    double mu0, tau_x, tau_t, theta, omega, h;
+} hawkes_params;
+
+typedef enum {
+    /* FP32 pairwise kernel values and squared distances, compensated FP32
+     * row sums, FP64 logs, integrated rate, reductions and HMC update. */
+    HAWKES_PREC_MIXED = 0,
+    /* Every operation in FP64. */
+    HAWKES_PREC_FP64 = 1
+} hawkes_precision;
+
+typedef enum {
+    HAWKES_OK = 0,
+    HAWKES_ERR_INVALID_ARG = 1,  /* bad size, pointer, parameter or option   */
+    HAWKES_ERR_ZERO_RATE = 2,    /* some lambda_n == 0: ell = -inf, grad NaN */
+    HAWKES_ERR_CUDA = 3,         /* a CUDA runtime call failed               */
+    HAWKES_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up       */
+    HAWKES_ERR_OOM = 5,          /* device workspace could not be allocated  */
+    HAWKES_ERR_INVALID_DATA = 6  /* non-finite X or t, or some t_n < 0       */
+} hawkes_status;
+
+typedef struct hawkes_ctx hawkes_ctx;
+typedef void *hawkes_stream; /* cudaStream_t */
+
+/* ------------------------------------------------------------ context -- */
+
+/* Create a context on CUDA device `device` whose device workspace holds
+ * problems of up to max_n events (summed over the sets of a batch) in up to
+ * max_d <= 8 dimensions.  Larger calls grow the workspace on demand, which
+ * allocates device memory at that call.  On success *ctx owns the workspace
+ * until hawkes_ctx_destroy. */
+hawkes_status hawkes_ctx_create(hawkes_ctx **ctx, int32_t device, int64_t max_n, int32_t max_d);
+
+/* Release a context and its device memory.  The caller must have finished
+ * (synchronized) all work enqueued on it.  NULL is accepted. */
+void hawkes_ctx_destroy(hawkes_ctx *ctx);
+
+/* Message for the last failure on ctx ("" if none); valid until the next
+ * call on ctx.  A NULL ctx returns the message of the last failed create. */
+const char *hawkes_last_error(const hawkes_ctx *ctx);
+
+/* Wait for `stream`, then return and clear the sticky device status of ctx
+ * (HAWKES_OK if no device-side error was recorded since the last check). */
+hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
+
+/* Tuning and profiling options (hawkes_ctx_set_option):
+ *   HAWKES_OPT_BLOCK_WARPS   warps per CTA of the pair kernels (0 = tuned)
+ *   HAWKES_OPT_CTAS_PER_SM   persistent CTAs per SM (0 = occupancy limit)
+ *   HAWKES_OPT_PROFILE       1: time every pair-kernel launch with events
+ *   HAWKES_OPT_TIMES_SORTED  1: the caller promises t is non-decreasing and
+ *                            the time sort is skipped (checked on device)
+ *   HAWKES_OPT_MIXED_FIXUP_EXP  log2 of the rate threshold below which a
+ *                            row of the mixed path is recomputed in FP64
+ *                            (default -76, range [-120, 0])                  */
+enum {
+    HAWKES_OPT_BLOCK_WARPS = 1,
+    HAWKES_OPT_CTAS_PER_SM = 2,
+    HAWKES_OPT_PROFILE = 3,
+    HAWKES_OPT_TIMES_SORTED = 4,
+    HAWKES_OPT_MIXED_FIXUP_EXP = 5
+};
+hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
+
+/* Kernel timing collected while HAWKES_OPT_PROFILE is on (waits for the
+ * recorded events).  kernel: 0 = rate pass (lambda row sums), 1 = gradient
+ * pass.  Returns the summed device time in ms, the number of launches and
+ * the number of unordered event pairs those launches processed. */
+hawkes_status hawkes_ctx_kernel_stats(hawkes_ctx *ctx, int32_t kernel, double *total_ms,
+                                      int64_t *launches, double *pairs);
+hawkes_status hawkes_ctx_reset_stats(hawkes_ctx *ctx);
+
+/* Number of kernel launches this context has enqueued since creation (or
+ * the last reset_stats): `own` counts the library's hand-written kernels,
+ * `library` the launches of the CUB radix sort used for the time order
+ * (counted as one per sort call). */
+hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64_t *library);
+
+/* ------------------------------------------------------- log-likelihood -- */
+
+/* ell(X, t | Theta) of Eq. (1).
+ *   t: device [n] event times (>= 0, finite), any order.
+ *   X: device [n*d] locations, row-major.
+ *   n >= 1, 1 <= d <= 8.
+ *   out_loglik: device [1].  A zero rate (e.g. n = 1, or an event tied in
+ *   time with every other) gives -inf and status OK. */
+hawkes_status hawkes_loglik(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                            const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                            double *out_loglik);
+
+/* ell of Eq. (1) and its gradient with respect to every location
+ * (Appendix A), optionally with respect to Theta.
+ *   out_grad_X: device [n*d], row-major, in the caller's event order.
+ *   out_grad_params: device [6] in Theta order, or NULL to skip.
+ * A zero rate records HAWKES_ERR_ZERO_RATE in the device status, writes
+ * ell = -inf and fills the gradients with NaN. */
+hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, const double *X, int64_t n,
+                                           int32_t d, const hawkes_params *params, hawkes_precision prec,
+                                           hawkes_stream stream, double *out_loglik, double *out_grad_X,
+                                           double *out_grad_params);
+
+/* ------------------------------------------------------------------ HMC -- */
+
+/* One Hamiltonian Monte Carlo proposal over all locations (Section 3: HMC
+ * over X, after Neal 2011) with potential U = -ell, identity mass matrix,
+ * and n_steps leapfrog steps of size eps:
+ *   p += eps/2 grad ell(X);  X += eps p;  reflect at box walls;  p += eps/2 grad ell(X)
+ * (the gradient at the end of one step is reused at the start of the next).
+ * Reflection mirrors a coordinate that left [lo, hi] back across the wall it
+ * crossed and flips its momentum, repeatedly (at most 1000 times, else the
+ * proposal is rejected).  Box walls carry the uniform location priors of
+ * Eq. (2); pass box_lo = box_hi = NULL for unconstrained locations.
+ *   X_inout: device [n*d]; replaced by the proposal when accepted.
+ *   p0:      device [n*d] initial momenta (drawn by the caller).
+ *   log_u:   device [1] log of the caller's uniform draw; the proposal is
+ *            accepted iff log_u < H0 - H1 with H = -ell + |p|^2/2 (FP64) and
+ *            H1 finite.
+ *   out_H0, out_H1: device [1];  out_accepted: device int32 [1].
+ * The L-step trajectory runs as one CUDA graph cached in the context (keyed
+ * by n, d, n_steps, precision and the presence of boxes); the first call
+ * with a new key captures it. */
+hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
+                                      const double *box_lo, const double *box_hi, int64_t n, int32_t d,
+                                      const hawkes_params *params, double eps, int32_t n_steps,
+                                      const double *log_u, hawkes_precision prec, hawkes_stream stream,
+                                      double *out_H0, double *out_H1, int32_t *out_accepted);
+
+/* ------------------------------------------------------------- batched -- */
+
+/* Log-likelihoods and location gradients of n_sets independent data sets
+ * in one pass: set b has n_b = offsets[b+1]-offsets[b] events of dimension
+ * dims[b] and parameters params[b].  offsets (n_sets+1 entries, offsets[0]
+ * = 0), dims and params are HOST arrays.
+ *   t: device, the sets' times back to back (offsets index it).
+ *   X: device, the sets' locations back to back, each set row-major with its
+ *      own width: set b starts at element sum_{b'<b} n_b' * dims[b'].
+ *   out_loglik: device [n_sets];  out_grad_X: device, laid out like X.
+ * Every set's rows are pair-evaluated by one persistent launch per distinct
+ * dimension, with work items from all sets of that dimension balanced over
+ * the SMs. */
+hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets,
+                                       const int32_t *dims, const double *t, const double *X,
+                                       const hawkes_params *params, hawkes_precision prec,
+                                       hawkes_stream stream, double *out_loglik, double *out_grad_X);
+
+/* Library version, e.g. "hawkes 0.1.0 sm_103a". */
+const char *hawkes_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAWKES_H */

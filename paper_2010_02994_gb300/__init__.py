@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) implementation of the spatiotemporal Hawkes log-likelihood,
+its location and parameter gradients, and HMC over event locations
+(Holbrook, Ji & Suchard, arXiv 2010.02994).
+
+The computation lives in libhawkes.so (C ABI: include/hawkes.h); this package
+only marshals torch tensors into it.
+"""
+from .api import (HawkesContext, HawkesError, hawkes_batch_loglik_grad, hawkes_loglik,  # noqa: F401
+                  hawkes_loglik_grad_locations, hmc_leapfrog_trajectory, params_struct, version)

@@ -1,0 +1,98 @@
+"""ctypes declarations of the libhawkes C ABI (include/hawkes.h).
+
+Loading fails loudly when the in-tree library is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhawkes.so")
+
+HAWKES_OK = 0
+STATUS_NAMES = {
+    0: "HAWKES_OK",
+    1: "HAWKES_ERR_INVALID_ARG",
+    2: "HAWKES_ERR_ZERO_RATE",
+    3: "HAWKES_ERR_CUDA",
+    4: "HAWKES_ERR_TIMEOUT",
+    5: "HAWKES_ERR_OOM",
+    6: "HAWKES_ERR_INVALID_DATA",
+}
+PREC = {"mixed": 0, "fp64": 1}
+OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5}
+
+# every function declared in include/hawkes.h
+EXPORTED = (
+    "hawkes_ctx_create", "hawkes_ctx_destroy", "hawkes_last_error", "hawkes_ctx_sync_status",
+    "hawkes_ctx_set_option", "hawkes_ctx_kernel_stats", "hawkes_ctx_reset_stats", "hawkes_loglik",
+    "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
+    "hawkes_ctx_launch_count",
+)
+
+
+class HawkesParams(ctypes.Structure):
+    """Theta = (mu0, tau_x, tau_t, theta, omega, h) in the paper's order."""
+
+    _fields_ = [(n, ctypes.c_double) for n in ("mu0", "tau_x", "tau_t", "theta", "omega", "h")]
+
+
+class HawkesError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    pp = ctypes.POINTER(HawkesParams)
+    st = ctypes.c_int
+    lib.hawkes_ctx_create.argtypes = [ctypes.POINTER(vp), i32, i64, i32]
+    lib.hawkes_ctx_create.restype = st
+    lib.hawkes_ctx_destroy.argtypes = [vp]
+    lib.hawkes_ctx_destroy.restype = None
+    lib.hawkes_last_error.argtypes = [vp]
+    lib.hawkes_last_error.restype = ctypes.c_char_p
+    lib.hawkes_ctx_sync_status.argtypes = [vp, vp]
+    lib.hawkes_ctx_sync_status.restype = st
+    lib.hawkes_ctx_set_option.argtypes = [vp, i32, i64]
+    lib.hawkes_ctx_set_option.restype = st
+    lib.hawkes_ctx_kernel_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                            ctypes.POINTER(ctypes.c_double)]
+    lib.hawkes_ctx_kernel_stats.restype = st
+    lib.hawkes_ctx_launch_count.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.hawkes_ctx_launch_count.restype = st
+    lib.hawkes_ctx_reset_stats.argtypes = [vp]
+    lib.hawkes_ctx_reset_stats.restype = st
+    lib.hawkes_loglik.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
+    lib.hawkes_loglik.restype = st
+    lib.hawkes_loglik_grad_locations.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp, dp, dp]
+    lib.hawkes_loglik_grad_locations.restype = st
+    lib.hmc_leapfrog_trajectory.argtypes = [vp, dp, dp, dp, dp, dp, i64, i32, pp, ctypes.c_double, i32, dp, i32,
+                                            vp, dp, dp, dp]
+    lib.hmc_leapfrog_trajectory.restype = st
+    lib.hawkes_batch_loglik_grad.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, pp, i32,
+                                             vp, dp, dp]
+    lib.hawkes_batch_loglik_grad.restype = st
+    lib.hawkes_version.argtypes = []
+    lib.hawkes_version.restype = ctypes.c_char_p
+    return lib
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libhawkes.so (built by ``build.py``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libhawkes.so not found at {p}; build it with paper_2010_02994_gb300/build.py")
+            _lib = _declare(ctypes.CDLL(p))
+        return _lib

@@ -1,0 +1,204 @@
+"""Python binding of libhawkes: argument marshalling only.
+
+Functions named after the C entry points take torch CUDA tensors (float64,
+contiguous) and enqueue the work on the current torch stream of the tensors'
+device.  Every step of the computation runs in the library's CUDA kernels.
+
+    ctx = HawkesContext(device=0, max_n=100_000, max_d=2)
+    ell, grad = hawkes_loglik_grad_locations(ctx, t, X, params)   # device tensors
+    ctx.sync_status()                                             # raises on a device-side error
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import HawkesError, HawkesParams
+
+PARAM_NAMES = ("mu0", "tau_x", "tau_t", "theta", "omega", "h")
+
+
+def params_struct(params) -> HawkesParams:
+    """A mapping with the six names, a sequence in Theta order, or HawkesParams."""
+    if isinstance(params, HawkesParams):
+        return params
+    if isinstance(params, dict):
+        return HawkesParams(*(float(params[k]) for k in PARAM_NAMES))
+    if isinstance(params, torch.Tensor):
+        params = params.detach().cpu().tolist()
+    vals = [float(v) for v in params]
+    if len(vals) != 6:
+        raise ValueError("Theta has six components")
+    return HawkesParams(*vals)
+
+
+def _ptr(x: torch.Tensor | None) -> int | None:
+    return None if x is None else x.data_ptr()
+
+
+def _dev_f64(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    return x.contiguous()
+
+
+def _precision(p) -> int:
+    if isinstance(p, int):
+        return p
+    return _lib.PREC[p]
+
+
+class HawkesContext:
+    """Owns a libhawkes context (device workspace, cached HMC graphs)."""
+
+    def __init__(self, device: int = 0, max_n: int = 1024, max_d: int = 8):
+        self.lib = _lib.load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = self.lib.hawkes_ctx_create(ctypes.byref(h), self.device, int(max_n), int(max_d))
+        if st != _lib.HAWKES_OK:
+            raise HawkesError(st, self.lib.hawkes_last_error(None).decode())
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hawkes_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status: int):
+        if status != _lib.HAWKES_OK:
+            raise HawkesError(status, self.lib.hawkes_last_error(self.handle).decode())
+
+    def stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def sync_status(self):
+        """Wait for the current stream and raise if a device-side error was recorded."""
+        self.check(self.lib.hawkes_ctx_sync_status(self.handle, self.stream()))
+
+    def set_option(self, name: str, value: int):
+        self.check(self.lib.hawkes_ctx_set_option(self.handle, _lib.OPTIONS[name], int(value)))
+
+    def kernel_stats(self, kernel: int):
+        ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        self.check(self.lib.hawkes_ctx_kernel_stats(self.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n),
+                                                    ctypes.byref(pairs)))
+        return {"ms": ms.value, "launches": n.value, "pairs": pairs.value}
+
+    def launch_count(self):
+        own, lib = ctypes.c_int64(), ctypes.c_int64()
+        self.check(self.lib.hawkes_ctx_launch_count(self.handle, ctypes.byref(own), ctypes.byref(lib)))
+        return {"own": own.value, "library": lib.value}
+
+    def reset_stats(self):
+        self.check(self.lib.hawkes_ctx_reset_stats(self.handle))
+
+
+def _shape(t: torch.Tensor, X: torch.Tensor):
+    n = t.numel()
+    if X.dim() == 1:
+        X = X.reshape(n, 1)
+    if X.dim() != 2 or X.shape[0] != n:
+        raise ValueError("X must be (N, D) with N = len(t)")
+    return n, X.shape[1], X
+
+
+def hawkes_loglik(ctx: HawkesContext, t, X, params, precision="mixed", check: bool = True) -> torch.Tensor:
+    """ell of Eq. (1) as a 0-d float64 tensor on the device."""
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X")
+    n, d, X = _shape(t, X)
+    out = torch.empty((), dtype=torch.float64, device=t.device)
+    p = params_struct(params)
+    ctx.check(ctx.lib.hawkes_loglik(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p), _precision(precision),
+                                    ctx.stream(), _ptr(out)))
+    if check:
+        ctx.sync_status()
+    return out
+
+
+def hawkes_loglik_grad_locations(ctx: HawkesContext, t, X, params, precision="mixed", grad_params: bool = False,
+                                 check: bool = True, out=None):
+    """(ell, d ell/d X) -- and d ell/d Theta when grad_params -- as device tensors."""
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X")
+    n, d, X = _shape(t, X)
+    if out is None:
+        ell = torch.empty((), dtype=torch.float64, device=t.device)
+        g = torch.empty((n, d), dtype=torch.float64, device=t.device)
+        gp = torch.empty(6, dtype=torch.float64, device=t.device) if grad_params else None
+    else:
+        ell, g, gp = out
+    p = params_struct(params)
+    ctx.check(ctx.lib.hawkes_loglik_grad_locations(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p),
+                                                   _precision(precision), ctx.stream(), _ptr(ell), _ptr(g),
+                                                   _ptr(gp)))
+    if check:
+        ctx.sync_status()
+    return (ell, g, gp) if grad_params else (ell, g)
+
+
+def hmc_leapfrog_trajectory(ctx: HawkesContext, t, X, p0, params, eps: float, n_steps: int, log_u,
+                            box_lo=None, box_hi=None, precision="mixed", check: bool = True):
+    """One HMC proposal (Section 3).  X is updated in place when accepted.
+    Returns (H0, H1, accepted) as device tensors."""
+    t = _dev_f64(t, "t")
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (it is updated in place)")
+    n, d, _ = _shape(t, X)
+    p0 = _dev_f64(p0, "p0")
+    lo = None if box_lo is None else _dev_f64(box_lo, "box_lo")
+    hi = None if box_hi is None else _dev_f64(box_hi, "box_hi")
+    if not isinstance(log_u, torch.Tensor):
+        log_u = torch.tensor(float(log_u), dtype=torch.float64, device=t.device)
+    log_u = _dev_f64(log_u, "log_u")
+    H0 = torch.empty((), dtype=torch.float64, device=t.device)
+    H1 = torch.empty((), dtype=torch.float64, device=t.device)
+    acc = torch.empty((), dtype=torch.int32, device=t.device)
+    p = params_struct(params)
+    ctx.check(ctx.lib.hmc_leapfrog_trajectory(ctx.handle, _ptr(t), _ptr(X), _ptr(p0), _ptr(lo), _ptr(hi), n, d,
+                                              ctypes.byref(p), float(eps), int(n_steps), _ptr(log_u),
+                                              _precision(precision), ctx.stream(), _ptr(H0), _ptr(H1), _ptr(acc)))
+    if check:
+        ctx.sync_status()
+    return H0, H1, acc
+
+
+def hawkes_batch_loglik_grad(ctx: HawkesContext, sizes, dims, t, X, params_list, precision="mixed",
+                             check: bool = True):
+    """Log-likelihoods (n_sets,) and the packed location gradient of a batch
+    of independent sets.  sizes/dims: per-set event counts and dimensions;
+    t: all times back to back; X: all locations back to back, each set
+    row-major with its own width."""
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X").reshape(-1)
+    ns = len(sizes)
+    offs = (ctypes.c_int64 * (ns + 1))()
+    acc = 0
+    for i, s in enumerate(sizes):
+        offs[i] = acc
+        acc += int(s)
+    offs[ns] = acc
+    dims_c = (ctypes.c_int32 * ns)(*[int(v) for v in dims])
+    ps = (HawkesParams * ns)(*[params_struct(p) for p in params_list])
+    ell = torch.empty(ns, dtype=torch.float64, device=t.device)
+    g = torch.empty_like(X)
+    ctx.check(ctx.lib.hawkes_batch_loglik_grad(ctx.handle, ns, offs, dims_c, _ptr(t), _ptr(X), ps,
+                                               _precision(precision), ctx.stream(), _ptr(ell), _ptr(g)))
+    if check:
+        ctx.sync_status()
+    return ell, g
+
+
+def version() -> str:
+    return _lib.load().hawkes_version().decode()

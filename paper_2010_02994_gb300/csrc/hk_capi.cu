@@ -1,0 +1,996 @@
+// C ABI of libhawkes: context, workspace, validation and the launch
+// sequences of the log-likelihood, gradient, HMC and batched entry points.
+//
+// Every compute entry point builds a list of data sets (one for the single
+// calls), lays the sets out in the context's device workspace, and enqueues
+//   validate + time sort + pack   (hk_prep.cu)
+//   pass 1: rate row sums         (pair kernels)
+//   finalize rows, FP64 fixups, ell per set          (hk_finalize.cu)
+//   pass 2: gradient row sums     (pair kernels, when a gradient is wanted)
+//   finalize gradient, FP64 fixups                   (hk_finalize.cu)
+// on the caller's stream without waiting for it.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hk_internal.cuh"
+
+using namespace hk;
+
+namespace {
+
+std::mutex g_create_err_mu;
+std::string g_create_err;
+
+constexpr double kLog2e = 1.4426950408889634073599246810019;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// control block (int32 words): [0] status, [4..7] kernel counters, [16..) set flags
+constexpr int kCtlStatus = 0;
+constexpr int kCtlCounters = 4;
+constexpr int kCtlSetFlags = 16;
+
+struct DeviceBuffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct ProfEvent {
+    cudaEvent_t a, b;
+    int kernel;
+    double pairs;
+};
+
+// Host description of one call (a list of sets).
+struct Plan {
+    std::vector<SetDesc> sets;
+    std::vector<WorkItem> items;         // grouped by dimension
+    std::vector<int64_t> set_ev0;        // nsets+1
+    std::vector<int64_t> set_row0;       // nsets+1
+    std::vector<std::pair<int, int>> item_range_by_d;  // [d] -> (first, count)
+    std::vector<int> warps_by_d;
+    int64_t n_total = 0, x_total = 0, total_rows = 0, total_rec4 = 0, total_P1 = 0, total_P2 = 0;
+    int64_t total_F1 = 0, total_F2 = 0;
+    int32_t total_segs = 0, max_fsplit = 1;
+    int64_t max_ftiles = 1;
+    double pairs = 0.0;  // unordered pairs over all sets
+};
+
+struct HmcGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::tuple<int64_t, int32_t, int32_t, int32_t, bool, size_t> key;
+};
+
+}  // namespace
+
+struct hawkes_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    int32_t *ctl = nullptr;
+    int32_t ctl_sets = 0;
+    DeviceBuffer ws;
+    size_t ws_generation = 0;
+    // options
+    int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76;
+    std::vector<ProfEvent> prof_pending;
+    double prof_ms[2] = {0, 0};
+    int64_t prof_launches[2] = {0, 0};
+    double prof_pairs[2] = {0, 0};
+    int64_t launches_own = 0, launches_lib = 0;
+    HmcGraph hmc;
+    int occ[kMaxD + 1][3][9] = {};  // CTAs per SM of the pair kernels: [d][pass][warps]
+    std::vector<char> uploaded;     // bytes of the plan last copied to the device
+    // workspace views of the current plan
+    Work w{};
+    SetDesc *d_sets = nullptr;
+    WorkItem *d_items = nullptr;
+    int64_t *d_set_ev0 = nullptr, *d_set_row0 = nullptr;
+    double *keys_a = nullptr, *keys_b = nullptr;
+    int32_t *vals_a = nullptr, *vals_b = nullptr;
+    void *sort_temp = nullptr;
+    size_t sort_bytes = 0;
+    // HMC state (sorted rows, stride kMaxD)
+    double *hp = nullptr, *hg = nullptr, *hlo = nullptr, *hhi = nullptr;
+    double *hscal = nullptr;  // [0] eps, [1] log_u, [2] H0, [3] H1
+    int32_t *hint = nullptr;  // [0] accepted, [1] reflection failure
+};
+
+namespace {
+
+hawkes_status fail(hawkes_ctx *c, hawkes_status st, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    return st;
+}
+
+hawkes_status cuda_fail(hawkes_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, HAWKES_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HK_TRY(expr, where)                      \
+    do {                                         \
+        cudaError_t e_ = (expr);                 \
+        if (e_ != cudaSuccess)                   \
+            return cuda_fail(ctx, e_, where);    \
+    } while (0)
+
+bool params_ok(const hawkes_params *p)
+{
+    const double v[6] = {p->mu0, p->tau_x, p->tau_t, p->theta, p->omega, p->h};
+    for (double x : v)
+        if (!(x > 0.0) || !std::isfinite(x))
+            return false;
+    return true;
+}
+
+// Warps per CTA of the pair kernels for a set of n events in d dimensions:
+// the largest count that still gives every SM slot several pair blocks.
+int choose_warps(const hawkes_ctx *ctx, int64_t n, int d)
+{
+    if (ctx->opt_warps > 0)
+        return ctx->opt_warps;
+    const int R = rows_per_lane(d);
+    const int candidates[4] = {8, 4, 2, 1};
+    for (int wv : candidates) {
+        // shared memory per CTA must leave room for two CTAs per SM
+        if (pass_smem_bytes(d, 2, wv) > 110 * 1024)
+            continue;
+        const int64_t B = 32LL * R * wv;
+        const int64_t T = (n + B - 1) / B;
+        const int64_t items = T * (T + 1) / 2;
+        if (items >= 6LL * ctx->sm_count)
+            return wv;
+    }
+    return 1;
+}
+
+// Fill the derived fields of one set.
+void describe_set(SetDesc &S, int64_t n, int d, const hawkes_params &p, double fixup_exp)
+{
+    S.n = (int32_t)n;
+    S.d = d;
+    S.mu0 = p.mu0;
+    S.tau_x = p.tau_x;
+    S.tau_t = p.tau_t;
+    S.theta = p.theta;
+    S.omega = p.omega;
+    S.h = p.h;
+    const double k0 = std::sqrt(kLog2e / 2.0);
+    S.kx = k0 / p.tau_x;
+    S.kt = k0 / p.tau_t;
+    S.Pmu = p.mu0 / (std::pow(p.tau_x, d) * p.tau_t * std::pow(kTwoPi, 0.5 * (d + 1)));
+    S.Cg = 1.0 / (p.tau_x * p.tau_x * S.kx);
+    const double rho = (p.tau_x * p.tau_x) / (p.h * p.h);
+    const double cxi1 = std::log2(p.theta * p.omega * std::pow(p.tau_x, d) * p.tau_t * std::sqrt(kTwoPi) /
+                                  (p.mu0 * std::pow(p.h, d)));
+    S.rho = (float)rho;
+    S.kappa = (float)(p.omega * kLog2e / S.kt);
+    S.cxi1 = (float)cxi1;
+    S.cxi2 = (float)(cxi1 + std::log2(rho));
+    S.s_min = std::ldexp(1.0, (int)fixup_exp);
+}
+
+bool mixed_range_ok(const SetDesc &S)
+{
+    return std::isfinite(S.cxi1) && std::isfinite(S.cxi2) && std::fabs(S.cxi1) < 64.0f &&
+           std::fabs(S.cxi2) < 64.0f && S.rho < 1e30f && S.rho > 1e-30f && S.kappa < 1e30f;
+}
+
+// Lay out the sets of one call and build the work list.
+hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t *ev_counts, const int32_t *dims,
+                         const hawkes_params *params, bool fp64)
+{
+    pl = Plan();
+    pl.sets.resize(nsets);
+    pl.set_ev0.resize(nsets + 1);
+    pl.set_row0.resize(nsets + 1);
+    pl.item_range_by_d.assign(kMaxD + 1, {0, 0});
+    pl.warps_by_d.assign(kMaxD + 1, 0);
+    // the block size is chosen per dimension from the largest set of that dimension
+    std::vector<int64_t> nmax_by_d(kMaxD + 1, 0);
+    for (int s = 0; s < nsets; ++s)
+        nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
+    for (int d = 1; d <= kMaxD; ++d)
+        if (nmax_by_d[d] > 0)
+            pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d);
+    int64_t ev = 0, x = 0, row = 0, rec4 = 0, p1 = 0, p2 = 0, f1 = 0, f2 = 0;
+    int32_t seg = 0;
+    for (int s = 0; s < nsets; ++s) {
+        SetDesc &S = pl.sets[s];
+        std::memset(&S, 0, sizeof(S));
+        const int d = dims[s];
+        const int64_t n = ev_counts[s];
+        describe_set(S, n, d, params[s], ctx->opt_fixup_exp);
+        if (!fp64 && !mixed_range_ok(S))
+            return fail(ctx, HAWKES_ERR_INVALID_ARG,
+                        "parameters outside the range of the mixed-precision path; use HAWKES_PREC_FP64");
+        const int B = fp64 ? kFp64Rows : 32 * rows_per_lane(d) * pl.warps_by_d[d];
+        S.B = B;
+        S.nblk = (int32_t)((n + B - 1) / B);
+        S.npad = S.nblk * B;
+        S.ev0 = ev;
+        S.x0 = x;
+        S.row0 = row;
+        S.rec0 = rec4;
+        S.part0 = p1;
+        S.part2_0 = p2;
+        S.fpart0 = f1;
+        S.fpart2_0 = f2;
+        S.vpc = 1;
+        S.seg0 = seg;
+        S.nseg = (int32_t)((n + kFinalizeThreads - 1) / kFinalizeThreads);
+        // FP64 kernels: enough column splits for about 8 CTAs per SM in total
+        const int64_t ftiles = (n + kFp64Rows - 1) / kFp64Rows;
+        int64_t fs = std::max<int64_t>(1, (8LL * ctx->sm_count) / std::max<int64_t>(1, ftiles * nsets));
+        fs = std::min<int64_t>(fs, ftiles);
+        S.fsplit = (int32_t)std::max<int64_t>(1, fs);
+        pl.max_fsplit = std::max(pl.max_fsplit, S.fsplit);
+        pl.max_ftiles = std::max(pl.max_ftiles, ftiles);
+        ev += n;
+        x += n * d;
+        row += S.npad;
+        rec4 += (int64_t)nrec(d) * S.npad;
+        p1 += (int64_t)S.nblk * S.npad * kPass1Vals;
+        p2 += (int64_t)S.nblk * S.npad * d;
+        f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
+        f2 += (int64_t)S.fsplit * S.npad * d;
+        seg += S.nseg;
+        pl.pairs += 0.5 * (double)n * (double)(n - 1);
+    }
+    pl.n_total = ev;
+    pl.x_total = x;
+    pl.total_rows = row;
+    pl.total_rec4 = rec4;
+    pl.total_P1 = p1;
+    pl.total_P2 = p2;
+    pl.total_F1 = f1;
+    pl.total_F2 = f2;
+    pl.total_segs = seg;
+    for (int s = 0; s <= nsets; ++s) {
+        pl.set_ev0[s] = s < nsets ? pl.sets[s].ev0 : ev;
+        pl.set_row0[s] = s < nsets ? pl.sets[s].row0 : row;
+    }
+    if (!fp64) {
+        // work items grouped by dimension; diagonal blocks (half the work) last
+        for (int d = 1; d <= kMaxD; ++d) {
+            const int first = (int)pl.items.size();
+            for (int s = 0; s < nsets; ++s) {
+                const SetDesc &S = pl.sets[s];
+                if (S.d != d)
+                    continue;
+                for (int I = 0; I < S.nblk; ++I)
+                    for (int J = I + 1; J < S.nblk; ++J)
+                        pl.items.push_back({s, I, J, 0});
+            }
+            for (int s = 0; s < nsets; ++s) {
+                const SetDesc &S = pl.sets[s];
+                if (S.d != d)
+                    continue;
+                for (int I = 0; I < S.nblk; ++I)
+                    pl.items.push_back({s, I, I, 1});
+            }
+            pl.item_range_by_d[d] = {first, (int)pl.items.size() - first};
+        }
+    }
+    return HAWKES_OK;
+}
+
+size_t plan_bytes(const Plan &pl, size_t sort_bytes)
+{
+    Carve c{nullptr};
+    const size_t ns = pl.sets.size();
+    c.take<SetDesc>(ns);
+    c.take<WorkItem>(std::max<size_t>(1, pl.items.size()));
+    c.take<int64_t>(ns + 1);
+    c.take<int64_t>(ns + 1);
+    c.take<float4>(pl.total_rec4);
+    c.take<float>(pl.total_rows);
+    c.take<int32_t>(pl.total_rows);
+    c.take<int32_t>(pl.total_rows);
+    for (int k = 0; k < 5; ++k)
+        c.take<double>(pl.total_rows);
+    c.take<double>(pl.total_rows * kMaxD);
+    c.take<double>(pl.total_rows * kPass1ThetaVals);
+    c.take<float>(pl.total_P1);
+    c.take<float>(pl.total_P2);
+    c.take<double>(pl.total_F1);
+    c.take<double>(pl.total_F2);
+    c.take<int32_t>(pl.total_segs);
+    c.take<int32_t>((size_t)pl.total_segs * kFinalizeThreads);
+    c.take<double>(pl.total_segs);
+    c.take<double>(ns);
+    c.take<double>(pl.n_total);
+    c.take<double>(pl.n_total);
+    c.take<int32_t>(pl.n_total);
+    c.take<int32_t>(pl.n_total);
+    c.take<char>(sort_bytes);
+    for (int k = 0; k < 4; ++k)
+        c.take<double>(pl.total_rows * kMaxD);
+    c.take<double>(8);
+    c.take<int32_t>(8);
+    return c.off + 256;
+}
+
+// Make the workspace large enough for the plan and point the views at it.
+hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
+{
+    const size_t ns = pl.sets.size();
+    const size_t sort_bytes = std::max<size_t>(256, sort_temp_bytes(pl.n_total, (int32_t)ns));
+    const size_t need = plan_bytes(pl, sort_bytes);
+    if (need > ctx->ws.bytes) {
+        HK_TRY(cudaDeviceSynchronize(), "synchronize before growing the workspace");
+        if (ctx->ws.ptr)
+            cudaFree(ctx->ws.ptr);
+        ctx->ws.ptr = nullptr;
+        ctx->ws.bytes = 0;
+        const size_t bytes = need + need / 4;
+        if (cudaMalloc(&ctx->ws.ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HAWKES_ERR_OOM, "device workspace of " + std::to_string(bytes) + " bytes");
+        }
+        ctx->ws.bytes = bytes;
+        ++ctx->ws_generation;
+    }
+    if ((int32_t)ns > ctx->ctl_sets) {
+        HK_TRY(cudaDeviceSynchronize(), "synchronize before growing the control block");
+        int32_t *ctl = nullptr;
+        const int32_t cap = (int32_t)std::max<size_t>(ns, 64);
+        HK_TRY(cudaMalloc(&ctl, sizeof(int32_t) * (kCtlSetFlags + cap)), "control block");
+        HK_TRY(cudaMemset(ctl, 0, sizeof(int32_t) * (kCtlSetFlags + cap)), "control block");
+        if (ctx->ctl) {
+            HK_TRY(cudaMemcpy(ctl, ctx->ctl, sizeof(int32_t) * kCtlSetFlags, cudaMemcpyDeviceToDevice), "control");
+            cudaFree(ctx->ctl);
+        }
+        ctx->ctl = ctl;
+        ctx->ctl_sets = cap;
+        ++ctx->ws_generation;
+    }
+    Carve c{reinterpret_cast<char *>(ctx->ws.ptr)};
+    Work &w = ctx->w;
+    ctx->d_sets = c.take<SetDesc>(ns);
+    ctx->d_items = c.take<WorkItem>(std::max<size_t>(1, pl.items.size()));
+    ctx->d_set_ev0 = c.take<int64_t>(ns + 1);
+    ctx->d_set_row0 = c.take<int64_t>(ns + 1);
+    w.sets = ctx->d_sets;
+    w.nsets = (int32_t)ns;
+    w.rec = c.take<float4>(pl.total_rec4);
+    w.w32 = c.take<float>(pl.total_rows);
+    w.tie_end = c.take<int32_t>(pl.total_rows);
+    w.perm = c.take<int32_t>(pl.total_rows);
+    w.t64 = c.take<double>(pl.total_rows);
+    w.lam64 = c.take<double>(pl.total_rows);
+    w.w64 = c.take<double>(pl.total_rows);
+    w.Lam64 = c.take<double>(pl.total_rows);
+    w.lnl = c.take<double>(pl.total_rows);
+    w.x64 = c.take<double>(pl.total_rows * kMaxD);
+    w.theta_rows = c.take<double>(pl.total_rows * kPass1ThetaVals);
+    w.P1 = c.take<float>(pl.total_P1);
+    w.P2 = c.take<float>(pl.total_P2);
+    w.F1 = c.take<double>(pl.total_F1);
+    w.F2 = c.take<double>(pl.total_F2);
+    w.seg_count = c.take<int32_t>(pl.total_segs);
+    w.seg_rows = c.take<int32_t>((size_t)pl.total_segs * kFinalizeThreads);
+    w.seg_sum = c.take<double>(pl.total_segs);
+    w.set_loglik = c.take<double>(ns);
+    ctx->keys_a = c.take<double>(pl.n_total);
+    ctx->keys_b = c.take<double>(pl.n_total);
+    ctx->vals_a = c.take<int32_t>(pl.n_total);
+    ctx->vals_b = c.take<int32_t>(pl.n_total);
+    ctx->sort_temp = c.take<char>(sort_bytes);
+    ctx->sort_bytes = sort_bytes;
+    ctx->hp = c.take<double>(pl.total_rows * kMaxD);
+    ctx->hg = c.take<double>(pl.total_rows * kMaxD);
+    ctx->hlo = c.take<double>(pl.total_rows * kMaxD);
+    ctx->hhi = c.take<double>(pl.total_rows * kMaxD);
+    ctx->hscal = c.take<double>(8);
+    ctx->hint = c.take<int32_t>(8);
+    w.set_flags = ctx->ctl + kCtlSetFlags;
+    w.counters = ctx->ctl + kCtlCounters;
+    w.status = reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus);
+    // Upload the plan, unless the device already holds exactly this plan at
+    // these addresses.  Copies from pageable memory are staged before the
+    // call returns, so the host vectors may go away afterwards.
+    std::vector<char> bytes;
+    auto append = [&bytes](const void *p, size_t n) {
+        const char *c = static_cast<const char *>(p);
+        bytes.insert(bytes.end(), c, c + n);
+    };
+    append(&ctx->ws_generation, sizeof(ctx->ws_generation));
+    append(&ctx->ws.ptr, sizeof(void *));
+    append(pl.sets.data(), sizeof(SetDesc) * ns);
+    append(pl.items.data(), sizeof(WorkItem) * pl.items.size());
+    append(pl.set_ev0.data(), sizeof(int64_t) * (ns + 1));
+    append(pl.set_row0.data(), sizeof(int64_t) * (ns + 1));
+    if (bytes == ctx->uploaded)
+        return HAWKES_OK;
+    ctx->uploaded.swap(bytes);
+    HK_TRY(cudaMemcpyAsync(ctx->d_sets, pl.sets.data(), sizeof(SetDesc) * ns, cudaMemcpyHostToDevice, stream),
+           "upload set descriptors");
+    if (!pl.items.empty())
+        HK_TRY(cudaMemcpyAsync(ctx->d_items, pl.items.data(), sizeof(WorkItem) * pl.items.size(),
+                               cudaMemcpyHostToDevice, stream),
+               "upload work items");
+    HK_TRY(cudaMemcpyAsync(ctx->d_set_ev0, pl.set_ev0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice,
+                           stream),
+           "upload set offsets");
+    HK_TRY(cudaMemcpyAsync(ctx->d_set_row0, pl.set_row0.data(), sizeof(int64_t) * (ns + 1),
+                           cudaMemcpyHostToDevice, stream),
+           "upload set rows");
+    return HAWKES_OK;
+}
+
+int persistent_grid(hawkes_ctx *ctx, int d, int pass, int warps, int nitems)
+{
+    int per_sm = ctx->occ[d][pass][warps];
+    if (ctx->opt_ctas > 0)
+        per_sm = std::min(per_sm, ctx->opt_ctas);
+    per_sm = std::max(per_sm, 1);
+    return std::max(1, std::min(nitems, per_sm * ctx->sm_count));
+}
+
+void prof_begin(hawkes_ctx *ctx, cudaStream_t s, ProfEvent &pe, int kernel, double pairs)
+{
+    pe.kernel = kernel;
+    pe.pairs = pairs;
+    cudaEventCreate(&pe.a);
+    cudaEventCreate(&pe.b);
+    cudaEventRecord(pe.a, s);
+}
+
+void prof_end(hawkes_ctx *ctx, cudaStream_t s, ProfEvent &pe)
+{
+    cudaEventRecord(pe.b, s);
+    ctx->prof_pending.push_back(pe);
+}
+
+// Validate, sort by time and pack every set of the plan.
+hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, const double *X, cudaStream_t s)
+{
+    Work &w = ctx->w;
+    const int32_t ns = (int32_t)pl.sets.size();
+    // per-evaluation control words: flagged-row count, fixup counter, set flags
+    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0, sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + ns),
+                           s),
+           "reset control words");
+    HK_TRY(launch_validate_keys(t, X, pl.n_total, pl.x_total, ctx->keys_a, ctx->vals_a, ctx->d_set_ev0, ns,
+                                w.status, s),
+           "validate");
+    ctx->launches_own += 2;  // validate, pack
+    ctx->launches_lib += ctx->opt_sorted ? 0 : 1;
+    ctx->launches_own += ctx->opt_sorted ? 1 : 0;
+    if (ctx->opt_sorted) {
+        HK_TRY(launch_identity_order(t, ctx->keys_b, ctx->vals_b, pl.n_total, ctx->d_set_ev0, ns, w.status, s),
+               "order check");
+    } else {
+        HK_TRY(launch_sort(ctx->sort_temp, ctx->sort_bytes, ctx->keys_a, ctx->keys_b, ctx->vals_a, ctx->vals_b,
+                           pl.n_total, ns, ctx->d_set_ev0, s),
+               "time sort");
+    }
+    HK_TRY(launch_pack_rows(w, X, ctx->keys_b, ctx->vals_b, pl.total_rows, ctx->d_set_row0, s), "pack");
+    return HAWKES_OK;
+}
+
+// Reset the per-evaluation control words (used between HMC evaluations).
+hawkes_status enqueue_eval_reset(hawkes_ctx *ctx, const Plan &pl, cudaStream_t s)
+{
+    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0,
+                           sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + pl.sets.size()), s),
+           "reset control words");
+    return HAWKES_OK;
+}
+
+// Pass 1 .. ell (and pass 2 .. gradient) on packed rows.
+hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
+                           double *out_grad, double *g_sorted, cudaStream_t s)
+{
+    Work &w = ctx->w;
+    const int32_t ns = (int32_t)pl.sets.size();
+    const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
+    int ndims = 0;
+    for (int d = 1; d <= kMaxD; ++d)
+        ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
+    if (fp64)
+        ctx->launches_own += want_grad ? 5 : 3;
+    else
+        ctx->launches_own += want_grad ? 2 * ndims + 4 : ndims + 2;
+    if (fp64) {
+        HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, false, s), "FP64 rate pass");
+        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, false, s), "finalize rows");
+        HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, s), "log-likelihood");
+        if (want_grad) {
+            HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
+            HK_TRY(launch_finalize_grad(w, pl.total_segs, true, out_grad, g_sorted, s), "finalize gradient");
+        }
+        return HAWKES_OK;
+    }
+    for (int d = 1; d <= kMaxD; ++d) {
+        const auto rg = pl.item_range_by_d[d];
+        if (rg.second == 0)
+            continue;
+        const int warps = pl.warps_by_d[d];
+        const int grid = persistent_grid(ctx, d, 1, warps, rg.second);
+        ProfEvent pe{};
+        if (ctx->opt_profile)
+            prof_begin(ctx, s, pe, 0, pl.pairs);
+        HK_TRY(launch_pass1_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
+        if (ctx->opt_profile)
+            prof_end(ctx, s, pe);
+    }
+    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, false, s), "finalize rows");
+    HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, s), "FP64 rate fixup");
+    if (!want_grad)
+        return HAWKES_OK;
+    for (int d = 1; d <= kMaxD; ++d) {
+        const auto rg = pl.item_range_by_d[d];
+        if (rg.second == 0)
+            continue;
+        const int warps = pl.warps_by_d[d];
+        const int grid = persistent_grid(ctx, d, 2, warps, rg.second);
+        ProfEvent pe{};
+        if (ctx->opt_profile)
+            prof_begin(ctx, s, pe, 1, pl.pairs);
+        HK_TRY(launch_pass2_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "gradient pass");
+        if (ctx->opt_profile)
+            prof_end(ctx, s, pe);
+    }
+    HK_TRY(launch_finalize_grad(w, pl.total_segs, false, out_grad, g_sorted, s), "finalize gradient");
+    HK_TRY(launch_fixup_grad(w, pl.total_segs, fix_grid, out_grad, g_sorted, s), "FP64 gradient fixup");
+    return HAWKES_OK;
+}
+
+__global__ void nan_on_invalid_kernel(const unsigned *status, double *a, int64_t na, double *b, int64_t nb)
+{
+    if ((*status & kStInvalidData) == 0)
+        return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < na)
+            a[i] = nan("");
+        else
+            b[i - na] = nan("");
+    }
+}
+
+hawkes_status enqueue_nan_on_invalid(hawkes_ctx *ctx, double *a, int64_t na, double *b, int64_t nb,
+                                     cudaStream_t s)
+{
+    if (!a)
+        na = 0;
+    if (!b)
+        nb = 0;
+    if (na + nb == 0)
+        return HAWKES_OK;
+    int grid = (int)std::min<int64_t>(1024, (na + nb + 255) / 256);
+    ++ctx->launches_own;
+    nan_on_invalid_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), a, na, b, nb);
+    HK_TRY(cudaGetLastError(), "NaN fill");
+    return HAWKES_OK;
+}
+
+hawkes_status check_common(hawkes_ctx *ctx, const void *t, const void *X, int64_t n, int32_t d,
+                           const hawkes_params *params, hawkes_precision prec)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (!t || !X)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "t and X must be device pointers");
+    if (n < 1 || n > (int64_t)1 << 30)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "n must be in [1, 2^30]");
+    if (d < 1 || d > kMaxD)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (!params || !params_ok(params))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "every parameter must be finite and > 0");
+    if (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "unknown precision");
+    return HAWKES_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI ==
+
+extern "C" {
+
+const char *hawkes_version(void) { return "hawkes 0.1.0 sm_103a"; }
+
+hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n, int32_t max_d)
+{
+    auto set_err = [](const std::string &m) {
+        std::lock_guard<std::mutex> g(g_create_err_mu);
+        g_create_err = m;
+    };
+    if (!out || max_n < 1 || max_d < 1 || max_d > kMaxD) {
+        set_err("hawkes_ctx_create: invalid argument");
+        return HAWKES_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_err("hawkes_ctx_create: no such CUDA device");
+        return HAWKES_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        set_err("hawkes_ctx_create: cudaSetDevice failed");
+        return HAWKES_ERR_CUDA;
+    }
+    hawkes_ctx *ctx = new hawkes_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // control block and a workspace sized for one set of max_n events
+    if (cudaMalloc(&ctx->ctl, sizeof(int32_t) * (kCtlSetFlags + 64)) != cudaSuccess ||
+        cudaMemset(ctx->ctl, 0, sizeof(int32_t) * (kCtlSetFlags + 64)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        set_err("hawkes_ctx_create: control block allocation failed");
+        return HAWKES_ERR_OOM;
+    }
+    ctx->ctl_sets = 64;
+    for (int d = 1; d <= kMaxD; ++d)
+        for (int pass = 1; pass <= 2; ++pass)
+            for (int wv : {1, 2, 4, 8})
+                ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
+    Plan pl;
+    hawkes_params p{1, 1, 1, 1, 1, 1};
+    const int64_t n64 = max_n;
+    if (build_plan(ctx, pl, 1, &n64, &max_d, &p, false) != HAWKES_OK ||
+        bind_plan(ctx, pl, 0) != HAWKES_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        set_err("hawkes_ctx_create: " + ctx->err);
+        hawkes_ctx_destroy(ctx);
+        return HAWKES_ERR_OOM;
+    }
+    *out = ctx;
+    return HAWKES_OK;
+}
+
+void hawkes_ctx_destroy(hawkes_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    for (auto &pe : ctx->prof_pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    if (ctx->hmc.exec)
+        cudaGraphExecDestroy(ctx->hmc.exec);
+    if (ctx->ws.ptr)
+        cudaFree(ctx->ws.ptr);
+    if (ctx->ctl)
+        cudaFree(ctx->ctl);
+    delete ctx;
+}
+
+const char *hawkes_last_error(const hawkes_ctx *ctx)
+{
+    if (!ctx) {
+        std::lock_guard<std::mutex> g(g_create_err_mu);
+        return g_create_err.c_str();
+    }
+    return ctx->err.c_str();
+}
+
+hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    HK_TRY(cudaStreamSynchronize(s), "stream synchronize");
+    unsigned st = 0;
+    HK_TRY(cudaMemcpy(&st, ctx->ctl + kCtlStatus, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+    HK_TRY(cudaMemset(ctx->ctl + kCtlStatus, 0, sizeof(unsigned)), "clear status");
+    if (st & kStInvalidData)
+        return fail(ctx, HAWKES_ERR_INVALID_DATA,
+                    (st & kStNotSorted) ? "times are not sorted although HAWKES_OPT_TIMES_SORTED is set"
+                                        : "non-finite location or time, or a negative time");
+    if (st & kStTimeout)
+        return fail(ctx, HAWKES_ERR_TIMEOUT, "a device-side wait timed out");
+    if (st & kStZeroRate)
+        return fail(ctx, HAWKES_ERR_ZERO_RATE, "some rate lambda_n is zero: ell = -inf, gradient undefined");
+    ctx->err.clear();
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    switch (option) {
+    case HAWKES_OPT_BLOCK_WARPS:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "block warps must be 0, 1, 2, 4 or 8");
+        ctx->opt_warps = (int)value;
+        return HAWKES_OK;
+    case HAWKES_OPT_CTAS_PER_SM:
+        if (value < 0 || value > 32)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "CTAs per SM must be in [0, 32]");
+        ctx->opt_ctas = (int)value;
+        return HAWKES_OK;
+    case HAWKES_OPT_PROFILE:
+        ctx->opt_profile = value ? 1 : 0;
+        return HAWKES_OK;
+    case HAWKES_OPT_TIMES_SORTED:
+        ctx->opt_sorted = value ? 1 : 0;
+        return HAWKES_OK;
+    case HAWKES_OPT_MIXED_FIXUP_EXP:
+        if (value < -120 || value > 0)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "fixup exponent must be in [-120, 0]");
+        ctx->opt_fixup_exp = (int)value;
+        return HAWKES_OK;
+    default:
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
+hawkes_status hawkes_ctx_kernel_stats(hawkes_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches,
+                                      double *pairs)
+{
+    if (!ctx || kernel < 0 || kernel > 1)
+        return HAWKES_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    for (auto &pe : ctx->prof_pending) {
+        HK_TRY(cudaEventSynchronize(pe.b), "profiling event");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, pe.a, pe.b);
+        ctx->prof_ms[pe.kernel] += ms;
+        ctx->prof_launches[pe.kernel] += 1;
+        ctx->prof_pairs[pe.kernel] += pe.pairs;
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    ctx->prof_pending.clear();
+    if (total_ms)
+        *total_ms = ctx->prof_ms[kernel];
+    if (launches)
+        *launches = ctx->prof_launches[kernel];
+    if (pairs)
+        *pairs = ctx->prof_pairs[kernel];
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_ctx_reset_stats(hawkes_ctx *ctx)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    hawkes_ctx_kernel_stats(ctx, 0, nullptr, nullptr, nullptr);
+    ctx->launches_own = 0;
+    ctx->launches_lib = 0;
+    for (int k = 0; k < 2; ++k) {
+        ctx->prof_ms[k] = 0;
+        ctx->prof_launches[k] = 0;
+        ctx->prof_pairs[k] = 0;
+    }
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64_t *library)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (own)
+        *own = ctx->launches_own;
+    if (library)
+        *library = ctx->launches_lib;
+    return HAWKES_OK;
+}
+
+static hawkes_status loglik_common(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                                   const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                                   double *out_loglik, double *out_grad_X, double *out_grad_params, bool grad)
+{
+    hawkes_status st = check_common(ctx, t, X, n, d, params, prec);
+    if (st != HAWKES_OK)
+        return st;
+    if (!out_loglik || (grad && !out_grad_X))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "output pointers must be device pointers");
+    if (out_grad_params)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "the parameter gradient is not available in this build");
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == HAWKES_PREC_FP64;
+    Plan pl;
+    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64)) != HAWKES_OK)
+        return st;
+    if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_eval(ctx, pl, fp64, grad, out_loglik, grad ? out_grad_X : nullptr, nullptr, s)) != HAWKES_OK)
+        return st;
+    return enqueue_nan_on_invalid(ctx, out_loglik, 1, grad ? out_grad_X : nullptr, n * d, s);
+}
+
+hawkes_status hawkes_loglik(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                            const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                            double *out_loglik)
+{
+    return loglik_common(ctx, t, X, n, d, params, prec, stream, out_loglik, nullptr, nullptr, false);
+}
+
+hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                                           const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                                           double *out_loglik, double *out_grad_X, double *out_grad_params)
+{
+    return loglik_common(ctx, t, X, n, d, params, prec, stream, out_loglik, out_grad_X, out_grad_params, true);
+}
+
+hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
+                                      const double *box_lo, const double *box_hi, int64_t n, int32_t d,
+                                      const hawkes_params *params, double eps, int32_t n_steps, const double *log_u,
+                                      hawkes_precision prec, hawkes_stream stream, double *out_H0, double *out_H1,
+                                      int32_t *out_accepted)
+{
+    hawkes_status st = check_common(ctx, t, X_inout, n, d, params, prec);
+    if (st != HAWKES_OK)
+        return st;
+    if (!p0 || !log_u || !out_H0 || !out_H1 || !out_accepted)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "p0, log_u and the outputs must be device pointers");
+    if ((box_lo == nullptr) != (box_hi == nullptr))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "box_lo and box_hi must both be given or both be NULL");
+    if (!(eps > 0.0) || !std::isfinite(eps))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (n_steps < 0 || n_steps > 100000)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "n_steps must be in [0, 100000]");
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == HAWKES_PREC_FP64;
+    Plan pl;
+    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64)) != HAWKES_OK)
+        return st;
+    if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_prep(ctx, pl, t, X_inout, s)) != HAWKES_OK)
+        return st;
+    Work &w = ctx->w;
+    HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, p0, ctx->hp, pl.total_rows, 0.0, s), "gather momenta");
+    const bool box = box_lo != nullptr;
+    if (box) {
+        HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, box_lo, ctx->hlo, pl.total_rows, 0.0, s), "gather box");
+        HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, box_hi, ctx->hhi, pl.total_rows, 0.0, s), "gather box");
+    }
+    HK_TRY(launch_set_scalar(ctx->hscal + 0, eps, s), "step size");
+    HK_TRY(cudaMemcpyAsync(ctx->hscal + 1, log_u, sizeof(double), cudaMemcpyDeviceToDevice, s), "log u");
+    HK_TRY(cudaMemsetAsync(ctx->hint, 0, sizeof(int32_t) * 2, s), "flags");
+
+    // the trajectory itself: captured once per shape, replayed as a graph
+    const auto key = std::make_tuple((int64_t)n, d, n_steps, (int32_t)prec, box, ctx->ws_generation);
+    if (!ctx->hmc.exec || ctx->hmc.key != key || ctx->opt_profile) {
+        if (ctx->hmc.exec) {
+            cudaGraphExecDestroy(ctx->hmc.exec);
+            ctx->hmc.exec = nullptr;
+        }
+        cudaStream_t cs;
+        HK_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        const bool capture = !ctx->opt_profile;  // event timing is not captured
+        cudaStream_t es = capture ? cs : s;
+        if (capture)
+            HK_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        hawkes_status st2 = HAWKES_OK;
+        auto body = [&]() -> hawkes_status {
+            hawkes_status r;
+            if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
+                return r;
+            if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+                return r;
+            HK_TRY(launch_energy(w, ctx->hp, ctx->hscal + 2, es), "H0");
+            for (int32_t k = 0; k < n_steps; ++k) {
+                HK_TRY(launch_kick_drift(w, ctx->d_set_row0, ctx->hp, ctx->hg, box ? ctx->hlo : nullptr,
+                                         box ? ctx->hhi : nullptr, ctx->hscal, pl.total_rows, k == 0 ? 1 : 2, !fp64,
+                                         ctx->hint + 1, es),
+                       "leapfrog drift");
+                if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
+                    return r;
+                if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+                    return r;
+            }
+            if (n_steps > 0)
+                HK_TRY(launch_kick(w, ctx->d_set_row0, ctx->hp, ctx->hg, ctx->hscal, pl.total_rows, es),
+                       "leapfrog kick");
+            HK_TRY(launch_energy(w, ctx->hp, ctx->hscal + 3, es), "H1");
+            HK_TRY(launch_accept(ctx->hscal + 2, ctx->hscal + 3, ctx->hscal + 1, ctx->hint + 1, ctx->hint, es),
+                   "accept");
+            return HAWKES_OK;
+        };
+        if (capture) {
+            // capture only records; the graph later runs on s after the prologue
+            cudaGraph_t graph = nullptr;
+            st2 = body();
+            cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (st2 != HAWKES_OK) {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                cudaStreamDestroy(cs);
+                return st2;
+            }
+            if (ce != cudaSuccess) {
+                cudaStreamDestroy(cs);
+                return cuda_fail(ctx, ce, "end capture");
+            }
+            ce = cudaGraphInstantiate(&ctx->hmc.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            if (ce != cudaSuccess) {
+                ctx->hmc.exec = nullptr;
+                return cuda_fail(ctx, ce, "instantiate trajectory graph");
+            }
+            ctx->hmc.key = key;
+        } else {
+            cudaStreamDestroy(cs);
+            if ((st2 = body()) != HAWKES_OK)
+                return st2;
+        }
+    }
+    if (ctx->hmc.exec && !ctx->opt_profile)
+        HK_TRY(cudaGraphLaunch(ctx->hmc.exec, s), "launch trajectory graph");
+    HK_TRY(launch_scatter(w, ctx->d_set_row0, w.x64, X_inout, ctx->hint, pl.total_rows, s), "write back");
+    HK_TRY(cudaMemcpyAsync(out_H0, ctx->hscal + 2, sizeof(double), cudaMemcpyDeviceToDevice, s), "H0 out");
+    HK_TRY(cudaMemcpyAsync(out_H1, ctx->hscal + 3, sizeof(double), cudaMemcpyDeviceToDevice, s), "H1 out");
+    HK_TRY(cudaMemcpyAsync(out_accepted, ctx->hint, sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "accept out");
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets, const int32_t *dims,
+                                       const double *t, const double *X, const hawkes_params *params,
+                                       hawkes_precision prec, hawkes_stream stream, double *out_loglik,
+                                       double *out_grad_X)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (n_sets < 1 || !offsets || !dims || !params || !t || !X || !out_loglik || !out_grad_X)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "invalid batch arguments");
+    if (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "unknown precision");
+    if (offsets[0] != 0)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "offsets[0] must be 0");
+    std::vector<int64_t> counts(n_sets);
+    int64_t xt = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        counts[s] = offsets[s + 1] - offsets[s];
+        if (counts[s] < 1 || counts[s] > (int64_t)1 << 30)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "every set needs at least one event");
+        if (dims[s] < 1 || dims[s] > kMaxD)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "dims must be in [1, 8]");
+        if (!params_ok(&params[s]))
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "every parameter must be finite and > 0");
+        xt += counts[s] * dims[s];
+    }
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == HAWKES_PREC_FP64;
+    Plan pl;
+    hawkes_status st;
+    if ((st = build_plan(ctx, pl, n_sets, counts.data(), dims, params, fp64)) != HAWKES_OK)
+        return st;
+    if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_eval(ctx, pl, fp64, true, out_loglik, out_grad_X, nullptr, s)) != HAWKES_OK)
+        return st;
+    return enqueue_nan_on_invalid(ctx, out_loglik, n_sets, out_grad_X, xt, s);
+}
+
+}  // extern "C"

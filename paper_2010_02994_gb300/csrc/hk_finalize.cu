@@ -1,0 +1,428 @@
+// Row finalization in FP64: rates and log-likelihood (Eq. (1)), gradients
+// (Appendix A), and the FP64 recomputation of rows whose mixed-precision
+// rate is too small to trust in FP32.
+//
+// Mixed path.  S_n is the FP64 sum of the pair kernel's FP32 partial slots
+// (fixed slot order).  A row with S_n < s_min (or not finite) is "flagged":
+// FP32 kernel values below 2^-126 flush to zero, so such a row's rate could
+// have lost a noticeable share of its terms.  Flagged rows get their rate,
+// their own gradient, and their 1/lambda_n contribution to every other row's
+// gradient from FP64 loops over all events; in the FP32 gradient pass their
+// weight w_n is zero.  Flagged rows are listed per finalize CTA (segment) in
+// row order, so every sum over them is also taken in a fixed order.
+#include <cmath>
+
+#include "hk_internal.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr int kT = kFinalizeThreads;
+
+struct Nsum {
+    double s = 0.0, c = 0.0;
+    __device__ void add(double x)
+    {
+        const double t = s + x;
+        if (!isfinite(t)) {
+            s = t;
+            c = 0.0;
+            return;
+        }
+        if (fabs(s) >= fabs(x))
+            c += (s - t) + x;
+        else
+            c += (x - t) + s;
+        s = t;
+    }
+    __device__ double value() const { return isfinite(s) ? s + c : s; }
+};
+
+__device__ __forceinline__ int set_of_segment(const Work &w, int g)
+{
+    int lo = 0, hi = w.nsets - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (w.sets[mid].seg0 <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Fixed-order tree sum over the CTA (blockDim.x == kT).
+__device__ double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+struct PairFp64 {
+    double a, b, c, Cmu, Cxi, omega, itx2, ih2;
+    __device__ explicit PairFp64(const SetDesc &S)
+    {
+        const double two_pi = 6.283185307179586476925286766559;
+        a = 0.5 / (S.tau_x * S.tau_x);
+        b = 0.5 / (S.tau_t * S.tau_t);
+        c = 0.5 / (S.h * S.h);
+        Cmu = S.mu0 / (pow(S.tau_x, (double)S.d) * S.tau_t * pow(two_pi, 0.5 * (S.d + 1)));
+        Cxi = S.theta * S.omega / (pow(S.h, (double)S.d) * pow(two_pi, 0.5 * S.d));
+        omega = S.omega;
+        itx2 = 1.0 / (S.tau_x * S.tau_x);
+        ih2 = 1.0 / (S.h * S.h);
+    }
+};
+
+// ------------------------------------------------------ finalize rows --
+
+__global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int theta)
+{
+    __shared__ double sh[kT];
+    __shared__ int wcount[kT / 32];
+    const int g = blockIdx.x;
+    const int s = set_of_segment(w, g);
+    const SetDesc &S = w.sets[s];
+    const int i = (g - S.seg0) * kT + threadIdx.x;
+    const bool active = i < S.n;
+    bool flagged = false;
+    double lnl_v = 0.0;
+    if (active) {
+        const int64_t r = S.row0 + i;
+        double lam;
+        if (fp64) {
+            const int V = theta ? kPass1ThetaVals : 1;
+            Nsum acc;
+            Nsum th[kPass1ThetaVals];
+            for (int sp = 0; sp < S.fsplit; ++sp) {
+                const double *F = w.F1 + S.fpart0 + (int64_t)sp * V * S.npad + i;
+                if (theta) {
+                    for (int v = 0; v < kPass1ThetaVals; ++v)
+                        th[v].add(F[(int64_t)v * S.npad]);
+                } else {
+                    acc.add(F[0]);
+                }
+            }
+            if (theta) {
+                for (int v = 0; v < kPass1ThetaVals; ++v)
+                    w.theta_rows[r * kPass1ThetaVals + v] = th[v].value();
+                lam = th[0].value() + th[1].value();
+            } else {
+                lam = acc.value();
+            }
+        } else {
+            double sum = 0.0;
+            const float *P = w.P1 + S.part0 + i;
+            for (int slot = 0; slot < S.nblk; ++slot)
+                sum += (double)P[(int64_t)slot * S.npad];
+            flagged = !(sum >= S.s_min);
+            lam = S.Pmu * sum;
+            w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
+        }
+        if (!flagged) {
+            w.lam64[r] = lam;
+            w.w64[r] = 1.0 / lam;
+            lnl_v = log(lam) - w.Lam64[r];
+            w.lnl[r] = lnl_v;
+            if (!(lam > 0.0))
+                atomicOr(&w.set_flags[s], 1);
+        }
+    }
+    // flagged rows of this segment, in row order
+    const unsigned ball = __ballot_sync(0xffffffffu, flagged);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        wcount[wid] = __popc(ball);
+    const double tot = block_sum(flagged ? 0.0 : lnl_v, sh);
+    int off = 0;
+    for (int q = 0; q < wid; ++q)
+        off += wcount[q];
+    if (flagged)
+        w.seg_rows[(int64_t)g * kT + off + __popc(ball & ((1u << lane) - 1u))] = i;
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int q = 0; q < kT / 32; ++q)
+            cnt += wcount[q];
+        w.seg_count[g] = cnt;
+        w.seg_sum[g] = tot;
+        if (cnt)
+            atomicAdd(&w.counters[2], cnt);
+    }
+}
+
+// FP64 rate of one row, summed by the whole CTA in a fixed order.
+__device__ double rate_fp64(const Work &w, const SetDesc &S, int i, double *sh)
+{
+    const PairFp64 k(S);
+    const int64_t R0 = S.row0;
+    const double tn = w.t64[R0 + i];
+    Nsum acc;
+    for (int m = threadIdx.x; m < S.n; m += kT) {
+        const double tm = w.t64[R0 + m];
+        if (tm == tn)
+            continue;
+        double r2 = 0.0;
+        for (int q = 0; q < S.d; ++q) {
+            const double df = w.x64[(R0 + i) * kMaxD + q] - w.x64[(R0 + m) * kMaxD + q];
+            r2 += df * df;
+        }
+        const double dt = tn - tm;
+        double v = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+        if (tm < tn)
+            v += k.Cxi * exp(-(k.omega * dt + r2 * k.c));
+        acc.add(v);
+    }
+    return block_sum(acc.value(), sh);
+}
+
+// Flagged rows get their rate in FP64; the last CTA to finish writes ell of
+// every set: the segments' sums in order, then the flagged rows in order.
+__global__ void __launch_bounds__(kT) fixup_rows_kernel(Work w, int total_segs, double *out_loglik)
+{
+    __shared__ double sh[kT];
+    __shared__ int s_last;
+    const int total_flagged = w.counters[2];
+    if (total_flagged > 0) {
+        int f = 0;  // flat index of the first flagged row of segment g
+        for (int g = 0; g < total_segs; ++g) {
+            const int cnt = w.seg_count[g];
+            for (int k2 = 0; k2 < cnt; ++k2) {
+                if ((f + k2) % (int)gridDim.x != (int)blockIdx.x)
+                    continue;
+                const int s = set_of_segment(w, g);
+                const SetDesc &S = w.sets[s];
+                const int i = w.seg_rows[(int64_t)g * kT + k2];
+                const double lam = rate_fp64(w, S, i, sh);
+                if (threadIdx.x == 0) {
+                    const int64_t r = S.row0 + i;
+                    w.lam64[r] = lam;
+                    w.w64[r] = 1.0 / lam;
+                    w.lnl[r] = log(lam) - w.Lam64[r];
+                    if (!(lam > 0.0))
+                        atomicOr(&w.set_flags[s], 1);
+                }
+            }
+            f += cnt;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&w.counters[3], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    for (int s = 0; s < w.nsets; ++s) {
+        const SetDesc &S = w.sets[s];
+        double v = 0.0;
+        for (int g = S.seg0 + threadIdx.x; g < S.seg0 + S.nseg; g += kT)
+            v += w.seg_sum[g];
+        double ell = block_sum(v, sh);
+        if (threadIdx.x == 0) {
+            if (total_flagged > 0) {
+                for (int g = S.seg0; g < S.seg0 + S.nseg; ++g)
+                    for (int k2 = 0; k2 < w.seg_count[g]; ++k2)
+                        ell += w.lnl[S.row0 + w.seg_rows[(int64_t)g * kT + k2]];
+            }
+            w.set_loglik[s] = ell;
+            if (out_loglik)
+                out_loglik[s] = ell;
+        }
+    }
+    if (threadIdx.x == 0)
+        w.counters[3] = 0;
+}
+
+// ------------------------------------------------------ finalize grad --
+
+// One thread per row: sum the gradient slots, add the FP64 contributions of
+// the flagged rows' 1/lambda terms, write in the caller's order (and sorted,
+// for the HMC integrator).
+__global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, double *out_grad, double *g_sorted)
+{
+    const int g = blockIdx.x;
+    const int s = set_of_segment(w, g);
+    const SetDesc &S = w.sets[s];
+    const int i = (g - S.seg0) * kT + threadIdx.x;
+    if (i >= S.n)
+        return;
+    const int d = S.d;
+    const int64_t r = S.row0 + i;
+    const bool zero_rate = (w.set_flags[s] & 1) != 0;
+    double gv[kMaxD];
+    if (fp64) {
+        for (int q = 0; q < d; ++q) {
+            Nsum acc;
+            for (int sp = 0; sp < S.fsplit; ++sp)
+                acc.add(w.F2[S.fpart2_0 + ((int64_t)sp * d + q) * S.npad + i]);
+            gv[q] = acc.value();
+        }
+    } else {
+        if (zero_rate && i == 0)
+            atomicOr(w.status, kStZeroRate);
+        if (w.w32[r] == 0.0f)
+            return;  // a flagged row: fixup_grad_kernel writes its gradient
+        for (int q = 0; q < d; ++q) {
+            double acc = 0.0;
+            const float *P = w.P2 + S.part2_0 + (int64_t)q * S.npad + i;
+            for (int slot = 0; slot < S.nblk; ++slot)
+                acc += (double)P[(int64_t)slot * d * S.npad];
+            gv[q] = S.Cg * acc;
+        }
+        if (w.counters[2] > 0) {
+            // contributions through the flagged rows' own rates:
+            // w_n [mu_nm / tau_x^2 + xi_nm / h^2] (x_n - x_m), xi_nm when t_m < t_n
+            const PairFp64 k(S);
+            const double tm = w.t64[r];
+            for (int gg = S.seg0; gg < S.seg0 + S.nseg; ++gg) {
+                const int cnt = w.seg_count[gg];
+                for (int k2 = 0; k2 < cnt; ++k2) {
+                    const int nrow = w.seg_rows[(int64_t)gg * kT + k2];
+                    if (nrow == i)
+                        continue;
+                    const int64_t rn = S.row0 + nrow;
+                    const double tn = w.t64[rn];
+                    if (tn == tm)
+                        continue;
+                    double r2 = 0.0;
+                    for (int q = 0; q < d; ++q) {
+                        const double df = w.x64[rn * kMaxD + q] - w.x64[r * kMaxD + q];
+                        r2 += df * df;
+                    }
+                    const double dt = tn - tm;
+                    double coef = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b)) * k.itx2;
+                    if (tm < tn)
+                        coef += k.Cxi * exp(-(k.omega * dt + r2 * k.c)) * k.ih2;
+                    coef *= w.w64[rn];
+                    for (int q = 0; q < d; ++q)
+                        gv[q] += coef * (w.x64[rn * kMaxD + q] - w.x64[r * kMaxD + q]);
+                }
+            }
+        }
+    }
+    if (zero_rate) {
+        for (int q = 0; q < d; ++q)
+            gv[q] = nan("");
+        if (fp64 && i == 0)
+            atomicOr(w.status, kStZeroRate);
+    }
+    const int src = w.perm[r];
+    if (out_grad)
+        for (int q = 0; q < d; ++q)
+            out_grad[S.x0 + (int64_t)src * d + q] = gv[q];
+    if (g_sorted)
+        for (int q = 0; q < d; ++q)
+            g_sorted[r * kMaxD + q] = gv[q];
+}
+
+// Own gradient of every flagged row, in FP64 over all events (the paper's
+// Appendix A formula in its ordered form).
+__global__ void __launch_bounds__(kT) fixup_grad_kernel(Work w, int total_segs, double *out_grad, double *g_sorted)
+{
+    __shared__ double sh[kT];
+    if (w.counters[2] == 0)
+        return;
+    int f = 0;
+    for (int g = 0; g < total_segs; ++g) {
+        const int cnt = w.seg_count[g];
+        for (int k2 = 0; k2 < cnt; ++k2) {
+            if ((f + k2) % (int)gridDim.x != (int)blockIdx.x)
+                continue;
+            const int s = set_of_segment(w, g);
+            const SetDesc &S = w.sets[s];
+            const PairFp64 k(S);
+            const int i = w.seg_rows[(int64_t)g * kT + k2];
+            const int64_t R0 = S.row0, r = R0 + i;
+            const double tn = w.t64[r], wn = w.w64[r];
+            const bool zero_rate = (w.set_flags[s] & 1) != 0;
+            const int src = w.perm[r];
+            for (int q = 0; q < S.d; ++q) {
+                Nsum acc;
+                for (int m = threadIdx.x; m < S.n; m += kT) {
+                    const double tm = w.t64[R0 + m];
+                    if (tm == tn)
+                        continue;
+                    double r2 = 0.0;
+                    for (int q2 = 0; q2 < S.d; ++q2) {
+                        const double df = w.x64[r * kMaxD + q2] - w.x64[(R0 + m) * kMaxD + q2];
+                        r2 += df * df;
+                    }
+                    const double dt = tn - tm;
+                    const double wm = w.w64[R0 + m];
+                    const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+                    const double xi = k.Cxi * exp(-(k.omega * fabs(dt) + r2 * k.c));
+                    const double coef = mu * (wn + wm) * k.itx2 + xi * (tm < tn ? wn : wm) * k.ih2;
+                    acc.add(coef * (w.x64[(R0 + m) * kMaxD + q] - w.x64[r * kMaxD + q]));
+                }
+                double gq = block_sum(acc.value(), sh);
+                if (zero_rate)
+                    gq = nan("");
+                if (threadIdx.x == 0) {
+                    if (out_grad)
+                        out_grad[S.x0 + (int64_t)src * S.d + q] = gq;
+                    if (g_sorted)
+                        g_sorted[r * kMaxD + q] = gq;
+                }
+            }
+        }
+        f += cnt;
+    }
+}
+
+__global__ void fill_nan_kernel(double *p, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = nan("");
+}
+
+}  // namespace
+
+cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s)
+{
+    finalize_rows_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, theta ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, cudaStream_t s)
+{
+    fixup_rows_kernel<<<grid, kT, 0, s>>>(w, total_segs, out_loglik);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
+                                 cudaStream_t s)
+{
+    finalize_grad_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, out_grad, g_sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,
+                              cudaStream_t s)
+{
+    fixup_grad_kernel<<<grid, kT, 0, s>>>(w, total_segs, out_grad, g_sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_nan(double *p, int64_t n, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 1024)
+        grid = 1024;
+    fill_nan_kernel<<<grid, 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -1,0 +1,162 @@
+// Internal declarations shared by the libhawkes translation units.
+//
+// Data layout (every array lives in the context's device workspace):
+//   Events are processed in time-sorted order ("rows").  A call is a list of
+//   data sets; set s owns rows [row0, row0 + npad) of every per-row array,
+//   npad = nblk * B padded up to whole blocks of B rows.
+//   rec   float4 planes: plane p of set s is rec[rec0 + p*npad + i]; the
+//         fields of row i are, in order, xh_0, xl_0, ..., xh_{D-1}, xl_{D-1},
+//         th, tl: the FP32 hi/lo split of the scaled coordinate kx*x_k and
+//         of the scaled time kt*t (nrec(D) planes, unused fields zero).
+//   w32   FP32 1/S_n for the gradient pass (0 for rows recomputed in FP64).
+//   tie_end  first set-relative row whose time exceeds this row's time.
+//   perm  set-relative caller index of each row.
+//   t64, x64  FP64 sorted times and coordinates (x64 row stride kMaxD).
+//   P1    pass-1 partial row sums, slot-major: P1[part0 + (slot*vpc + v)*npad + i]
+//   P2    pass-2 partial gradients: P2[part2_0 + (slot*D + k)*npad + i]
+//   A row n of block I receives its partial from the pair block {I, J} in
+//   slot J; each slot has exactly one writer, so every sum below is taken
+//   in a fixed order and the results are deterministic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hawkes.h"
+
+namespace hk {
+
+constexpr int kMaxD = 8;
+constexpr float kPadTime = 1.0e30f;
+constexpr int kPass1Vals = 1;       // S
+constexpr int kPass1ThetaVals = 6;  // M, Xi, sum mu' q, sum mu' dt^2, sum xi'' dt, sum xi'' q
+constexpr int kFinalizeThreads = 256;
+constexpr int kMaxThetaSets = 1;
+
+// Bits of the sticky device status word.
+enum : unsigned {
+    kStInvalidData = 1u,
+    kStZeroRate = 2u,
+    kStTimeout = 4u,
+    kStNotSorted = 8u,
+};
+
+__host__ __device__ constexpr int nrec(int d) { return (2 * d + 2 + 3) / 4; }
+// Rows each lane keeps in registers in the pair kernels.
+__host__ __device__ constexpr int rows_per_lane(int d) { return d <= 4 ? 4 : 2; }
+
+struct SetDesc {
+    int64_t row0;     // first row of the set in the per-row arrays
+    int64_t ev0;      // first event of the set in the caller's t
+    int64_t x0;       // first element of the set in the caller's X
+    int64_t rec0;     // first float4 of the set's record planes
+    int64_t part0;    // first float of the set's pass-1 partial slots
+    int64_t part2_0;  // first float of the set's pass-2 partial slots
+    int64_t fpart0;   // first double of the set's FP64 rate partial slots
+    int64_t fpart2_0; // first double of the set's FP64 gradient partial slots
+    int32_t n, d, npad, nblk, B, vpc;
+    int32_t item0, nitems;  // the set's work items (in the item list)
+    int32_t seg0;           // first finalize CTA of the set
+    int32_t nseg;           // finalize CTAs of the set
+    int32_t fsplit;         // column splits of the FP64 pair kernels
+    int32_t pad_;
+    // mixed-path exponent constants (base 2; see the pass kernels)
+    float rho, kappa, cxi1, cxi2;
+    // FP64 constants
+    double kx, kt;    // coordinate scalings sqrt(log2(e)/2)/tau_x and /tau_t
+    double Pmu;       // mu0 / (tau_x^D tau_t (2 pi)^((D+1)/2))
+    double Cg;        // 1 / (tau_x^2 kx): scaled pass-2 sums -> d ell / d x
+    double s_min;     // rows with S_n < s_min are recomputed in FP64
+    double mu0, tau_x, tau_t, theta, omega, h;
+};
+
+struct WorkItem {
+    int32_t set, I, J, kind;  // kind 0: off-diagonal pair block, 1: diagonal
+};
+
+// Device workspace views handed to the kernels.
+struct Work {
+    const SetDesc *sets;
+    int32_t nsets;
+    float4 *rec;
+    float *w32;
+    int32_t *tie_end;
+    int32_t *perm;
+    double *t64;
+    double *x64;
+    double *lam64;       // lambda_n (FP64) per row
+    double *w64;         // 1 / lambda_n per row
+    double *Lam64;       // Lambda_n per row
+    double *lnl;         // log lambda_n - Lambda_n per row
+    float *P1;
+    float *P2;
+    double *F1;          // FP64 pair-kernel partials (rates)
+    double *F2;          // FP64 pair-kernel partials (gradients)
+    double *theta_rows;  // per-row Theta-gradient sums (kPass1ThetaVals per row, FP64)
+    int32_t *seg_count;  // flagged rows found by each finalize CTA
+    int32_t *seg_rows;   // their set-relative rows (kFinalizeThreads slots per CTA)
+    double *seg_sum;     // each finalize CTA's sum of lnl over its unflagged rows
+    double *set_loglik;  // ell per set
+    int32_t *set_flags;  // bit 0: some rate of the set is zero
+    int32_t *counters;   // [0] work items taken, [1] CTAs done, [2] flagged rows, [3] fixup CTAs done
+    unsigned *status;    // sticky device status
+};
+
+// ------------------------------------------------------------ launchers --
+// Host functions that enqueue the kernels of one translation unit.  Row
+// loops locate their set by binary search in set_row0 (nsets+1 entries).
+
+// hk_prep.cu
+cudaError_t launch_validate_keys(const double *t, const double *X, int64_t n_total, int64_t x_total,
+                                 double *keys, int32_t *vals, const int64_t *set_ev0, int32_t nsets,
+                                 unsigned *status, cudaStream_t s);
+size_t sort_temp_bytes(int64_t n_total, int32_t nsets);
+cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *keys_in, double *keys_out,
+                        const int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
+                        const int64_t *d_seg_offsets, cudaStream_t s);
+cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *vals_out, int64_t n_total,
+                                  const int64_t *set_ev0, int32_t nsets, unsigned *status, cudaStream_t s);
+cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
+                             int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
+cudaError_t launch_pack_x_rows(const Work &w, int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
+
+// hk_pairs_mixed_*.cu
+cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                               cudaStream_t s);
+cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                               cudaStream_t s);
+size_t pass_smem_bytes(int d, int pass, int warps);
+int pass_max_ctas_per_sm(int d, int pass, int warps);
+
+// hk_pairs_fp64.cu
+constexpr int kFp64Rows = 128;  // rows per CTA of the FP64 pair kernels
+cudaError_t launch_pass1_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int32_t max_fsplit, int64_t max_nblk,
+                              bool theta, cudaStream_t s);
+cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int32_t max_fsplit, int64_t max_nblk,
+                              cudaStream_t s);
+
+// hk_finalize.cu
+cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s);
+cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, cudaStream_t s);
+cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
+                                 cudaStream_t s);
+cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,
+                              cudaStream_t s);
+cudaError_t launch_fill_nan(double *p, int64_t n, cudaStream_t s);
+
+// hk_hmc.cu
+cudaError_t launch_gather_sorted(const Work &w, const int64_t *set_row0, const double *src, double *dst,
+                                 int64_t total_rows, double pad, cudaStream_t s);
+cudaError_t launch_kick_drift(const Work &w, const int64_t *set_row0, double *p, const double *g, const double *lo,
+                              const double *hi, const double *eps_dev, int64_t total_rows, int kicks, bool repack,
+                              int32_t *refl_bad, cudaStream_t s);
+cudaError_t launch_kick(const Work &w, const int64_t *set_row0, double *p, const double *g, const double *eps_dev,
+                        int64_t total_rows, cudaStream_t s);
+cudaError_t launch_energy(const Work &w, const double *p, double *H_out, cudaStream_t s);
+cudaError_t launch_accept(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
+                          int32_t *accepted, cudaStream_t s);
+cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
+                           const int32_t *accepted, int64_t total_rows, cudaStream_t s);
+cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s);
+
+}  // namespace hk

@@ -1,0 +1,66 @@
+// Mixed pair kernels for D = 5..8, and the dispatch on D.
+#include "hk_pairs_mixed_launch.cuh"
+
+namespace hk {
+HK_INSTANTIATE_MIXED(5)
+HK_INSTANTIATE_MIXED(6)
+HK_INSTANTIATE_MIXED(7)
+HK_INSTANTIATE_MIXED(8)
+
+extern template cudaError_t launch_pass1_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass2_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass2_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass2_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass2_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template int occupancy_t<1>(int, int);
+extern template int occupancy_t<2>(int, int);
+extern template int occupancy_t<3>(int, int);
+extern template int occupancy_t<4>(int, int);
+extern template size_t pass_smem_bytes_t<1>(int, bool, int);
+extern template size_t pass_smem_bytes_t<2>(int, bool, int);
+extern template size_t pass_smem_bytes_t<3>(int, bool, int);
+extern template size_t pass_smem_bytes_t<4>(int, bool, int);
+
+#define HK_SWITCH_D(d, EXPR)                                                                                   \
+    switch (d) {                                                                                               \
+    case 1: { constexpr int D = 1; return EXPR; }                                                             \
+    case 2: { constexpr int D = 2; return EXPR; }                                                             \
+    case 3: { constexpr int D = 3; return EXPR; }                                                             \
+    case 4: { constexpr int D = 4; return EXPR; }                                                             \
+    case 5: { constexpr int D = 5; return EXPR; }                                                             \
+    case 6: { constexpr int D = 6; return EXPR; }                                                             \
+    case 7: { constexpr int D = 7; return EXPR; }                                                             \
+    case 8: { constexpr int D = 8; return EXPR; }                                                             \
+    default: break;                                                                                            \
+    }
+
+cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                               cudaStream_t s)
+{
+    HK_SWITCH_D(d, launch_pass1_t<D>(w, items, nitems, grid, warps, s))
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                               cudaStream_t s)
+{
+    HK_SWITCH_D(d, launch_pass2_t<D>(w, items, nitems, grid, warps, s))
+    return cudaErrorInvalidValue;
+}
+
+size_t pass_smem_bytes(int d, int pass, int warps)
+{
+    HK_SWITCH_D(d, pass_smem_bytes_t<D>(pass, false, warps))
+    return 0;
+}
+
+int pass_max_ctas_per_sm(int d, int pass, int warps)
+{
+    HK_SWITCH_D(d, occupancy_t<D>(pass, warps))
+    return 0;
+}
+
+}  // namespace hk

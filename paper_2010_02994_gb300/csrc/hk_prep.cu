@@ -1,0 +1,236 @@
+// Input validation, time sort and packing of the per-row arrays.
+//
+// The pair kernels visit events in time order: the self-excitation indicator
+// I[t_n' < t_n] of Section 2.1 then says that, of an unordered pair, only the
+// later event is excited, and exactly tied times form contiguous runs that
+// the kernels mask by index.  Coordinates and times are scaled so that the
+// background kernel's exponent is a plain sum of squares in base 2, and split
+// into an FP32 hi/lo pair so that differences of nearby events keep their
+// full relative accuracy in FP32.
+#include <cub/cub.cuh>
+
+#include <cmath>
+
+#include "hk_internal.cuh"
+
+namespace hk {
+
+namespace {
+
+__device__ __forceinline__ int find_set_by(const int64_t *starts, int nsets, int64_t idx)
+{
+    // largest s with starts[s] <= idx (starts ascending, nsets >= 1)
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= idx)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void validate_keys_kernel(const double *__restrict__ t, const double *__restrict__ X, int64_t n_total,
+                                     int64_t x_total, double *__restrict__ keys, int32_t *__restrict__ vals,
+                                     const int64_t *__restrict__ set_ev0, int32_t nsets, unsigned *status)
+{
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_total; e += stride) {
+        double v = t[e];
+        if (!(v >= 0.0) || !isfinite(v))
+            bad = true;
+        keys[e] = v;
+        int s = find_set_by(set_ev0, nsets, e);
+        vals[e] = (int32_t)(e - set_ev0[s]);
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < x_total; e += stride) {
+        if (!isfinite(X[e]))
+            bad = true;
+    }
+    if (bad)
+        atomicOr(status, kStInvalidData);
+}
+
+__global__ void identity_order_kernel(const double *__restrict__ t, double *__restrict__ keys,
+                                      int32_t *__restrict__ vals, int64_t n_total,
+                                      const int64_t *__restrict__ set_ev0, int32_t nsets, unsigned *status)
+{
+    bool unsorted = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_total; e += stride) {
+        int s = find_set_by(set_ev0, nsets, e);
+        keys[e] = t[e];
+        vals[e] = (int32_t)(e - set_ev0[s]);
+        if (e + 1 < set_ev0[s + 1] && t[e + 1] < t[e])
+            unsorted = true;
+    }
+    if (unsorted)
+        atomicOr(status, kStNotSorted | kStInvalidData);
+}
+
+// FP32 hi/lo split: hi = fl(v), lo = fl(v - hi).  For two events the
+// difference (hi_a - hi_b) + (lo_a - lo_b) then has a relative error of a
+// few FP32 units of the difference itself, not of the coordinates.
+__device__ __forceinline__ void split_hilo(double v, float &hi, float &lo)
+{
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+// One thread per row of every set.
+__global__ void pack_kernel(Work w, const double *__restrict__ X, const double *__restrict__ keys_sorted,
+                            const int32_t *__restrict__ vals_sorted, int64_t total_rows,
+                            const int64_t *__restrict__ set_row0)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows; r += stride) {
+        const int s = find_set_by(set_row0, w.nsets, r);
+        const SetDesc &S = w.sets[s];
+        const int64_t i = r - S.row0;
+        const int d = S.d;
+        const int np = nrec(d);
+        float f[4 * nrec(kMaxD)];
+#pragma unroll
+        for (int k = 0; k < 4 * nrec(kMaxD); ++k)
+            f[k] = 0.0f;
+        if (i < S.n) {
+            const int32_t src = vals_sorted[S.ev0 + i];
+            const double tv = keys_sorted[S.ev0 + i];
+            w.perm[r] = src;
+            w.t64[r] = tv;
+            for (int k = 0; k < d; ++k) {
+                double xv = X[S.x0 + (int64_t)src * d + k];
+                w.x64[r * kMaxD + k] = xv;
+                split_hilo(xv * S.kx, f[2 * k], f[2 * k + 1]);
+            }
+            split_hilo(tv * S.kt, f[2 * d], f[2 * d + 1]);
+            // Lambda_n, Section 2.1 (T = the set's largest time)
+            const double T = keys_sorted[S.ev0 + S.n - 1];
+            const double a = T - tv;
+            w.Lam64[r] = S.mu0 * (normcdf(a / S.tau_t) - normcdf(-tv / S.tau_t)) - S.theta * expm1(-S.omega * a);
+            // first row of a strictly later time (upper bound of tv)
+            int64_t lo = i + 1, hi = S.n;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (keys_sorted[S.ev0 + mid] > tv)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            w.tie_end[r] = (int32_t)lo;
+        } else {
+            w.perm[r] = -1;
+            w.t64[r] = 0.0;
+            for (int k = 0; k < d; ++k)
+                w.x64[r * kMaxD + k] = 0.0;
+            f[2 * d] = kPadTime;
+            w.Lam64[r] = 0.0;
+            w.tie_end[r] = (int32_t)(i + 1);
+        }
+        w.w32[r] = 0.0f;
+        for (int p = 0; p < np; ++p)
+            w.rec[S.rec0 + (int64_t)p * S.npad + i] = make_float4(f[4 * p], f[4 * p + 1], f[4 * p + 2], f[4 * p + 3]);
+    }
+}
+
+// Re-pack the coordinate fields from x64 (HMC: the locations moved, the
+// times did not).
+__global__ void pack_x_kernel(Work w, int64_t total_rows, const int64_t *__restrict__ set_row0)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows; r += stride) {
+        const int s = find_set_by(set_row0, w.nsets, r);
+        const SetDesc &S = w.sets[s];
+        const int64_t i = r - S.row0;
+        if (i >= S.n)
+            continue;
+        const int d = S.d;
+        float f[2 * kMaxD];
+        for (int k = 0; k < d; ++k)
+            split_hilo(w.x64[r * kMaxD + k] * S.kx, f[2 * k], f[2 * k + 1]);
+        // rewrite the planes that hold coordinate fields, keeping th/tl
+        const int np = nrec(d);
+        for (int p = 0; p < np; ++p) {
+            float4 v = w.rec[S.rec0 + (int64_t)p * S.npad + i];
+            float *c = reinterpret_cast<float *>(&v);
+            for (int q = 0; q < 4; ++q) {
+                int fld = 4 * p + q;
+                if (fld < 2 * d)
+                    c[q] = f[fld];
+            }
+            w.rec[S.rec0 + (int64_t)p * S.npad + i] = v;
+        }
+    }
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1)
+        g = 1;
+    if (g > 4096)
+        g = 4096;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_validate_keys(const double *t, const double *X, int64_t n_total, int64_t x_total, double *keys,
+                                 int32_t *vals, const int64_t *set_ev0, int32_t nsets, unsigned *status,
+                                 cudaStream_t s)
+{
+    validate_keys_kernel<<<grid_for(x_total > n_total ? x_total : n_total, 256), 256, 0, s>>>(
+        t, X, n_total, x_total, keys, vals, set_ev0, nsets, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *vals_out, int64_t n_total,
+                                  const int64_t *set_ev0, int32_t nsets, unsigned *status, cudaStream_t s)
+{
+    identity_order_kernel<<<grid_for(n_total, 256), 256, 0, s>>>(t, keys_out, vals_out, n_total, set_ev0, nsets,
+                                                                    status);
+    return cudaGetLastError();
+}
+
+size_t sort_temp_bytes(int64_t n_total, int32_t nsets)
+{
+    size_t bytes = 0;
+    if (nsets <= 1) {
+        cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const double *)nullptr, (double *)nullptr,
+                                        (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total);
+    } else {
+        cub::DeviceSegmentedRadixSort::SortPairs(nullptr, bytes, (const double *)nullptr, (double *)nullptr,
+                                                 (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total, nsets,
+                                                 (const int64_t *)nullptr, (const int64_t *)nullptr);
+    }
+    return bytes;
+}
+
+cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *keys_in, double *keys_out,
+                        const int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
+                        const int64_t *d_seg_offsets, cudaStream_t s)
+{
+    // Radix sort is stable: events with equal times keep the caller's order.
+    if (nsets <= 1)
+        return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out, (int)n_total,
+                                               0, 64, s);
+    return cub::DeviceSegmentedRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out,
+                                                    (int)n_total, nsets, d_seg_offsets, d_seg_offsets + 1, 0, 64, s);
+}
+
+cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
+                             int64_t total_rows, const int64_t *set_row0, cudaStream_t s)
+{
+    pack_kernel<<<grid_for(total_rows, 256), 256, 0, s>>>(w, X, keys_sorted, vals_sorted, total_rows, set_row0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_x_rows(const Work &w, int64_t total_rows, const int64_t *set_row0, cudaStream_t s)
+{
+    pack_x_kernel<<<grid_for(total_rows, 256), 256, 0, s>>>(w, total_rows, set_row0);
+    return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -1,0 +1,216 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (fixed for this method): the FP64 path within 1e-12 (relative for
+ell, relative L2 for the gradient); the mixed path within 1e-6 for ell and
+1e-5 for the gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-12, 1e-12), "mixed": (1e-6, 1e-5)}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2010_02994_gb300 import HawkesContext
+
+    c = HawkesContext(device=0, max_n=100_000, max_d=8)
+    yield c
+    c.close()
+
+
+def gpu_eval(ctx, w, prec, t=None, X=None):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik_grad_locations
+
+    t = torch.tensor(w.t if t is None else t, device="cuda")
+    X = torch.tensor(w.X if X is None else X, device="cuda")
+    ell, g = hawkes_loglik_grad_locations(ctx, t, X, w.params, precision=prec)
+    return ell.item(), g.cpu().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close(ctx, w, prec, ref=None):
+    ell_ref, g_ref = ref if ref is not None else oracle.loglik_and_grad(w.t, w.X, w.params)[:2]
+    ell, g = gpu_eval(ctx, w, prec)
+    tl, tg = TOL[prec]
+    assert math.isfinite(ell)
+    el = abs(ell - ell_ref) / abs(ell_ref)
+    eg = rel_l2(g, g_ref)
+    assert el <= tl, f"{w.name} {prec}: ell {ell} vs {ell_ref} (rel {el:.2e})"
+    assert eg <= tg, f"{w.name} {prec}: grad rel-L2 {eg:.2e}"
+    return el, eg
+
+
+CASES = [
+    (1, 2, 1, 0), (2, 3, 3, 0), (3, 37, 2, 0), (4, 130, 1, 1), (5, 700, 2, 2), (6, 1100, 3, 0),
+    (7, 300, 5, 1), (8, 260, 8, 0), (9, 513, 4, 2), (10, 129, 6, 0), (11, 200, 7, 0), (12, 2600, 2, 3),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed,n,d,ties", CASES)
+def test_random_cases(ctx, prec, seed, n, d, ties):
+    w = synth.random_case(seed, n, d, ties=ties, shuffle=True)
+    assert_close(ctx, w, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("make", [synth.make_c1, synth.make_c3, synth.make_c2])
+def test_paper_shaped_workloads(ctx, prec, make):
+    w = make()
+    assert_close(ctx, w, prec)
+
+
+@pytest.fixture(scope="module")
+def c5_reference():
+    """Oracle rates of every row of the N=1e5 workload, and ell_n, grad_n of
+    2,000 seeded random rows."""
+    w = synth.make_c5()
+    lam = oracle.rates(w.t, w.X, w.params)
+    _, Lam = oracle.Lambda(w.t, w.params, per_event=True)
+    ell = float(np.sum(np.log(lam)) - np.sum(Lam))
+    rows = np.sort(np.random.default_rng(5).choice(w.n, size=2000, replace=False))
+    g_rows = oracle.grad_rows(w.t, w.X, w.params, lam, rows)
+    return w, ell, rows, g_rows
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_large_workload_sampled_rows(ctx, c5_reference, prec):
+    w, ell_ref, rows, g_rows = c5_reference
+    ell, g = gpu_eval(ctx, w, prec)
+    tl, tg = TOL[prec]
+    assert abs(ell - ell_ref) / abs(ell_ref) <= tl
+    assert rel_l2(g[rows], g_rows) <= tg
+    # translation invariance holds at every size: sum_n grad_n = 0
+    assert np.all(np.abs(g.sum(axis=0)) <= 1e-6 * np.abs(g).sum(axis=0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_event_and_all_tied(ctx, prec):
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesError, hawkes_loglik, hawkes_loglik_grad_locations
+
+    P = synth.random_case(0, 2, 2).params
+    for t_np, X_np in (([1.0], [[0.3, 0.2]]), ([2.0, 2.0, 2.0], [[0.0, 0.0], [0.1, 0.0], [0.0, 0.2]])):
+        t = torch.tensor(t_np, dtype=torch.float64, device="cuda")
+        X = torch.tensor(X_np, dtype=torch.float64, device="cuda")
+        ell = hawkes_loglik(ctx, t, X, P, precision=prec)
+        assert ell.item() == -math.inf
+        with pytest.raises(HawkesError) as e:
+            hawkes_loglik_grad_locations(ctx, t, X, P, precision=prec)
+        assert "ZERO_RATE" in str(e.value)
+        ctx.sync_status()  # the status is cleared once reported
+
+
+def test_ragged_block_edges(ctx):
+    """Sizes around the pair-block edge with the smallest block (128 rows at D=2)."""
+    ctx.set_option("block_warps", 1)
+    try:
+        for n in (127, 128, 129, 257, 383):
+            w = synth.random_case(40 + n, n, 2, ties=1, shuffle=True)
+            assert_close(ctx, w, "mixed")
+    finally:
+        ctx.set_option("block_warps", 0)
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+def test_every_block_shape(ctx, warps):
+    ctx.set_option("block_warps", warps)
+    try:
+        for d in (2, 3, 8):
+            w = synth.random_case(60 + warps * 10 + d, 1500, d, ties=2, shuffle=True)
+            assert_close(ctx, w, "mixed")
+    finally:
+        ctx.set_option("block_warps", 0)
+
+
+def test_isolated_events_take_the_fp64_fixup(ctx):
+    """Events far from every other in space and time have rates far below the
+    FP32 range of the kernel values; they are recomputed in FP64."""
+    w = synth.random_case(77, 600, 2, shuffle=True)
+    t = w.t.copy()
+    X = w.X.copy()
+    t[5] += 400.0       # far in time: the background kernel underflows
+    X[5] += 60.0
+    t[17] = 200.0
+    X[17] = [-50.0, 30.0]
+    w2 = synth.Workload("isolated", t, X, X, None, None, w.params)
+    lam = oracle.rates(t, X, w.params)
+    assert lam[5] < 1e-30 and lam[17] < 1e-30
+    assert_close(ctx, w2, "mixed")
+    assert_close(ctx, w2, "fp64")
+
+
+def test_invalid_data_is_reported(ctx):
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesError, hawkes_loglik_grad_locations
+
+    w = synth.random_case(3, 50, 2)
+    for bad in ("nan_x", "neg_t", "inf_t"):
+        t = torch.tensor(w.t, device="cuda")
+        X = torch.tensor(w.X, device="cuda")
+        if bad == "nan_x":
+            X[3, 1] = float("nan")
+        elif bad == "neg_t":
+            t[7] = -1.0
+        else:
+            t[0] = float("inf")
+        with pytest.raises(HawkesError) as e:
+            hawkes_loglik_grad_locations(ctx, t, X, w.params)
+        assert "INVALID_DATA" in str(e.value)
+    # the context is usable afterwards
+    assert_close(ctx, w, "mixed")
+
+
+def test_invalid_arguments(ctx):
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesError, hawkes_loglik
+
+    t = torch.zeros(4, dtype=torch.float64, device="cuda")
+    X = torch.zeros(4, 9, dtype=torch.float64, device="cuda")
+    with pytest.raises(HawkesError):
+        hawkes_loglik(ctx, t, X, synth.random_case(0, 2, 2).params)
+    with pytest.raises(HawkesError):
+        hawkes_loglik(ctx, t, X[:, :2], dict(synth.random_case(0, 2, 2).params, h=-1.0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_deterministic_and_permutation_equivariant(ctx, prec):
+    w = synth.random_case(91, 1800, 2, shuffle=True)
+    a = gpu_eval(ctx, w, prec)
+    b = gpu_eval(ctx, w, prec)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    perm = np.random.default_rng(1).permutation(w.n)
+    c = gpu_eval(ctx, w, prec, t=w.t[perm], X=w.X[perm])
+    assert c[0] == a[0] and np.array_equal(c[1], a[1][perm])
+
+
+def test_times_sorted_option(ctx):
+    from paper_2010_02994_gb300 import HawkesError
+
+    w = synth.random_case(5, 900, 2, shuffle=False)
+    ref = gpu_eval(ctx, w, "mixed")
+    ctx.set_option("times_sorted", 1)
+    try:
+        got = gpu_eval(ctx, w, "mixed")
+        assert got[0] == ref[0] and np.array_equal(got[1], ref[1])
+        ws = synth.random_case(5, 900, 2, shuffle=True)
+        with pytest.raises(HawkesError):
+            gpu_eval(ctx, ws, "mixed")
+    finally:
+        ctx.set_option("times_sorted", 0)
