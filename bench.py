@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
     args = ap.parse_args()
     args.steps_ref = max(1, min(args.steps, 10))
     args.warmup_ref = min(args.warmup, 1)
@@ -221,6 +223,13 @@ def main():
     X = torch.tensor(w.X, device=dev)
     ell = torch.empty((), dtype=torch.float64, device=dev)
     g = torch.empty((n, d), dtype=torch.float64, device=dev)
+    if args.kernels_only:
+        for _ in range(args.warmup + args.steps):
+            hawkes_loglik_grad_locations(ctx, t, X, w.params, precision="mixed", check=False, out=(ell, g, None))
+        ctx.sync_status()
+        torch.cuda.synchronize()
+        ctx.close()
+        return 0
     l2 = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 

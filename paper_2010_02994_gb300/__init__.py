@@ -7,3 +7,4 @@ only marshals torch tensors into it.
 """
 from .api import (HawkesContext, HawkesError, hawkes_batch_loglik_grad, hawkes_loglik,  # noqa: F401
                   hawkes_loglik_grad_locations, hmc_leapfrog_trajectory, params_struct, version)
+from .autograd import HawkesLogLik, hawkes_loglik_autograd  # noqa: F401,E402

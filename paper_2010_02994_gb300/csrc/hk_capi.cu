@@ -98,7 +98,7 @@ struct hawkes_ctx {
     double prof_pairs[2] = {0, 0};
     int64_t launches_own = 0, launches_lib = 0;
     HmcGraph hmc;
-    int occ[kMaxD + 1][3][9] = {};  // CTAs per SM of the pair kernels: [d][pass][warps]
+    int occ[kMaxD + 1][4][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..3][warps]
     std::vector<char> uploaded;     // bytes of the plan last copied to the device
     // workspace views of the current plan
     Work w{};
@@ -147,7 +147,7 @@ bool params_ok(const hawkes_params *p)
 
 // Warps per CTA of the pair kernels for a set of n events in d dimensions:
 // the largest count that still gives every SM slot several pair blocks.
-int choose_warps(const hawkes_ctx *ctx, int64_t n, int d)
+int choose_warps(const hawkes_ctx *ctx, int64_t n, int d, bool theta)
 {
     if (ctx->opt_warps > 0)
         return ctx->opt_warps;
@@ -155,7 +155,7 @@ int choose_warps(const hawkes_ctx *ctx, int64_t n, int d)
     const int candidates[4] = {8, 4, 2, 1};
     for (int wv : candidates) {
         // shared memory per CTA must leave room for two CTAs per SM
-        if (pass_smem_bytes(d, 2, wv) > 110 * 1024)
+        if (pass_smem_bytes(d, 2, wv) > 110 * 1024 || (theta && pass_smem_bytes(d, 3, wv) > 110 * 1024))
             continue;
         const int64_t B = 32LL * R * wv;
         const int64_t T = (n + B - 1) / B;
@@ -200,7 +200,7 @@ bool mixed_range_ok(const SetDesc &S)
 
 // Lay out the sets of one call and build the work list.
 hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t *ev_counts, const int32_t *dims,
-                         const hawkes_params *params, bool fp64)
+                         const hawkes_params *params, bool fp64, bool theta = false)
 {
     pl = Plan();
     pl.sets.resize(nsets);
@@ -214,7 +214,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
     for (int d = 1; d <= kMaxD; ++d)
         if (nmax_by_d[d] > 0)
-            pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d);
+            pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d, theta);
     int64_t ev = 0, x = 0, row = 0, rec4 = 0, p1 = 0, p2 = 0, f1 = 0, f2 = 0;
     int32_t seg = 0;
     for (int s = 0; s < nsets; ++s) {
@@ -238,7 +238,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         S.part2_0 = p2;
         S.fpart0 = f1;
         S.fpart2_0 = f2;
-        S.vpc = 1;
+        S.vpc = theta ? kPass1ThetaVals : kPass1Vals;
         S.seg0 = seg;
         S.nseg = (int32_t)((n + kFinalizeThreads - 1) / kFinalizeThreads);
         // FP64 kernels: enough column splits for about 8 CTAs per SM in total
@@ -252,7 +252,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         x += n * d;
         row += S.npad;
         rec4 += (int64_t)nrec(d) * S.npad;
-        p1 += (int64_t)S.nblk * S.npad * kPass1Vals;
+        p1 += (int64_t)S.nblk * S.npad * (theta ? kPass1ThetaVals : kPass1Vals);
         p2 += (int64_t)S.nblk * S.npad * d;
         f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
         f2 += (int64_t)S.fsplit * S.npad * d;
@@ -503,8 +503,9 @@ hawkes_status enqueue_eval_reset(hawkes_ctx *ctx, const Plan &pl, cudaStream_t s
 
 // Pass 1 .. ell (and pass 2 .. gradient) on packed rows.
 hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
-                           double *out_grad, double *g_sorted, cudaStream_t s)
+                           double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr)
 {
+    const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
     const int32_t ns = (int32_t)pl.sets.size();
     const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
@@ -516,12 +517,16 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     else
         ctx->launches_own += want_grad ? 2 * ndims + 4 : ndims + 2;
     if (fp64) {
-        HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, false, s), "FP64 rate pass");
-        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, false, s), "finalize rows");
-        HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, s), "log-likelihood");
+        HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
+        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, theta, s), "finalize rows");
+        HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, false, s), "log-likelihood");
         if (want_grad) {
             HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
             HK_TRY(launch_finalize_grad(w, pl.total_segs, true, out_grad, g_sorted, s), "finalize gradient");
+        }
+        if (theta) {
+            ++ctx->launches_own;
+            HK_TRY(launch_theta_grad(w, out_grad_params, s), "parameter gradient");
         }
         return HAWKES_OK;
     }
@@ -530,16 +535,23 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         if (rg.second == 0)
             continue;
         const int warps = pl.warps_by_d[d];
-        const int grid = persistent_grid(ctx, d, 1, warps, rg.second);
+        const int grid = persistent_grid(ctx, d, theta ? 3 : 1, warps, rg.second);
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 0, pl.pairs);
-        HK_TRY(launch_pass1_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
+        if (theta)
+            HK_TRY(launch_pass1_theta_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
+        else
+            HK_TRY(launch_pass1_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
-    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, false, s), "finalize rows");
-    HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, s), "FP64 rate fixup");
+    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, theta, s), "finalize rows");
+    HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, theta, s), "FP64 rate fixup");
+    if (theta) {
+        ++ctx->launches_own;
+        HK_TRY(launch_theta_grad(w, out_grad_params, s), "parameter gradient");
+    }
     if (!want_grad)
         return HAWKES_OK;
     for (int d = 1; d <= kMaxD; ++d) {
@@ -652,6 +664,9 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
         for (int pass = 1; pass <= 2; ++pass)
             for (int wv : {1, 2, 4, 8})
                 ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
+    for (int d = 1; d <= kMaxD; ++d)
+        for (int wv : {1, 2, 4, 8})
+            ctx->occ[d][3][wv] = pass_max_ctas_per_sm(d, 3, wv);
     Plan pl;
     hawkes_params p{1, 1, 1, 1, 1, 1};
     const int64_t n64 = max_n;
@@ -806,21 +821,23 @@ static hawkes_status loglik_common(hawkes_ctx *ctx, const double *t, const doubl
         return st;
     if (!out_loglik || (grad && !out_grad_X))
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "output pointers must be device pointers");
-    if (out_grad_params)
-        return fail(ctx, HAWKES_ERR_INVALID_ARG, "the parameter gradient is not available in this build");
     HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = prec == HAWKES_PREC_FP64;
     Plan pl;
-    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64)) != HAWKES_OK)
+    const bool theta = grad && out_grad_params != nullptr;
+    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64, theta)) != HAWKES_OK)
         return st;
     if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
         return st;
     if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
         return st;
-    if ((st = enqueue_eval(ctx, pl, fp64, grad, out_loglik, grad ? out_grad_X : nullptr, nullptr, s)) != HAWKES_OK)
+    if ((st = enqueue_eval(ctx, pl, fp64, grad, out_loglik, grad ? out_grad_X : nullptr, nullptr, s,
+                           theta ? out_grad_params : nullptr)) != HAWKES_OK)
         return st;
-    return enqueue_nan_on_invalid(ctx, out_loglik, 1, grad ? out_grad_X : nullptr, n * d, s);
+    if ((st = enqueue_nan_on_invalid(ctx, out_loglik, 1, grad ? out_grad_X : nullptr, n * d, s)) != HAWKES_OK)
+        return st;
+    return theta ? enqueue_nan_on_invalid(ctx, out_grad_params, 6, nullptr, 0, s) : HAWKES_OK;
 }
 
 hawkes_status hawkes_loglik(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,

@@ -119,6 +119,25 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             } else {
                 lam = acc.value();
             }
+        } else if (theta) {
+            double v[kPass1ThetaVals] = {0, 0, 0, 0, 0, 0};
+            const float *P = w.P1 + S.part0 + i;
+            for (int slot = 0; slot < S.nblk; ++slot)
+                for (int q = 0; q < kPass1ThetaVals; ++q)
+                    v[q] += (double)P[((int64_t)slot * kPass1ThetaVals + q) * S.npad];
+            const double sum = v[0] + v[1];
+            flagged = !(sum >= S.s_min);
+            lam = S.Pmu * sum;
+            w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
+            // natural units: sum mu, sum xi, sum mu r^2, sum mu dt^2, sum xi dt, sum xi r^2
+            const double ikx2 = 1.0 / (S.kx * S.kx), ikt = 1.0 / S.kt;
+            double *T = w.theta_rows + r * kPass1ThetaVals;
+            T[0] = S.Pmu * v[0];
+            T[1] = S.Pmu * v[1];
+            T[2] = S.Pmu * v[2] * ikx2;
+            T[3] = S.Pmu * v[3] * ikt * ikt;
+            T[4] = S.Pmu * v[4] * ikt;
+            T[5] = S.Pmu * v[5] * ikx2;
         } else {
             double sum = 0.0;
             const float *P = w.P1 + S.part0 + i;
@@ -184,9 +203,41 @@ __device__ double rate_fp64(const Work &w, const SetDesc &S, int i, double *sh)
     return block_sum(acc.value(), sh);
 }
 
+// The six parameter-gradient row sums of one row in FP64 (natural units).
+__device__ void theta_sums_fp64(const Work &w, const SetDesc &S, int i, double *sh, double *out6)
+{
+    const PairFp64 k(S);
+    const int64_t R0 = S.row0;
+    const double tn = w.t64[R0 + i];
+    Nsum acc[kPass1ThetaVals];
+    for (int m = threadIdx.x; m < S.n; m += kT) {
+        const double tm = w.t64[R0 + m];
+        if (tm == tn)
+            continue;
+        double r2 = 0.0;
+        for (int q = 0; q < S.d; ++q) {
+            const double df = w.x64[(R0 + i) * kMaxD + q] - w.x64[(R0 + m) * kMaxD + q];
+            r2 += df * df;
+        }
+        const double dt = tn - tm;
+        const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+        acc[0].add(mu);
+        acc[2].add(mu * r2);
+        acc[3].add(mu * dt * dt);
+        if (tm < tn) {
+            const double xi = k.Cxi * exp(-(k.omega * dt + r2 * k.c));
+            acc[1].add(xi);
+            acc[4].add(xi * dt);
+            acc[5].add(xi * r2);
+        }
+    }
+    for (int q = 0; q < kPass1ThetaVals; ++q)
+        out6[q] = block_sum(acc[q].value(), sh);
+}
+
 // Flagged rows get their rate in FP64; the last CTA to finish writes ell of
 // every set: the segments' sums in order, then the flagged rows in order.
-__global__ void __launch_bounds__(kT) fixup_rows_kernel(Work w, int total_segs, double *out_loglik)
+__global__ void __launch_bounds__(kT) fixup_rows_kernel(Work w, int total_segs, double *out_loglik, int theta)
 {
     __shared__ double sh[kT];
     __shared__ int s_last;
@@ -202,6 +253,13 @@ __global__ void __launch_bounds__(kT) fixup_rows_kernel(Work w, int total_segs, 
                 const SetDesc &S = w.sets[s];
                 const int i = w.seg_rows[(int64_t)g * kT + k2];
                 const double lam = rate_fp64(w, S, i, sh);
+                if (theta) {
+                    double v6[kPass1ThetaVals];
+                    theta_sums_fp64(w, S, i, sh, v6);
+                    if (threadIdx.x == 0)
+                        for (int q = 0; q < kPass1ThetaVals; ++q)
+                            w.theta_rows[(S.row0 + i) * kPass1ThetaVals + q] = v6[q];
+                }
                 if (threadIdx.x == 0) {
                     const int64_t r = S.row0 + i;
                     w.lam64[r] = lam;
@@ -380,6 +438,42 @@ __global__ void __launch_bounds__(kT) fixup_grad_kernel(Work w, int total_segs, 
     }
 }
 
+// d ell / d Theta of set 0 (Theta order mu0, tau_x, tau_t, theta, omega, h):
+// per row, the rate-term sums divided by lambda_n plus the derivative of
+// -Lambda_n; summed over rows in a fixed order.
+__global__ void __launch_bounds__(kT) theta_grad_kernel(Work w, double *out6)
+{
+    __shared__ double sh[kT];
+    const SetDesc &S = w.sets[0];
+    const double D = (double)S.d;
+    const double tx = S.tau_x, tt = S.tau_t, h = S.h, om = S.omega, th = S.theta, mu0 = S.mu0;
+    const double T = w.t64[S.row0 + S.n - 1];
+    const double inv_sqrt_2pi = 0.39894228040143267793994605993438;
+    Nsum acc[6];
+    for (int i = threadIdx.x; i < S.n; i += kT) {
+        const int64_t r = S.row0 + i;
+        const double *A = w.theta_rows + r * kPass1ThetaVals;
+        const double lam = w.lam64[r];
+        const double tn = w.t64[r];
+        const double a = T - tn;
+        const double ea = exp(-om * a);
+        acc[0].add(A[0] / (mu0 * lam) - (normcdf(a / tt) - normcdf(-tn / tt)));
+        acc[1].add((A[2] / (tx * tx * tx) - D * A[0] / tx) / lam);
+        acc[2].add((A[3] / (tt * tt * tt) - A[0] / tt) / lam +
+                   mu0 * inv_sqrt_2pi * (exp(-0.5 * (a / tt) * (a / tt)) * a + exp(-0.5 * (tn / tt) * (tn / tt)) * tn) /
+                       (tt * tt));
+        acc[3].add(A[1] / (th * lam) + expm1(-om * a));
+        acc[4].add((A[1] / om - A[4]) / lam - th * a * ea);
+        acc[5].add((A[5] / (h * h * h) - D * A[1] / h) / lam);
+    }
+    const bool zero_rate = (w.set_flags[0] & 1) != 0;
+    for (int q = 0; q < 6; ++q) {
+        const double v = block_sum(acc[q].value(), sh);
+        if (threadIdx.x == 0)
+            out6[q] = zero_rate ? nan("") : v;
+    }
+}
+
 __global__ void fill_nan_kernel(double *p, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -394,9 +488,10 @@ cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, b
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, cudaStream_t s)
+cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
+                              cudaStream_t s)
 {
-    fixup_rows_kernel<<<grid, kT, 0, s>>>(w, total_segs, out_loglik);
+    fixup_rows_kernel<<<grid, kT, 0, s>>>(w, total_segs, out_loglik, theta ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -411,6 +506,12 @@ cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, d
                               cudaStream_t s)
 {
     fixup_grad_kernel<<<grid, kT, 0, s>>>(w, total_segs, out_grad, g_sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta_grad(const Work &w, double *out6, cudaStream_t s)
+{
+    theta_grad_kernel<<<1, kT, 0, s>>>(w, out6);
     return cudaGetLastError();
 }
 

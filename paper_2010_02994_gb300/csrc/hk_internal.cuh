@@ -123,8 +123,11 @@ cudaError_t launch_pack_x_rows(const Work &w, int64_t total_rows, const int64_t 
 // hk_pairs_mixed_*.cu
 cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s);
+cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+                                     int warps, cudaStream_t s);
 cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s);
+// pass: 1 rates, 2 gradient, 3 rates with Theta sums
 size_t pass_smem_bytes(int d, int pass, int warps);
 int pass_max_ctas_per_sm(int d, int pass, int warps);
 
@@ -137,7 +140,9 @@ cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int
 
 // hk_finalize.cu
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s);
-cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, cudaStream_t s);
+cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
+                              cudaStream_t s);
+cudaError_t launch_theta_grad(const Work &w, double *out6, cudaStream_t s);
 cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
                                  cudaStream_t s);
 cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,

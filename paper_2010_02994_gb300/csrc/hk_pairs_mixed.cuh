@@ -255,6 +255,211 @@ __global__ void __launch_bounds__(256) pass1_mixed_kernel(Work w, const WorkItem
     }
 }
 
+// ------------------------------------------------ pass 1 with Theta sums --
+// Besides the rate, every row collects the sums the parameter gradient needs
+// (scaled units; the finalize kernel converts them): for the earlier event of
+// a pair mu', mu' q, mu' dt^2; for the later one also xi'', xi'' dt, xi'' q.
+// Partial planes per slot: 0 mu', 1 xi'', 2 mu' q, 3 mu' dt^2, 4 xi'' dt, 5 xi'' q.
+
+template <int D, bool MASKED>
+__device__ __forceinline__ void pass1_theta_chunk(const float4 *__restrict__ scol, int B, int c0, int lane, int m0,
+                                                  const float (&rx)[rows_per_lane(D)][2 * D],
+                                                  const float (&rt)[rows_per_lane(D)],
+                                                  const int (&rte)[rows_per_lane(D)], const PairConsts<D> &k,
+                                                  float (&part)[rows_per_lane(D)][3], float (&acc)[6])
+{
+    constexpr int R = rows_per_lane(D);
+#pragma unroll 2
+    for (int j = 0; j < 32; ++j) {
+        const int cc = (lane + j) & 31;
+        float cf[4 * nrec(D)];
+        load_rec<D>(scol, B, c0 + cc, cf);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float q;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float dx = (cf[2 * d] - rx[r][2 * d]) + (cf[2 * d + 1] - rx[r][2 * d + 1]);
+                q = d == 0 ? dx * dx : fmaf(dx, dx, q);
+            }
+            const float dt = cf[2 * D] - rt[r];
+            const float dt2 = dt * dt;
+            float mu = ex2_approx(-q - dt2);
+            float xi = ex2_approx(fmaf(-k.rho, q, fmaf(-k.kappa, dt, k.cxi)));
+            if (MASKED) {
+                const bool valid = m0 + cc >= rte[r];
+                mu = valid ? mu : 0.0f;
+                xi = valid ? xi : 0.0f;
+            }
+            part[r][0] += mu;
+            part[r][1] = fmaf(mu, q, part[r][1]);
+            part[r][2] = fmaf(mu, dt2, part[r][2]);
+            acc[0] += mu;
+            acc[1] += xi;
+            acc[2] = fmaf(mu, q, acc[2]);
+            acc[3] = fmaf(mu, dt2, acc[3]);
+            acc[4] = fmaf(xi, dt, acc[4]);
+            acc[5] = fmaf(xi, q, acc[5]);
+        }
+#pragma unroll
+        for (int v = 0; v < 6; ++v)
+            acc[v] = __shfl_sync(0xffffffffu, acc[v], (lane + 1) & 31);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) pass1_theta_kernel(Work w, const WorkItem *__restrict__ items, int nitems)
+{
+    constexpr int R = rows_per_lane(D);
+    constexpr int NP = nrec(D);
+    constexpr int V = kPass1ThetaVals;
+    constexpr int row_plane[3] = {0, 2, 3};
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int B = 32 * R * warps;
+    extern __shared__ float4 smem4[];
+    float4 *scol = smem4;
+    const size_t scol_floats = (size_t)(NP * 4 > V ? NP * 4 : V) * B;
+    float *colpart = reinterpret_cast<float *>(smem4) + scol_floats;  // [warps][V][B]
+    __shared__ int s_item;
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(&w.counters[0], 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems)
+            break;
+        const WorkItem wi = items[it];
+        const SetDesc &S = w.sets[wi.set];
+        const int I = wi.I, J = wi.J, n = S.n, npad = S.npad;
+        const float4 *rec = w.rec + S.rec0;
+        PairConsts<D> kc{S.rho, S.kappa, S.cxi1};
+        float oh, ol;
+        {
+            const int io = min(I * B + B / 2, n - 1);
+            const float4 v = rec[(int64_t)((2 * D) / 4) * npad + io];
+            const float *c = reinterpret_cast<const float *>(&v);
+            oh = c[(2 * D) % 4];
+            ol = c[(2 * D) % 4 + 1];
+        }
+        for (int c = threadIdx.x; c < B; c += blockDim.x) {
+            float f[4 * NP];
+            load_rec<D>(rec, npad, (int64_t)J * B + c, f);
+            f[2 * D] = (f[2 * D] - oh) + (f[2 * D + 1] - ol);
+            f[2 * D + 1] = 0.0f;
+            store_rec<D>(scol, B, c, f);
+        }
+        float rx[R][2 * D], rt[R], part[R][3], rs[R][3], rc[R][3];
+        int rte[R];
+        const int rbase = I * B + warp * 32 * R;
+        int te_min = 0x7fffffff, te_max = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = rbase + 32 * r + lane;
+            float f[4 * NP];
+            load_rec<D>(rec, npad, row, f);
+#pragma unroll
+            for (int q = 0; q < 2 * D; ++q)
+                rx[r][q] = f[q];
+            rt[r] = (f[2 * D] - oh) + (f[2 * D + 1] - ol);
+            rte[r] = w.tie_end[S.row0 + row];
+            te_min = min(te_min, rte[r]);
+            te_max = max(te_max, rte[r]);
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                rs[r][v] = 0.0f;
+                rc[r][v] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            te_min = min(te_min, __shfl_xor_sync(0xffffffffu, te_min, o));
+            te_max = max(te_max, __shfl_xor_sync(0xffffffffu, te_max, o));
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < B; c0 += 32) {
+            const int m0 = J * B + c0;
+            float *cp = colpart + (warp * V) * B + c0;
+            if (m0 + 32 <= te_min) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    cp[v * B + lane] = 0.0f;
+                continue;
+            }
+            float acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                acc[v] = 0.0f;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int v = 0; v < 3; ++v)
+                    part[r][v] = 0.0f;
+            if (m0 < te_max)
+                pass1_theta_chunk<D, true>(scol, B, c0, lane, m0, rx, rt, rte, kc, part, acc);
+            else
+                pass1_theta_chunk<D, false>(scol, B, c0, lane, m0, rx, rt, rte, kc, part, acc);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                cp[v * B + lane] = acc[v];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float y = part[r][v] - rc[r][v];
+                    const float t = rs[r][v] + y;
+                    rc[r][v] = (t - rs[r][v]) - y;
+                    rs[r][v] = t;
+                }
+        }
+        __syncthreads();
+        float *P = w.P1 + S.part0;
+        float *rowbuf = reinterpret_cast<float *>(scol);  // [V][B]
+        for (int c = threadIdx.x; c < V * B; c += blockDim.x)
+            rowbuf[c] = 0.0f;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                rowbuf[row_plane[v] * B + warp * 32 * R + 32 * r + lane] = rs[r][v] - rc[r][v];
+        __syncthreads();
+        if (I != J) {
+            for (int c = threadIdx.x; c < B; c += blockDim.x) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    P[((int64_t)J * V + v) * npad + (int64_t)I * B + c] = rowbuf[v * B + c];
+                    float tot = 0.0f;
+                    for (int q = 0; q < warps; ++q)
+                        tot += colpart[(q * V + v) * B + c];
+                    P[((int64_t)I * V + v) * npad + (int64_t)J * B + c] = tot;
+                }
+            }
+        } else {
+            for (int c = threadIdx.x; c < B; c += blockDim.x) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    float tot = rowbuf[v * B + c];
+                    for (int q = 0; q < warps; ++q)
+                        tot += colpart[(q * V + v) * B + c];
+                    P[((int64_t)I * V + v) * npad + (int64_t)I * B + c] = tot;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(&w.counters[1], 1);
+        if (done == (int)gridDim.x - 1) {
+            w.counters[0] = 0;
+            w.counters[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
 // -------------------------------------------------------------- pass 2 --
 
 template <int D, bool MASKED>
@@ -455,11 +660,9 @@ size_t pass_smem_bytes_t(int pass, bool theta, int warps)
 {
     const int B = 32 * rows_per_lane(D) * warps;
     const int vals = pass == 1 ? (theta ? kPass1ThetaVals : 1) : D;
-    size_t scol = (size_t)nrec(D) * B * sizeof(float4);
-    size_t rowbuf = (size_t)vals * B * sizeof(float);
-    if (rowbuf > scol)
-        scol = rowbuf;
-    return scol + (size_t)warps * vals * B * sizeof(float);
+    // staged columns (reused as the row buffer at the end of a block)
+    const size_t scol_floats = (size_t)(nrec(D) * 4 > vals ? nrec(D) * 4 : vals) * B;
+    return (scol_floats + (size_t)warps * vals * B) * sizeof(float);
 }
 
 }  // namespace hk

@@ -15,6 +15,10 @@ extern template cudaError_t launch_pass2_t<1>(const Work &, const WorkItem *, in
 extern template cudaError_t launch_pass2_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
 extern template cudaError_t launch_pass2_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
 extern template cudaError_t launch_pass2_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_theta_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_theta_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_theta_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
+extern template cudaError_t launch_pass1_theta_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
 extern template int occupancy_t<1>(int, int);
 extern template int occupancy_t<2>(int, int);
 extern template int occupancy_t<3>(int, int);
@@ -44,6 +48,13 @@ cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int3
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+                                     int warps, cudaStream_t s)
+{
+    HK_SWITCH_D(d, launch_pass1_theta_t<D>(w, items, nitems, grid, warps, s))
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s)
 {
@@ -53,7 +64,7 @@ cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int3
 
 size_t pass_smem_bytes(int d, int pass, int warps)
 {
-    HK_SWITCH_D(d, pass_smem_bytes_t<D>(pass, false, warps))
+    HK_SWITCH_D(d, pass_smem_bytes_t<D>(pass == 3 ? 1 : pass, pass == 3, warps))
     return 0;
 }
 

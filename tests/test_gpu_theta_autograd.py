@@ -1,0 +1,109 @@
+"""Parameter gradient and the autograd wrapper against the FP64 oracle and
+against finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2010_02994_gb300 import HawkesContext
+
+    c = HawkesContext(device=0, max_n=20_000, max_d=8)
+    yield c
+    c.close()
+
+
+def gpu_all(ctx, w, prec):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik_grad_locations
+
+    t = torch.tensor(w.t, device="cuda")
+    X = torch.tensor(w.X, device="cuda")
+    ell, g, gp = hawkes_loglik_grad_locations(ctx, t, X, w.params, precision=prec, grad_params=True)
+    return ell.item(), g.cpu().numpy(), gp.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed,n,d,ties", [(1, 300, 2, 0), (2, 900, 3, 1), (3, 2000, 1, 0), (4, 700, 8, 0),
+                                           (5, 1500, 2, 2)])
+def test_parameter_gradient_matches_oracle(ctx, prec, seed, n, d, ties):
+    w = synth.random_case(seed, n, d, ties=ties, shuffle=True)
+    ell_ref, g_ref, lam = oracle.loglik_and_grad(w.t, w.X, w.params)
+    gp_ref = oracle.grad_params(w.t, w.X, w.params, lam)
+    ell, g, gp = gpu_all(ctx, w, prec)
+    theta = w.theta_vector()
+    # the score in log-parameter units per event, d ell / d log theta_k / N
+    err = np.max(np.abs(gp - gp_ref) * theta) / n
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert err <= tol, (gp, gp_ref, err)
+    scale = float(np.sum(np.abs(np.log(lam))) + oracle.Lambda(w.t, w.params))
+    assert abs(ell - ell_ref) <= (1e-12 if prec == "fp64" else 1e-6) * scale
+
+
+def test_parameter_gradient_wildfire_like(ctx):
+    w = synth.make_c3()
+    ell_ref, g_ref, lam = oracle.loglik_and_grad(w.t, w.X, w.params)
+    gp_ref = oracle.grad_params(w.t, w.X, w.params, lam)
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-6)):
+        _, _, gp = gpu_all(ctx, w, prec)
+        assert np.max(np.abs(gp - gp_ref) * w.theta_vector()) / w.n <= tol
+
+
+def test_autograd_gradcheck_fp64(ctx):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik_autograd
+
+    w = synth.random_case(9, 25, 2, shuffle=True)
+    t = torch.tensor(w.t, device="cuda")
+    X = torch.tensor(w.X, device="cuda", requires_grad=True)
+    th = torch.tensor(w.theta_vector(), device="cuda", requires_grad=True)
+    f = lambda X_, th_: hawkes_loglik_autograd(ctx, t, X_, th_, "fp64")
+    assert torch.autograd.gradcheck(f, (X, th), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
+def test_autograd_backward_matches_oracle(ctx):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik_autograd
+
+    w = synth.make_c3()
+    t = torch.tensor(w.t, device="cuda")
+    X = torch.tensor(w.X, device="cuda", requires_grad=True)
+    th = torch.tensor(w.theta_vector(), device="cuda", requires_grad=True)
+    ll = hawkes_loglik_autograd(ctx, t, X, th, "mixed")
+    (2.0 * ll).backward()
+    ell_ref, g_ref, lam = oracle.loglik_and_grad(w.t, w.X, w.params)
+    gp_ref = oracle.grad_params(w.t, w.X, w.params, lam)
+    gx = X.grad.cpu().numpy()
+    assert np.linalg.norm(gx - 2 * g_ref) <= 1e-5 * np.linalg.norm(2 * g_ref)
+    assert np.max(np.abs(th.grad.cpu().numpy() - 2 * gp_ref) * w.theta_vector()) / w.n <= 2e-6
+
+
+def test_location_gradient_against_finite_differences_of_gpu_loglik(ctx):
+    """The wildfire-shaped workload's location gradient against central
+    differences of the GPU FP64 log-likelihood on a few coordinates."""
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik
+
+    w = synth.make_c3()
+    _, g, _ = gpu_all(ctx, w, "fp64")
+    t = torch.tensor(w.t, device="cuda")
+    rng = np.random.default_rng(0)
+    for i in rng.choice(w.n, size=6, replace=False):
+        for k in range(w.d):
+            h = 1e-4 * w.params["h"]
+            vals = []
+            for sgn in (1, -1):
+                X = w.X.copy()
+                X[i, k] += sgn * h
+                vals.append(hawkes_loglik(ctx, t, torch.tensor(X, device="cuda"), w.params, precision="fp64").item())
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - g[i, k]) <= 1e-5 * max(1.0, abs(g[i, k]))
