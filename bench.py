@@ -30,20 +30,19 @@ if ROOT not in sys.path:
 METRIC = "loglik+location-gradient evals/s and pairs/s at N=1e5, mixed vs FP64 GPU"
 UNIT = "evals/s"
 MAX_SM_MHZ_NOMINAL = 2070.0  # GB300 maximum SM clock
-FP32_LANES_PER_SM = 128      # FP32 FMA-pipe lanes per SM per clock
-MUFU_PER_SM = 16             # MUFU (ex2) results per SM per clock
 CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 
 
-def pass_bound_cycles(d: int, which: str) -> float:
-    """SM cycles per unordered pair: max(FMA ops / 128, ex2 / 16) with the
-    algorithmic counts of each pass (no hi/lo overhead)."""
+def pass_bound_cycles(d: int, which: str, fma_rate: float, ex2_rate: float) -> float:
+    """SM cycles per unordered pair: max(FP32 ops / FMA rate, ex2 / MUFU rate),
+    with the algorithmic counts of each pass (2D+9 and 4D+10 FP32 ops, two
+    ex2 each; no hi/lo overhead) and the measured per-SM rates."""
     f1, f2, e1, e2 = 2 * d + 9, 4 * d + 10, 2, 2
     if which == "pass1":
-        return max(f1 / FP32_LANES_PER_SM, e1 / MUFU_PER_SM)
+        return max(f1 / fma_rate, e1 / ex2_rate)
     if which == "pass2":
-        return max(f2 / FP32_LANES_PER_SM, e2 / MUFU_PER_SM)
-    return max((f1 + f2) / FP32_LANES_PER_SM, (e1 + e2) / MUFU_PER_SM)
+        return max(f2 / fma_rate, e2 / ex2_rate)
+    return max((f1 + f2) / fma_rate, (e1 + e2) / ex2_rate)
 
 
 class ClockSampler:
@@ -211,7 +210,7 @@ def main():
     import torch
 
     import synth
-    from paper_2010_02994_gb300 import HawkesContext, hawkes_loglik_grad_locations
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_loglik_grad_locations, probe_pipe_rates
 
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
@@ -235,6 +234,10 @@ def main():
 
     def step(prec):
         hawkes_loglik_grad_locations(ctx, t, X, w.params, precision=prec, check=False, out=(ell, g, None))
+
+    rates = probe_pipe_rates(local)
+    fma_rate = 128.0 if not rates["fma_per_sm_clk"] > 0 else rates["fma_per_sm_clk"]
+    ex2_rate = 16.0 if not rates["ex2_per_sm_clk"] > 0 else rates["ex2_per_sm_clk"]
 
     # --- device-resident timing (mixed path) ---------------------------------
     for _ in range(args.warmup):
@@ -280,14 +283,15 @@ def main():
 
     def roof(stat, which):
         achieved = stat["pairs"] / (stat["ms"] * 1e-3) / 1e9
-        peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, which) / 1e9
+        peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, which, fma_rate, ex2_rate) / 1e9
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
                 "traffic": None, "ms_per_launch": stat["ms"] / max(1, stat["launches"]),
-                "peak_basis": f"{sms} SMs x {MAX_SM_MHZ_NOMINAL:.0f} MHz / max(FMA/128, ex2/16) cycles per pair"}
+                "peak_basis": (f"{sms} SMs x {MAX_SM_MHZ_NOMINAL:.0f} MHz / max(FP32 ops/{fma_rate:.1f}, "
+                               f"ex2/{ex2_rate:.1f}) cycles per unordered pair (measured per-SM rates)")}
 
     r1, r2 = roof(k1, "pass1"), roof(k2, "pass2")
     dominant = ("pass2_gradient", r2) if k2["ms"] >= k1["ms"] else ("pass1_rates", r1)
-    eval_peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, "both") / pairs
+    eval_peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, "both", fma_rate, ex2_rate) / pairs
 
     # --- FP64 GPU path on the same inputs ------------------------------------
     fp64 = None
@@ -372,6 +376,7 @@ def main():
         "gpu_launches_per_step": per_step_launches,
         "library_sort_launches": int(launches["library"]),
         "sm_count": sms,
+        "pipe_rates": rates,
         "wall_s": wall,
     }
     if rank == 0:

@@ -194,6 +194,16 @@ hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const in
                                        const hawkes_params *params, hawkes_precision prec,
                                        hawkes_stream stream, double *out_loglik, double *out_grad_X);
 
+/* ------------------------------------------------------------ probing -- */
+
+/* Measure, on `device`, how many FP32 fused multiply-adds and how many MUFU
+ * ex2 (ex2.approx.ftz.f32) results one SM completes per clock, and the SM
+ * clock during the measurement (MHz).  The pair kernels are bound by these
+ * two pipes; the benchmark derives their roofline from this measurement.
+ * Runs two short kernels and synchronizes the device. */
+hawkes_status hawkes_probe_pipe_rates(int32_t device, double *fma_per_sm_clk, double *ex2_per_sm_clk,
+                                      double *sm_clock_mhz);
+
 /* Library version, e.g. "hawkes 0.1.0 sm_103a". */
 const char *hawkes_version(void);
 

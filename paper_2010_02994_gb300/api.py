@@ -200,5 +200,15 @@ def hawkes_batch_loglik_grad(ctx: HawkesContext, sizes, dims, t, X, params_list,
     return ell, g
 
 
+def probe_pipe_rates(device: int = 0) -> dict:
+    """Measured FP32 FMA and MUFU ex2 results per SM per clock (and the SM clock)."""
+    lib = _lib.load()
+    f, e, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib.hawkes_probe_pipe_rates(int(device), ctypes.byref(f), ctypes.byref(e), ctypes.byref(mhz))
+    if st != _lib.HAWKES_OK:
+        raise HawkesError(st, "pipe-rate probe failed")
+    return {"fma_per_sm_clk": f.value, "ex2_per_sm_clk": e.value, "sm_mhz": mhz.value}
+
+
 def version() -> str:
     return _lib.load().hawkes_version().decode()

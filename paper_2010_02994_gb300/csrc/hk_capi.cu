@@ -189,6 +189,7 @@ void describe_set(SetDesc &S, int64_t n, int d, const hawkes_params &p, double f
     S.kappa = (float)(p.omega * kLog2e / S.kt);
     S.cxi1 = (float)cxi1;
     S.cxi2 = (float)(cxi1 + std::log2(rho));
+    S.cxi2_d = cxi1 + std::log2(rho);
     S.s_min = std::ldexp(1.0, (int)fixup_exp);
 }
 
@@ -307,6 +308,7 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
     c.take<int64_t>(ns + 1);
     c.take<float4>(pl.total_rec4);
     c.take<float>(pl.total_rows);
+    c.take<float>(pl.total_rows);
     c.take<int32_t>(pl.total_rows);
     c.take<int32_t>(pl.total_rows);
     for (int k = 0; k < 5; ++k)
@@ -377,6 +379,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     w.nsets = (int32_t)ns;
     w.rec = c.take<float4>(pl.total_rec4);
     w.w32 = c.take<float>(pl.total_rows);
+    w.cm32 = c.take<float>(pl.total_rows);
     w.tie_end = c.take<int32_t>(pl.total_rows);
     w.perm = c.take<int32_t>(pl.total_rows);
     w.t64 = c.take<double>(pl.total_rows);

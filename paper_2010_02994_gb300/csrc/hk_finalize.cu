@@ -67,6 +67,26 @@ __device__ double block_sum(double v, double *sh)
     return r;
 }
 
+// sum_{k < count} (double)p[k * stride], added in order k = 0, 1, ...; the
+// loads of eight consecutive terms are issued before they are added.
+__device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ p, int count, int64_t stride)
+{
+    double acc = 0.0;
+    int k = 0;
+    for (; k + 8 <= count; k += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = p[(int64_t)(k + u) * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            acc += (double)v[u];
+    }
+    for (; k < count; ++k)
+        acc += (double)p[(int64_t)k * stride];
+    return acc;
+}
+
 struct PairFp64 {
     double a, b, c, Cmu, Cxi, omega, itx2, ih2;
     __device__ explicit PairFp64(const SetDesc &S)
@@ -120,15 +140,15 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
                 lam = acc.value();
             }
         } else if (theta) {
-            double v[kPass1ThetaVals] = {0, 0, 0, 0, 0, 0};
-            const float *P = w.P1 + S.part0 + i;
-            for (int slot = 0; slot < S.nblk; ++slot)
-                for (int q = 0; q < kPass1ThetaVals; ++q)
-                    v[q] += (double)P[((int64_t)slot * kPass1ThetaVals + q) * S.npad];
+            double v[kPass1ThetaVals];
+            for (int q = 0; q < kPass1ThetaVals; ++q)
+                v[q] = ordered_strided_sum(w.P1 + S.part0 + (int64_t)q * S.npad + i, S.nblk,
+                                           (int64_t)kPass1ThetaVals * S.npad);
             const double sum = v[0] + v[1];
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
             w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
+            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log2(sum));
             // natural units: sum mu, sum xi, sum mu r^2, sum mu dt^2, sum xi dt, sum xi r^2
             const double ikx2 = 1.0 / (S.kx * S.kx), ikt = 1.0 / S.kt;
             double *T = w.theta_rows + r * kPass1ThetaVals;
@@ -139,13 +159,11 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             T[4] = S.Pmu * v[4] * ikt;
             T[5] = S.Pmu * v[5] * ikx2;
         } else {
-            double sum = 0.0;
-            const float *P = w.P1 + S.part0 + i;
-            for (int slot = 0; slot < S.nblk; ++slot)
-                sum += (double)P[(int64_t)slot * S.npad];
+            const double sum = ordered_strided_sum(w.P1 + S.part0 + i, S.nblk, S.npad);
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
             w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
+            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log2(sum));
         }
         if (!flagged) {
             w.lam64[r] = lam;
@@ -331,13 +349,9 @@ __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, dou
             atomicOr(w.status, kStZeroRate);
         if (w.w32[r] == 0.0f)
             return;  // a flagged row: fixup_grad_kernel writes its gradient
-        for (int q = 0; q < d; ++q) {
-            double acc = 0.0;
-            const float *P = w.P2 + S.part2_0 + (int64_t)q * S.npad + i;
-            for (int slot = 0; slot < S.nblk; ++slot)
-                acc += (double)P[(int64_t)slot * d * S.npad];
-            gv[q] = S.Cg * acc;
-        }
+        for (int q = 0; q < d; ++q)
+            gv[q] = S.Cg * ordered_strided_sum(w.P2 + S.part2_0 + (int64_t)q * S.npad + i, S.nblk,
+                                               (int64_t)d * S.npad);
         if (w.counters[2] > 0) {
             // contributions through the flagged rows' own rates:
             // w_n [mu_nm / tau_x^2 + xi_nm / h^2] (x_n - x_m), xi_nm when t_m < t_n

@@ -9,6 +9,8 @@
 //         th, tl: the FP32 hi/lo split of the scaled coordinate kx*x_k and
 //         of the scaled time kt*t (nrec(D) planes, unused fields zero).
 //   w32   FP32 1/S_n for the gradient pass (0 for rows recomputed in FP64).
+//   cm32  FP32 c_xi1 + log2(rho) + log2(w_n), the gradient pass's per-column
+//         self-excitation exponent constant (-inf where w_n = 0).
 //   tie_end  first set-relative row whose time exceeds this row's time.
 //   perm  set-relative caller index of each row.
 //   t64, x64  FP64 sorted times and coordinates (x64 row stride kMaxD).
@@ -27,7 +29,7 @@
 namespace hk {
 
 constexpr int kMaxD = 8;
-constexpr float kPadTime = 1.0e30f;
+constexpr float kPadTime = 1.0e18f;  // its square stays finite in FP32
 constexpr int kPass1Vals = 1;       // S
 constexpr int kPass1ThetaVals = 6;  // M, Xi, sum mu' q, sum mu' dt^2, sum xi'' dt, sum xi'' q
 constexpr int kFinalizeThreads = 256;
@@ -62,6 +64,7 @@ struct SetDesc {
     int32_t pad_;
     // mixed-path exponent constants (base 2; see the pass kernels)
     float rho, kappa, cxi1, cxi2;
+    double cxi2_d;    // c_xi1 + log2(rho) in FP64
     // FP64 constants
     double kx, kt;    // coordinate scalings sqrt(log2(e)/2)/tau_x and /tau_t
     double Pmu;       // mu0 / (tau_x^D tau_t (2 pi)^((D+1)/2))
@@ -80,6 +83,7 @@ struct Work {
     int32_t nsets;
     float4 *rec;
     float *w32;
+    float *cm32;
     int32_t *tie_end;
     int32_t *perm;
     double *t64;

@@ -7,26 +7,15 @@ HK_INSTANTIATE_MIXED(6)
 HK_INSTANTIATE_MIXED(7)
 HK_INSTANTIATE_MIXED(8)
 
-extern template cudaError_t launch_pass1_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass2_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass2_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass2_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass2_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_theta_t<1>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_theta_t<2>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_theta_t<3>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template cudaError_t launch_pass1_theta_t<4>(const Work &, const WorkItem *, int, int, int, cudaStream_t);
-extern template int occupancy_t<1>(int, int);
-extern template int occupancy_t<2>(int, int);
-extern template int occupancy_t<3>(int, int);
-extern template int occupancy_t<4>(int, int);
-extern template size_t pass_smem_bytes_t<1>(int, bool, int);
-extern template size_t pass_smem_bytes_t<2>(int, bool, int);
-extern template size_t pass_smem_bytes_t<3>(int, bool, int);
-extern template size_t pass_smem_bytes_t<4>(int, bool, int);
+#define HK_EXTERN_MIXED(D)                                                                                      \
+    extern template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int,           \
+                                                 cudaStream_t);                                                \
+    extern template size_t smem_t<D>(int, int);                                                                 \
+    extern template int occupancy_t<D>(int, int);
+HK_EXTERN_MIXED(1)
+HK_EXTERN_MIXED(2)
+HK_EXTERN_MIXED(3)
+HK_EXTERN_MIXED(4)
 
 #define HK_SWITCH_D(d, EXPR)                                                                                   \
     switch (d) {                                                                                               \
@@ -44,27 +33,27 @@ extern template size_t pass_smem_bytes_t<4>(int, bool, int);
 cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s)
 {
-    HK_SWITCH_D(d, launch_pass1_t<D>(w, items, nitems, grid, warps, s))
+    HK_SWITCH_D(d, launch_pass_t<D>(1, w, items, nitems, grid, warps, s))
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
                                      int warps, cudaStream_t s)
 {
-    HK_SWITCH_D(d, launch_pass1_theta_t<D>(w, items, nitems, grid, warps, s))
+    HK_SWITCH_D(d, launch_pass_t<D>(3, w, items, nitems, grid, warps, s))
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s)
 {
-    HK_SWITCH_D(d, launch_pass2_t<D>(w, items, nitems, grid, warps, s))
+    HK_SWITCH_D(d, launch_pass_t<D>(2, w, items, nitems, grid, warps, s))
     return cudaErrorInvalidValue;
 }
 
 size_t pass_smem_bytes(int d, int pass, int warps)
 {
-    HK_SWITCH_D(d, pass_smem_bytes_t<D>(pass == 3 ? 1 : pass, pass == 3, warps))
+    HK_SWITCH_D(d, smem_t<D>(pass, warps))
     return 0;
 }
 

@@ -1,65 +1,70 @@
 // Launch helpers of the mixed pair kernels, instantiated per dimension by
 // hk_pairs_mixed_lo.cu (D = 1..4) and hk_pairs_mixed_hi.cu (D = 5..8).
+// pass: 1 rates, 2 gradient, 3 rates with Theta sums.
 #pragma once
 
 #include "hk_pairs_mixed.cuh"
 
 namespace hk {
 
-template <int D>
-cudaError_t launch_pass1_t(const Work &w, const WorkItem *items, int nitems, int grid, int warps, cudaStream_t s)
+template <int KIND, int D>
+cudaError_t launch_kind_t(const Work &w, const WorkItem *items, int nitems, int grid, int warps, cudaStream_t s)
 {
-    const size_t smem = pass_smem_bytes_t<D>(1, false, warps);
-    pass1_mixed_kernel<D><<<grid, warps * 32, smem, s>>>(w, items, nitems);
+    constexpr int R = rows_per_lane(D);
+    const size_t smem = pair_smem_bytes<KIND, D, R>(warps);
+    pair_kernel<KIND, D, R><<<grid, warps * 32, smem, s>>>(w, items, nitems);
     return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_pass1_theta_t(const Work &w, const WorkItem *items, int nitems, int grid, int warps,
-                                 cudaStream_t s)
+cudaError_t launch_pass_t(int pass, const Work &w, const WorkItem *items, int nitems, int grid, int warps,
+                          cudaStream_t s)
 {
-    const size_t smem = pass_smem_bytes_t<D>(1, true, warps);
-    pass1_theta_kernel<D><<<grid, warps * 32, smem, s>>>(w, items, nitems);
-    return cudaGetLastError();
+    if (pass == 1)
+        return launch_kind_t<kRate, D>(w, items, nitems, grid, warps, s);
+    if (pass == 2)
+        return launch_kind_t<kGrad, D>(w, items, nitems, grid, warps, s);
+    return launch_kind_t<kRateTheta, D>(w, items, nitems, grid, warps, s);
 }
 
 template <int D>
-cudaError_t launch_pass2_t(const Work &w, const WorkItem *items, int nitems, int grid, int warps, cudaStream_t s)
+size_t smem_t(int pass, int warps)
 {
-    const size_t smem = pass_smem_bytes_t<D>(2, false, warps);
-    pass2_mixed_kernel<D><<<grid, warps * 32, smem, s>>>(w, items, nitems);
-    return cudaGetLastError();
+    constexpr int R = rows_per_lane(D);
+    if (pass == 1)
+        return pair_smem_bytes<kRate, D, R>(warps);
+    if (pass == 2)
+        return pair_smem_bytes<kGrad, D, R>(warps);
+    return pair_smem_bytes<kRateTheta, D, R>(warps);
+}
+
+template <int KIND, int D>
+int occupancy_kind(int warps)
+{
+    constexpr int R = rows_per_lane(D);
+    const size_t smem = pair_smem_bytes<KIND, D, R>(warps);
+    const size_t smem_max = pair_smem_bytes<KIND, D, R>(8);
+    cudaFuncSetAttribute(pair_kernel<KIND, D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<KIND, D, R>, warps * 32, smem);
+    return nb;
 }
 
 // Allow the largest dynamic shared memory any warp count needs, and return
 // how many CTAs of `warps` warps fit on one SM.
-// pass: 1 rates, 2 gradient, 3 rates with Theta sums.
 template <int D>
 int occupancy_t(int pass, int warps)
 {
-    const bool theta = pass == 3;
-    const int p = theta ? 1 : pass;
-    const size_t smem = pass_smem_bytes_t<D>(p, theta, warps);
-    const size_t smem_max = pass_smem_bytes_t<D>(p, theta, 8);
-    int nb = 0;
-    if (theta) {
-        cudaFuncSetAttribute(pass1_theta_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass1_theta_kernel<D>, warps * 32, smem);
-    } else if (pass == 1) {
-        cudaFuncSetAttribute(pass1_mixed_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass1_mixed_kernel<D>, warps * 32, smem);
-    } else {
-        cudaFuncSetAttribute(pass2_mixed_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass2_mixed_kernel<D>, warps * 32, smem);
-    }
-    return nb;
+    if (pass == 1)
+        return occupancy_kind<kRate, D>(warps);
+    if (pass == 2)
+        return occupancy_kind<kGrad, D>(warps);
+    return occupancy_kind<kRateTheta, D>(warps);
 }
 
-#define HK_INSTANTIATE_MIXED(D)                                                                              \
-    template cudaError_t launch_pass1_t<D>(const Work &, const WorkItem *, int, int, int, cudaStream_t);      \
-    template cudaError_t launch_pass2_t<D>(const Work &, const WorkItem *, int, int, int, cudaStream_t);      \
-    template cudaError_t launch_pass1_theta_t<D>(const Work &, const WorkItem *, int, int, int, cudaStream_t);\
-    template int occupancy_t<D>(int, int);                                                                     \
-    template size_t pass_smem_bytes_t<D>(int, bool, int);
+#define HK_INSTANTIATE_MIXED(D)                                                                               \
+    template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, cudaStream_t);  \
+    template size_t smem_t<D>(int, int);                                                                        \
+    template int occupancy_t<D>(int, int);
 
 }  // namespace hk

@@ -110,8 +110,11 @@ __global__ void pack_kernel(Work w, const double *__restrict__ X, const double *
             const double T = keys_sorted[S.ev0 + S.n - 1];
             const double a = T - tv;
             w.Lam64[r] = S.mu0 * (normcdf(a / S.tau_t) - normcdf(-tv / S.tau_t)) - S.theta * expm1(-S.omega * a);
-            // first row of a strictly later time (upper bound of tv)
+            // first row of a strictly later time (upper bound of tv); most
+            // times are unique, so look at the next row before searching
             int64_t lo = i + 1, hi = S.n;
+            if (lo < hi && keys_sorted[S.ev0 + lo] > tv)
+                hi = lo;
             while (lo < hi) {
                 int64_t mid = (lo + hi) >> 1;
                 if (keys_sorted[S.ev0 + mid] > tv)
@@ -130,6 +133,7 @@ __global__ void pack_kernel(Work w, const double *__restrict__ X, const double *
             w.tie_end[r] = (int32_t)(i + 1);
         }
         w.w32[r] = 0.0f;
+        w.cm32[r] = -INFINITY;
         for (int p = 0; p < np; ++p)
             w.rec[S.rec0 + (int64_t)p * S.npad + i] = make_float4(f[4 * p], f[4 * p + 1], f[4 * p + 2], f[4 * p + 3]);
     }

@@ -154,15 +154,19 @@ def test_isolated_events_take_the_fp64_fixup(ctx):
     """Events far from every other in space and time have rates far below the
     FP32 range of the kernel values; they are recomputed in FP64."""
     w = synth.random_case(77, 600, 2, shuffle=True)
+    P = w.params
     t = w.t.copy()
     X = w.X.copy()
-    t[5] += 400.0       # far in time: the background kernel underflows
-    X[5] += 60.0
-    t[17] = 200.0
-    X[17] = [-50.0, 30.0]
-    w2 = synth.Workload("isolated", t, X, X, None, None, w.params)
-    lam = oracle.rates(t, X, w.params)
-    assert lam[5] < 1e-30 and lam[17] < 1e-30
+    last = int(np.argmax(t))
+    # the latest event, 15 tau_t after the others and 6 km away: every kernel
+    # value it sees is ~e^-140, far below FP32's range but not zero in FP64
+    t[5] = t[last] + 15.0 * P["tau_t"]
+    X[5] = X[last] + [6.0, 0.0]
+    # an event 12 km from all others, inside the time range: ~e^-112
+    X[17] = X.min(axis=0) - [12.0, 0.0]
+    w2 = synth.Workload("isolated", t, X, X, None, None, P)
+    lam = oracle.rates(t, X, P)
+    assert 0.0 < lam[5] < 1e-40 and 0.0 < lam[17] < 1e-40
     assert_close(ctx, w2, "mixed")
     assert_close(ctx, w2, "fp64")
 
