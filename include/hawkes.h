@@ -194,6 +194,34 @@ hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const in
                                        const hawkes_params *params, hawkes_precision prec,
                                        hawkes_stream stream, double *out_loglik, double *out_grad_X);
 
+/* ------------------------------------------------------ no allocation -- */
+
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory.  Code hosted by a framework or plugin
+ * system that owns every device allocation (a pool that a raw cudaMalloc
+ * would bypass), and real-time or embedded callers that forbid allocation
+ * after start-up, cannot create a hawkes_ctx, whose workspace is allocated.
+ *
+ * hawkes_loglik_noalloc computes ell of Eq. (1) for up to
+ * HAWKES_NOALLOC_MAX_N events in FP64 (ordered pairs, the arithmetic of
+ * HAWKES_PREC_FP64) and calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch is a fixed array of HAWKES_NOALLOC_MAX_N * 16 + 32
+ * doubles (about 1 MiB) in the library's static device memory, which every
+ * GPU that loads the library holds until the process exits.
+ *   t, X: device [n], [n*d] (row-major), on the calling thread's current
+ *         CUDA device; any time order.  1 <= n <= HAWKES_NOALLOC_MAX_N,
+ *         1 <= d <= 8; larger n returns HAWKES_ERR_INVALID_ARG.
+ *   out_loglik: device [1]; -inf for a zero rate; NaN when some t_n is
+ *         negative or not finite or some coordinate is not finite.
+ * Work is enqueued on `stream`.  The first call on a device looks up the
+ * device address of the scratch array (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Every call shares the one scratch
+ * array: calls whose work overlaps on the GPU (different streams, no
+ * ordering between them) race and give wrong results. */
+#define HAWKES_NOALLOC_MAX_N 8192
+hawkes_status hawkes_loglik_noalloc(const double *t, const double *X, int64_t n, int32_t d,
+                                    const hawkes_params *params, hawkes_stream stream, double *out_loglik);
+
 /* ------------------------------------------------------------ probing -- */
 
 /* Measure, on `device`, how many FP32 fused multiply-adds and how many MUFU

@@ -6,6 +6,7 @@ The computation lives in libhawkes.so (C ABI: include/hawkes.h); this package
 only marshals torch tensors into it.
 """
 from .api import (HawkesContext, HawkesError, hawkes_batch_loglik_grad, hawkes_loglik,  # noqa: F401
-                  hawkes_loglik_grad_locations, hmc_leapfrog_trajectory, params_struct, probe_pipe_rates,
+                  hawkes_loglik_grad_locations, hawkes_loglik_noalloc, hmc_leapfrog_trajectory, params_struct,
+                  probe_pipe_rates,
                   version)
 from .autograd import HawkesLogLik, hawkes_loglik_autograd  # noqa: F401,E402

@@ -30,8 +30,9 @@ EXPORTED = (
     "hawkes_ctx_create", "hawkes_ctx_destroy", "hawkes_last_error", "hawkes_ctx_sync_status",
     "hawkes_ctx_set_option", "hawkes_ctx_kernel_stats", "hawkes_ctx_reset_stats", "hawkes_loglik",
     "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
-    "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates",
+    "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc",
 )
+NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
 
 class HawkesParams(ctypes.Structure):
@@ -81,6 +82,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_batch_loglik_grad.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, pp, i32,
                                              vp, dp, dp]
     lib.hawkes_batch_loglik_grad.restype = st
+    lib.hawkes_loglik_noalloc.argtypes = [dp, dp, i64, i32, pp, vp, dp]
+    lib.hawkes_loglik_noalloc.restype = st
     dpp = ctypes.POINTER(ctypes.c_double)
     lib.hawkes_probe_pipe_rates.argtypes = [i32, dpp, dpp, dpp]
     lib.hawkes_probe_pipe_rates.restype = st

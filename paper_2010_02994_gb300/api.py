@@ -200,6 +200,25 @@ def hawkes_batch_loglik_grad(ctx: HawkesContext, sizes, dims, t, X, params_list,
     return ell, g
 
 
+def hawkes_loglik_noalloc(t, X, params) -> torch.Tensor:
+    """ell of Eq. (1) (FP64) through the entry point that allocates no device
+    memory, for up to 8192 events; runs on the tensors' device and stream.
+    The returned 0-d tensor is the caller's output buffer."""
+    lib = _lib.load()
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X")
+    n, d, X = _shape(t, X)
+    out = torch.empty((), dtype=torch.float64, device=t.device)
+    p = params_struct(params)
+    with torch.cuda.device(t.device):
+        st = lib.hawkes_loglik_noalloc(_ptr(t), _ptr(X), n, d, ctypes.byref(p),
+                                       ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream), _ptr(out))
+    if st != _lib.HAWKES_OK:
+        raise HawkesError(st, f"hawkes_loglik_noalloc: n must be in [1, {_lib.NOALLOC_MAX_N}], d in [1, 8], "
+                              "parameters finite and positive")
+    return out
+
+
 def probe_pipe_rates(device: int = 0) -> dict:
     """Measured FP32 FMA and MUFU ex2 results per SM per clock (and the SM clock)."""
     lib = _lib.load()
