@@ -32,6 +32,23 @@ UNIT = "evals/s"
 MAX_SM_MHZ_NOMINAL = 2070.0  # GB300 maximum SM clock
 CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 
+# DRAM bytes (read + write) per launch of each pair kernel at N=1e5, D=2, from
+# one ncu capture (profiles/pair_kernels_n100000_d2.md), valid for the kernel
+# source whose SHA-256 is recorded with it; reported as null otherwise.
+PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", "hk_pairs_mixed.cuh")
+MEASURED_TRAFFIC = {"source_sha256": "8ca4c7532c0a2761e9f6ad1c25fc7dafbd8a73abe3279b64ea700d6006394956",
+                    "pass1_rates": 3724800 + 512, "pass2_gradient": 4715264 + 19836416}
+
+
+def measured_traffic(kernel: str):
+    import hashlib
+
+    try:
+        sha = hashlib.sha256(open(PAIR_KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return MEASURED_TRAFFIC.get(kernel) if sha == MEASURED_TRAFFIC["source_sha256"] else None
+
 
 def pass_bound_cycles(d: int, which: str, fma_rate: float, ex2_rate: float) -> float:
     """SM cycles per unordered pair: max(FP32 ops / FMA rate, ex2 / MUFU rate),
@@ -187,6 +204,73 @@ def flush_l2(buf):
     buf.zero_()
 
 
+def other_workloads(dev, stream, l2) -> dict:
+    """Batched 64-set latent-space workload (one call, mixed path) and one
+    20-step HMC trajectory at N=1e4 (mixed path, CUDA graph), timed with
+    CUDA events; L2 flushed before each timed call."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad, hmc_leapfrog_trajectory
+
+    out = {}
+    sets = synth.make_c4()
+    sizes = [w.n for w in sets]
+    dims = [w.d for w in sets]
+    ctx = HawkesContext(device=dev.index or 0, max_n=sum(sizes), max_d=8)
+    t = torch.tensor(np.concatenate([w.t for w in sets]), device=dev)
+    X = torch.tensor(np.concatenate([w.X.reshape(-1) for w in sets]), device=dev)
+    params = [w.params for w in sets]
+    for _ in range(2):
+        hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, check=False)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(10):
+        flush_l2(l2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.sync_status()
+    pairs = float(sum(n * n for n in sizes))
+    m = statistics.median(ms)
+    out["batched_c4"] = {"sets": len(sets), "events": sum(sizes), "dims": sorted(set(dims)), "ms_per_call": m,
+                         "calls_per_s": 1e3 / m, "pairs_per_s": pairs / (m * 1e-3)}
+    ctx.close()
+
+    w = synth.make_c2()
+    ctx = HawkesContext(device=dev.index or 0, max_n=w.n, max_d=w.d)
+    t = torch.tensor(w.t, device=dev)
+    X = torch.tensor(w.X, device=dev)
+    lo = torch.tensor(w.box_lo, device=dev)
+    hi = torch.tensor(w.box_hi, device=dev)
+    rng = np.random.default_rng(11)
+    p0 = torch.tensor(rng.standard_normal(size=w.X.shape), device=dev)
+    steps = w.meta.get("hmc_steps", 20)
+    eps = 2e-3
+    for _ in range(2):
+        hmc_leapfrog_trajectory(ctx, t, X, p0, w.params, eps, steps, 0.0, lo, hi, check=False)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(10):
+        flush_l2(l2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hmc_leapfrog_trajectory(ctx, t, X, p0, w.params, eps, steps, 0.0, lo, hi, check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.sync_status()
+    m = statistics.median(ms)
+    out["hmc_c2"] = {"n": w.n, "d": w.d, "leapfrog_steps": steps, "ms_per_trajectory": m,
+                     "trajectories_per_s": 1e3 / m, "grad_evals_per_s": (steps + 1) * 1e3 / m}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,6 +281,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and HMC workloads")
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--kernels-only", action="store_true",
                     help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
@@ -277,15 +362,21 @@ def main():
         step("mixed")
     torch.cuda.synchronize()
     k1, k2 = ctx.kernel_stats(0), ctx.kernel_stats(1)
+    stages = {name: ctx.kernel_stats(i)["ms"] / prof_steps
+              for i, name in enumerate(("pass1_rates", "pass2_gradient", "prep_sort_pack", "finalize_rates",
+                                        "finalize_gradient"))}
     ctx.set_option("profile", 0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pairs = 0.5 * n * (n - 1)
+
+    which_name = {"pass1": "pass1_rates", "pass2": "pass2_gradient"}
 
     def roof(stat, which):
         achieved = stat["pairs"] / (stat["ms"] * 1e-3) / 1e9
         peak = sms * MAX_SM_MHZ_NOMINAL * 1e6 / pass_bound_cycles(d, which, fma_rate, ex2_rate) / 1e9
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
-                "traffic": None, "ms_per_launch": stat["ms"] / max(1, stat["launches"]),
+                "traffic": measured_traffic(which_name[which]), "traffic_unit": "bytes per launch",
+                "ms_per_launch": stat["ms"] / max(1, stat["launches"]),
                 "peak_basis": (f"{sms} SMs x {MAX_SM_MHZ_NOMINAL:.0f} MHz / max(FP32 ops/{fma_rate:.1f}, "
                                f"ex2/{ex2_rate:.1f}) cycles per unordered pair (measured per-SM rates)")}
 
@@ -343,6 +434,11 @@ def main():
     h2d = t_h.numel() * 8 + X_h.numel() * 8
     d2h = g_h.numel() * 8 + 8
 
+    # --- the other paper-shaped workloads (reported beside the headline) -----
+    extra = {}
+    if not args.no_extra:
+        extra = other_workloads(dev, stream, l2)
+
     # --- CPU baseline: the oracle on the host cores ---------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -371,6 +467,8 @@ def main():
         "e2e": {"value": world * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": ms_e2e},
         "cpu_baseline": cpu,
+        "stages_ms_per_eval": stages,
+        "other_workloads": extra,
         "clocks": clk,
         "gpu_launches": int(launches["own"]),
         "gpu_launches_per_step": per_step_launches,

@@ -115,8 +115,10 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
 
 /* Kernel timing collected while HAWKES_OPT_PROFILE is on (waits for the
  * recorded events).  kernel: 0 = rate pass (lambda row sums), 1 = gradient
- * pass.  Returns the summed device time in ms, the number of launches and
- * the number of unordered event pairs those launches processed. */
+ * pass, 2 = validation + time sort + packing, 3 = rate finalization (ell),
+ * 4 = gradient finalization.  Returns the summed device time in ms, the
+ * number of launches and the number of unordered event pairs those launches
+ * processed (0 for stages 2-4). */
 hawkes_status hawkes_ctx_kernel_stats(hawkes_ctx *ctx, int32_t kernel, double *total_ms,
                                       int64_t *launches, double *pairs);
 hawkes_status hawkes_ctx_reset_stats(hawkes_ctx *ctx);
@@ -126,6 +128,26 @@ hawkes_status hawkes_ctx_reset_stats(hawkes_ctx *ctx);
  * `library` the launches of the CUB radix sort used for the time order
  * (counted as one per sort call). */
 hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64_t *library);
+
+/* ----------------------------------------------------------- autotuner -- */
+
+/* Tile shape of the mixed pair kernels for one dimension d and one size
+ * bucket (bucket = ceil(log2 n)): warps per CTA (1, 2, 4 or 8; the pair block
+ * is 32 x rows-per-lane x warps events square) and the cap on persistent CTAs
+ * per SM (0 = as many as fit).  Entries set here or found by hawkes_autotune
+ * are used whenever HAWKES_OPT_BLOCK_WARPS / HAWKES_OPT_CTAS_PER_SM are 0. */
+hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t ctas_per_sm);
+hawkes_status hawkes_ctx_get_tuning(const hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t *warps,
+                                    int32_t *ctas_per_sm);
+
+/* Time every tile shape for the caller's data (t, X as in
+ * hawkes_loglik_grad_locations; mixed precision) with CUDA events on
+ * `stream`, store the fastest for (d, bucket of n) in the context, and
+ * return it.  Synchronizes the stream; out_ms (nullable) receives the
+ * fastest evaluation time. */
+hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                              const hawkes_params *params, hawkes_stream stream, int32_t *best_warps,
+                              int32_t *best_ctas_per_sm, double *out_ms);
 
 /* ------------------------------------------------------- log-likelihood -- */
 

@@ -30,7 +30,8 @@ EXPORTED = (
     "hawkes_ctx_create", "hawkes_ctx_destroy", "hawkes_last_error", "hawkes_ctx_sync_status",
     "hawkes_ctx_set_option", "hawkes_ctx_kernel_stats", "hawkes_ctx_reset_stats", "hawkes_loglik",
     "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
-    "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc",
+    "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc", "hawkes_ctx_set_tuning",
+    "hawkes_ctx_get_tuning", "hawkes_autotune",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -82,6 +83,13 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_batch_loglik_grad.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, pp, i32,
                                              vp, dp, dp]
     lib.hawkes_batch_loglik_grad.restype = st
+    ip = ctypes.POINTER(i32)
+    lib.hawkes_ctx_set_tuning.argtypes = [vp, i32, i32, i32, i32]
+    lib.hawkes_ctx_set_tuning.restype = st
+    lib.hawkes_ctx_get_tuning.argtypes = [vp, i32, i32, ip, ip]
+    lib.hawkes_ctx_get_tuning.restype = st
+    lib.hawkes_autotune.argtypes = [vp, dp, dp, i64, i32, pp, vp, ip, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.hawkes_autotune.restype = st
     lib.hawkes_loglik_noalloc.argtypes = [dp, dp, i64, i32, pp, vp, dp]
     lib.hawkes_loglik_noalloc.restype = st
     dpp = ctypes.POINTER(ctypes.c_double)

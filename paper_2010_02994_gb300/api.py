@@ -55,7 +55,8 @@ def _precision(p) -> int:
 class HawkesContext:
     """Owns a libhawkes context (device workspace, cached HMC graphs)."""
 
-    def __init__(self, device: int = 0, max_n: int = 1024, max_d: int = 8):
+    def __init__(self, device: int = 0, max_n: int = 1024, max_d: int = 8, tuning: bool = True):
+        """tuning: load this GPU's entries of the tile-shape table (tuning.json)."""
         self.lib = _lib.load()
         self.device = int(device)
         h = ctypes.c_void_p()
@@ -63,6 +64,15 @@ class HawkesContext:
         if st != _lib.HAWKES_OK:
             raise HawkesError(st, self.lib.hawkes_last_error(None).decode())
         self.handle = h
+        if tuning:
+            from . import tuning as _tuning
+
+            _tuning.load_into(self)
+
+    def get_tuning(self, d: int, bucket: int):
+        w, c = ctypes.c_int32(), ctypes.c_int32()
+        self.check(self.lib.hawkes_ctx_get_tuning(self.handle, int(d), int(bucket), ctypes.byref(w), ctypes.byref(c)))
+        return {"warps": w.value, "ctas_per_sm": c.value}
 
     def close(self):
         if getattr(self, "handle", None):

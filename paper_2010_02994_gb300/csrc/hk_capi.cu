@@ -93,12 +93,17 @@ struct hawkes_ctx {
     // options
     int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76;
     std::vector<ProfEvent> prof_pending;
-    double prof_ms[2] = {0, 0};
-    int64_t prof_launches[2] = {0, 0};
-    double prof_pairs[2] = {0, 0};
+    static constexpr int kStages = 5;
+    double prof_ms[kStages] = {};
+    int64_t prof_launches[kStages] = {};
+    double prof_pairs[kStages] = {};
     int64_t launches_own = 0, launches_lib = 0;
     HmcGraph hmc;
     int occ[kMaxD + 1][4][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..3][warps]
+    static constexpr int kBuckets = 32;
+    int tune_warps[kMaxD + 1][kBuckets] = {};  // 0: no entry
+    int tune_ctas[kMaxD + 1][kBuckets] = {};
+    int cur_ctas_by_d[kMaxD + 1] = {};         // CTA cap per dimension for the current plan
     std::vector<char> uploaded;     // bytes of the plan last copied to the device
     // workspace views of the current plan
     Work w{};
@@ -147,10 +152,22 @@ bool params_ok(const hawkes_params *p)
 
 // Warps per CTA of the pair kernels for a set of n events in d dimensions:
 // the largest count that still gives every SM slot several pair blocks.
+int size_bucket(int64_t n)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < n && b < 31)
+        ++b;
+    return b;
+}
+
 int choose_warps(const hawkes_ctx *ctx, int64_t n, int d, bool theta)
 {
     if (ctx->opt_warps > 0)
         return ctx->opt_warps;
+    const int tw = ctx->tune_warps[d][size_bucket(n)];
+    if (tw > 0 && pass_smem_bytes(d, 2, tw) <= 200 * 1024 &&
+        (!theta || pass_smem_bytes(d, 3, tw) <= 200 * 1024))
+        return tw;
     const int R = rows_per_lane(d);
     const int candidates[4] = {8, 4, 2, 1};
     for (int wv : candidates) {
@@ -214,8 +231,10 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
     for (int s = 0; s < nsets; ++s)
         nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
     for (int d = 1; d <= kMaxD; ++d)
-        if (nmax_by_d[d] > 0)
+        if (nmax_by_d[d] > 0) {
             pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d, theta);
+            ctx->cur_ctas_by_d[d] = ctx->tune_ctas[d][size_bucket(nmax_by_d[d])];
+        }
     int64_t ev = 0, x = 0, row = 0, rec4 = 0, p1 = 0, p2 = 0, f1 = 0, f2 = 0;
     int32_t seg = 0;
     for (int s = 0; s < nsets; ++s) {
@@ -449,6 +468,8 @@ int persistent_grid(hawkes_ctx *ctx, int d, int pass, int warps, int nitems)
     int per_sm = ctx->occ[d][pass][warps];
     if (ctx->opt_ctas > 0)
         per_sm = std::min(per_sm, ctx->opt_ctas);
+    else if (ctx->cur_ctas_by_d[d] > 0)
+        per_sm = std::min(per_sm, ctx->cur_ctas_by_d[d]);
     per_sm = std::max(per_sm, 1);
     return std::max(1, std::min(nitems, per_sm * ctx->sm_count));
 }
@@ -473,6 +494,9 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
 {
     Work &w = ctx->w;
     const int32_t ns = (int32_t)pl.sets.size();
+    ProfEvent pe{};
+    if (ctx->opt_profile)
+        prof_begin(ctx, s, pe, 2, 0.0);
     // per-evaluation control words: flagged-row count, fixup counter, set flags
     HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0, sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + ns),
                            s),
@@ -492,6 +516,8 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
                "time sort");
     }
     HK_TRY(launch_pack_rows(w, X, ctx->keys_b, ctx->vals_b, pl.total_rows, ctx->d_set_row0, s), "pack");
+    if (ctx->opt_profile)
+        prof_end(ctx, s, pe);
     return HAWKES_OK;
 }
 
@@ -549,8 +575,13 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
+    ProfEvent pf{};
+    if (ctx->opt_profile)
+        prof_begin(ctx, s, pf, 3, 0.0);
     HK_TRY(launch_finalize_rows(w, pl.total_segs, false, theta, s), "finalize rows");
     HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, theta, s), "FP64 rate fixup");
+    if (ctx->opt_profile)
+        prof_end(ctx, s, pf);
     if (theta) {
         ++ctx->launches_own;
         HK_TRY(launch_theta_grad(w, out_grad_params, s), "parameter gradient");
@@ -570,8 +601,13 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
+    ProfEvent pg{};
+    if (ctx->opt_profile)
+        prof_begin(ctx, s, pg, 4, 0.0);
     HK_TRY(launch_finalize_grad(w, pl.total_segs, false, out_grad, g_sorted, s), "finalize gradient");
     HK_TRY(launch_fixup_grad(w, pl.total_segs, fix_grid, out_grad, g_sorted, s), "FP64 gradient fixup");
+    if (ctx->opt_profile)
+        prof_end(ctx, s, pg);
     return HAWKES_OK;
 }
 
@@ -766,7 +802,7 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
 hawkes_status hawkes_ctx_kernel_stats(hawkes_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches,
                                       double *pairs)
 {
-    if (!ctx || kernel < 0 || kernel > 1)
+    if (!ctx || kernel < 0 || kernel >= hawkes_ctx::kStages)
         return HAWKES_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     for (auto &pe : ctx->prof_pending) {
@@ -796,7 +832,7 @@ hawkes_status hawkes_ctx_reset_stats(hawkes_ctx *ctx)
     hawkes_ctx_kernel_stats(ctx, 0, nullptr, nullptr, nullptr);
     ctx->launches_own = 0;
     ctx->launches_lib = 0;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < hawkes_ctx::kStages; ++k) {
         ctx->prof_ms[k] = 0;
         ctx->prof_launches[k] = 0;
         ctx->prof_pairs[k] = 0;
@@ -812,6 +848,31 @@ hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64
         *own = ctx->launches_own;
     if (library)
         *library = ctx->launches_lib;
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t ctas_per_sm)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (d < 1 || d > kMaxD || bucket < 0 || bucket >= hawkes_ctx::kBuckets ||
+        !(warps == 0 || warps == 1 || warps == 2 || warps == 4 || warps == 8) || ctas_per_sm < 0 ||
+        ctas_per_sm > 32)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "tuning entry out of range");
+    ctx->tune_warps[d][bucket] = warps;
+    ctx->tune_ctas[d][bucket] = ctas_per_sm;
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_ctx_get_tuning(const hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t *warps,
+                                    int32_t *ctas_per_sm)
+{
+    if (!ctx || d < 1 || d > kMaxD || bucket < 0 || bucket >= hawkes_ctx::kBuckets)
+        return HAWKES_ERR_INVALID_ARG;
+    if (warps)
+        *warps = ctx->tune_warps[d][bucket];
+    if (ctas_per_sm)
+        *ctas_per_sm = ctx->tune_ctas[d][bucket];
     return HAWKES_OK;
 }
 
@@ -855,6 +916,78 @@ hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, con
                                            double *out_loglik, double *out_grad_X, double *out_grad_params)
 {
     return loglik_common(ctx, t, X, n, d, params, prec, stream, out_loglik, out_grad_X, out_grad_params, true);
+}
+
+hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                              const hawkes_params *params, hawkes_stream stream, int32_t *best_warps,
+                              int32_t *best_ctas_per_sm, double *out_ms)
+{
+    hawkes_status st = check_common(ctx, t, X, n, d, params, HAWKES_PREC_MIXED);
+    if (st != HAWKES_OK)
+        return st;
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double *out = nullptr;
+    HK_TRY(cudaMalloc(&out, sizeof(double) * (1 + n * d)), "autotune output");
+    const int saved_w = ctx->opt_warps, saved_c = ctx->opt_ctas, saved_p = ctx->opt_profile;
+    ctx->opt_profile = 0;
+    double best = 1e300;
+    int bw = 0, bc = 0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int wv : {1, 2, 4, 8}) {
+        if (pass_smem_bytes(d, 2, wv) > 200 * 1024)
+            continue;
+        const int max_c = std::max(1, ctx->occ[d][2][wv]);
+        for (int cv = 0; cv <= max_c; ++cv) {
+            if (cv > 0 && cv == max_c)
+                continue;  // the same as "as many as fit"
+            ctx->opt_warps = wv;
+            ctx->opt_ctas = cv;
+            float ms = 0.0f, tot = 0.0f;
+            st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out, out + 1,
+                                              nullptr);
+            for (int rep = 0; rep < 3 && st == HAWKES_OK; ++rep) {
+                cudaEventRecord(a, s);
+                st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out,
+                                                  out + 1, nullptr);
+                cudaEventRecord(b, s);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+                tot += ms;
+            }
+            if (st != HAWKES_OK)
+                break;
+            if (tot / 3.0 < best) {
+                best = tot / 3.0;
+                bw = wv;
+                bc = cv;
+            }
+        }
+        if (st != HAWKES_OK)
+            break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->opt_warps = saved_w;
+    ctx->opt_ctas = saved_c;
+    ctx->opt_profile = saved_p;
+    cudaStreamSynchronize(s);
+    cudaFree(out);
+    if (st != HAWKES_OK)
+        return st;
+    if (bw == 0)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "no tile shape fits this dimension");
+    ctx->tune_warps[d][size_bucket(n)] = bw;
+    ctx->tune_ctas[d][size_bucket(n)] = bc;
+    if (best_warps)
+        *best_warps = bw;
+    if (best_ctas_per_sm)
+        *best_ctas_per_sm = bc;
+    if (out_ms)
+        *out_ms = best;
+    return HAWKES_OK;
 }
 
 hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,

@@ -67,11 +67,13 @@ __device__ double block_sum(double v, double *sh)
     return r;
 }
 
-// sum_{k < count} (double)p[k * stride], added in order k = 0, 1, ...; the
-// loads of eight consecutive terms are issued before they are added.
+// sum_{k < count} p[k * stride] of FP32 partials, added in the order
+// k = 0, 1, ... with Kahan compensation in FP32 (FP64 adds run at 1/64 of
+// the FP32 rate here), returned in FP64.  The error is about two FP32 units
+// of sum |p_k|; the loads of eight consecutive terms are issued together.
 __device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ p, int count, int64_t stride)
 {
-    double acc = 0.0;
+    float s = 0.0f, c = 0.0f;
     int k = 0;
     for (; k + 8 <= count; k += 8) {
         float v[8];
@@ -79,12 +81,20 @@ __device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ 
         for (int u = 0; u < 8; ++u)
             v[u] = p[(int64_t)(k + u) * stride];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            acc += (double)v[u];
+        for (int u = 0; u < 8; ++u) {
+            const float y = v[u] - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
     }
-    for (; k < count; ++k)
-        acc += (double)p[(int64_t)k * stride];
-    return acc;
+    for (; k < count; ++k) {
+        const float y = p[(int64_t)k * stride] - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    return (double)s - (double)c;
 }
 
 struct PairFp64 {

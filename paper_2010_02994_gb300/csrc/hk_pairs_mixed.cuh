@@ -154,7 +154,7 @@ __device__ __forceinline__ void chunk_steps(const float4 *__restrict__ pv, int s
                                             float (&acc)[KindTraits<KIND, D>::VC])
 {
     using T = KindTraits<KIND, D>;
-#pragma unroll(MASKED ? 1 : 32)
+#pragma unroll(MASKED ? 1 : 8)
     for (int j = 0; j < 32; ++j) {
         float cf[4 * T::NPP];
 #pragma unroll

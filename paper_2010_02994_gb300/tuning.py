@@ -1,0 +1,72 @@
+"""Tile-shape tuning table: measure with the library's autotuner, keep as JSON.
+
+The table maps a GPU name to entries {"d": D, "bucket": ceil(log2 N),
+"warps": W, "ctas_per_sm": C, "ms": t}.  `load_into(ctx)` copies the entries
+for the context's GPU into the context; `autotune(ctx, t, X, params)` times
+every shape on the caller's data, stores the best in the context, and
+`save(...)` writes the table.  The timing itself runs in the library
+(hawkes_autotune); this module only keeps the file.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+
+import torch
+
+from . import _lib
+from .api import HawkesContext, _dev_f64, _ptr, _shape, params_struct
+
+DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def gpu_name(device: int = 0) -> str:
+    return torch.cuda.get_device_name(device)
+
+
+def bucket(n: int) -> int:
+    return max(0, math.ceil(math.log2(max(1, n))))
+
+
+def read(path: str = DEFAULT_PATH) -> dict:
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def load_into(ctx: HawkesContext, path: str = DEFAULT_PATH) -> int:
+    """Copy the table's entries for this GPU into the context; returns how many."""
+    entries = read(path).get(gpu_name(ctx.device), [])
+    for e in entries:
+        ctx.check(ctx.lib.hawkes_ctx_set_tuning(ctx.handle, int(e["d"]), int(e["bucket"]), int(e["warps"]),
+                                                int(e["ctas_per_sm"])))
+    return len(entries)
+
+
+def autotune(ctx: HawkesContext, t, X, params) -> dict:
+    """Time every tile shape on (t, X) and keep the fastest in the context."""
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X")
+    n, d, X = _shape(t, X)
+    w, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    p = params_struct(params)
+    ctx.check(ctx.lib.hawkes_autotune(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p), ctx.stream(),
+                                      ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)))
+    return {"d": d, "bucket": bucket(n), "n": n, "warps": w.value, "ctas_per_sm": c.value, "ms": ms.value}
+
+
+def save(entries: list, device: int = 0, path: str = DEFAULT_PATH) -> None:
+    """Merge entries into the table under this GPU's name."""
+    table = read(path)
+    name = gpu_name(device)
+    cur = {(e["d"], e["bucket"]): e for e in table.get(name, [])}
+    for e in entries:
+        cur[(e["d"], e["bucket"])] = e
+    table[name] = sorted(cur.values(), key=lambda e: (e["d"], e["bucket"]))
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
