@@ -103,13 +103,21 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            the time sort is skipped (checked on device)
  *   HAWKES_OPT_MIXED_FIXUP_EXP  log2 of the rate threshold below which a
  *                            row of the mixed path is recomputed in FP64
- *                            (default -76, range [-120, 0])                  */
+ *                            (default -76, range [-120, 0])
+ *   HAWKES_OPT_SKIP_FAR_BLOCKS  1: the mixed path skips pair blocks whose
+ *                            time gap makes every kernel value underflow
+ *                            FP32 (exponent <= -130 for both terms); their
+ *                            contribution is exactly zero, so results are
+ *                            bit-identical to the dense evaluation, but the
+ *                            number of pairs evaluated depends on the data
+ *                            (default 0: every pair is evaluated)            */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,
     HAWKES_OPT_PROFILE = 3,
     HAWKES_OPT_TIMES_SORTED = 4,
-    HAWKES_OPT_MIXED_FIXUP_EXP = 5
+    HAWKES_OPT_MIXED_FIXUP_EXP = 5,
+    HAWKES_OPT_SKIP_FAR_BLOCKS = 6
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 
@@ -172,6 +180,15 @@ hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, con
                                            hawkes_stream stream, double *out_loglik, double *out_grad_X,
                                            double *out_grad_params);
 
+/* Probability that each event arises from self-excitation under the given
+ * state, xi(x_n, t_n) / (xi(x_n, t_n) + mu(x_n, t_n)) = Xi_n / lambda_n
+ * (Section 4.3; its posterior mean over MCMC states is the caller's
+ * average).  out_prob: device [n] in the caller's event order; NaN for an
+ * event whose rate is zero. */
+hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                                          const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                                          double *out_prob);
+
 /* ------------------------------------------------------------------ HMC -- */
 
 /* One Hamiltonian Monte Carlo proposal over all locations (Section 3: HMC
@@ -197,6 +214,21 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
                                       const hawkes_params *params, double eps, int32_t n_steps,
                                       const double *log_u, hawkes_precision prec, hawkes_stream stream,
                                       double *out_H0, double *out_H1, int32_t *out_accepted);
+
+/* One HMC proposal for each of n_sets independent sets (laid out as in
+ * hawkes_batch_loglik_grad), all advanced by one CUDA graph per shape: the
+ * leapfrog of hmc_leapfrog_trajectory with each set's own step size, box
+ * walls, Hamiltonian and accept decision.
+ *   eps: HOST [n_sets] step sizes;  log_u: device [n_sets];
+ *   X_inout, p0, box_lo, box_hi: device, laid out like X;
+ *   out_H0, out_H1: device [n_sets];  out_accepted: device int32 [n_sets].
+ * Each set's rows are replaced by its proposal when that set accepts. */
+hawkes_status hawkes_batch_hmc_trajectory(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets,
+                                          const int32_t *dims, const double *t, double *X_inout, const double *p0,
+                                          const double *box_lo, const double *box_hi, const hawkes_params *params,
+                                          const double *eps, int32_t n_steps, const double *log_u,
+                                          hawkes_precision prec, hawkes_stream stream, double *out_H0,
+                                          double *out_H1, int32_t *out_accepted);
 
 /* ------------------------------------------------------------- batched -- */
 

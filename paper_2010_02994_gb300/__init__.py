@@ -5,8 +5,10 @@ its location and parameter gradients, and HMC over event locations
 The computation lives in libhawkes.so (C ABI: include/hawkes.h); this package
 only marshals torch tensors into it.
 """
-from .api import (HawkesContext, HawkesError, hawkes_batch_loglik_grad, hawkes_loglik,  # noqa: F401
-                  hawkes_loglik_grad_locations, hawkes_loglik_noalloc, hmc_leapfrog_trajectory, params_struct,
+from .api import (HawkesContext, HawkesError, hawkes_batch_hmc_trajectory, hawkes_batch_loglik_grad,  # noqa: F401
+                  hawkes_loglik,
+                  hawkes_loglik_grad_locations, hawkes_loglik_noalloc, hawkes_self_excitation_prob,
+                  hmc_leapfrog_trajectory, params_struct,
                   probe_pipe_rates,
                   version)
 from .autograd import HawkesLogLik, hawkes_loglik_autograd  # noqa: F401,E402

@@ -23,7 +23,8 @@ STATUS_NAMES = {
     6: "HAWKES_ERR_INVALID_DATA",
 }
 PREC = {"mixed": 0, "fp64": 1}
-OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5}
+OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5,
+           "skip_far_blocks": 6}
 
 # every function declared in include/hawkes.h
 EXPORTED = (
@@ -31,7 +32,7 @@ EXPORTED = (
     "hawkes_ctx_set_option", "hawkes_ctx_kernel_stats", "hawkes_ctx_reset_stats", "hawkes_loglik",
     "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
     "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc", "hawkes_ctx_set_tuning",
-    "hawkes_ctx_get_tuning", "hawkes_autotune",
+    "hawkes_ctx_get_tuning", "hawkes_autotune", "hawkes_batch_hmc_trajectory", "hawkes_self_excitation_prob",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -73,6 +74,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_ctx_launch_count.restype = st
     lib.hawkes_ctx_reset_stats.argtypes = [vp]
     lib.hawkes_ctx_reset_stats.restype = st
+    lib.hawkes_self_excitation_prob.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
+    lib.hawkes_self_excitation_prob.restype = st
     lib.hawkes_loglik.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
     lib.hawkes_loglik.restype = st
     lib.hawkes_loglik_grad_locations.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp, dp, dp]
@@ -83,6 +86,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_batch_loglik_grad.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, pp, i32,
                                              vp, dp, dp]
     lib.hawkes_batch_loglik_grad.restype = st
+    lib.hawkes_batch_hmc_trajectory.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, dp, dp,
+                                                dp, pp, ctypes.POINTER(ctypes.c_double), i32, dp, i32, vp, dp, dp,
+                                                dp]
+    lib.hawkes_batch_hmc_trajectory.restype = st
     ip = ctypes.POINTER(i32)
     lib.hawkes_ctx_set_tuning.argtypes = [vp, i32, i32, i32, i32]
     lib.hawkes_ctx_set_tuning.restype = st

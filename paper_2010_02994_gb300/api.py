@@ -137,6 +137,20 @@ def hawkes_loglik(ctx: HawkesContext, t, X, params, precision="mixed", check: bo
     return out
 
 
+def hawkes_self_excitation_prob(ctx: HawkesContext, t, X, params, precision="mixed", check: bool = True):
+    """xi / (xi + mu) at every event (Section 4.3), as a device tensor (N,)."""
+    t = _dev_f64(t, "t")
+    X = _dev_f64(X, "X")
+    n, d, X = _shape(t, X)
+    out = torch.empty(n, dtype=torch.float64, device=t.device)
+    p = params_struct(params)
+    ctx.check(ctx.lib.hawkes_self_excitation_prob(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p),
+                                                  _precision(precision), ctx.stream(), _ptr(out)))
+    if check:
+        ctx.sync_status()
+    return out
+
+
 def hawkes_loglik_grad_locations(ctx: HawkesContext, t, X, params, precision="mixed", grad_params: bool = False,
                                  check: bool = True, out=None):
     """(ell, d ell/d X) -- and d ell/d Theta when grad_params -- as device tensors."""
@@ -237,6 +251,40 @@ def probe_pipe_rates(device: int = 0) -> dict:
     if st != _lib.HAWKES_OK:
         raise HawkesError(st, "pipe-rate probe failed")
     return {"fma_per_sm_clk": f.value, "ex2_per_sm_clk": e.value, "sm_mhz": mhz.value}
+
+
+def hawkes_batch_hmc_trajectory(ctx: HawkesContext, sizes, dims, t, X, p0, params_list, eps, n_steps: int, log_u,
+                                box_lo=None, box_hi=None, precision="mixed", check: bool = True):
+    """One HMC proposal per set (layout as in hawkes_batch_loglik_grad); X is
+    updated in place for the sets that accept.  eps: one step size per set;
+    log_u: (n_sets,) device tensor.  Returns (H0, H1, accepted) per set."""
+    t = _dev_f64(t, "t")
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (it is updated in place)")
+    p0 = _dev_f64(p0, "p0")
+    lo = None if box_lo is None else _dev_f64(box_lo, "box_lo")
+    hi = None if box_hi is None else _dev_f64(box_hi, "box_hi")
+    ns = len(sizes)
+    offs = (ctypes.c_int64 * (ns + 1))()
+    acc = 0
+    for i, s_ in enumerate(sizes):
+        offs[i] = acc
+        acc += int(s_)
+    offs[ns] = acc
+    dims_c = (ctypes.c_int32 * ns)(*[int(v) for v in dims])
+    ps = (HawkesParams * ns)(*[params_struct(p) for p in params_list])
+    eps_c = (ctypes.c_double * ns)(*[float(v) for v in eps])
+    log_u = _dev_f64(log_u, "log_u")
+    H0 = torch.empty(ns, dtype=torch.float64, device=t.device)
+    H1 = torch.empty(ns, dtype=torch.float64, device=t.device)
+    accd = torch.empty(ns, dtype=torch.int32, device=t.device)
+    ctx.check(ctx.lib.hawkes_batch_hmc_trajectory(ctx.handle, ns, offs, dims_c, _ptr(t), _ptr(X), _ptr(p0), _ptr(lo),
+                                                  _ptr(hi), ps, eps_c, int(n_steps), _ptr(log_u),
+                                                  _precision(precision), ctx.stream(), _ptr(H0), _ptr(H1),
+                                                  _ptr(accd)))
+    if check:
+        ctx.sync_status()
+    return H0, H1, accd
 
 
 def version() -> str:

@@ -31,10 +31,13 @@ std::string g_create_err;
 constexpr double kLog2e = 1.4426950408889634073599246810019;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-// control block (int32 words): [0] status, [4..7] kernel counters, [16..) set flags
+// control block (int32 words): [0] status, [4..7] kernel counters, [16..34)
+// work/done counters of the pair kernel of each dimension, [40..) set flags,
+// then one skip bound per set
 constexpr int kCtlStatus = 0;
 constexpr int kCtlCounters = 4;
-constexpr int kCtlSetFlags = 16;
+constexpr int kCtlDimCounters = 16;
+constexpr int kCtlSetFlags = 40;
 
 struct DeviceBuffer {
     void *ptr = nullptr;
@@ -77,7 +80,7 @@ struct Plan {
 
 struct HmcGraph {
     cudaGraphExec_t exec = nullptr;
-    std::tuple<int64_t, int32_t, int32_t, int32_t, bool, size_t> key;
+    std::vector<int64_t> key;
 };
 
 }  // namespace
@@ -91,7 +94,7 @@ struct hawkes_ctx {
     DeviceBuffer ws;
     size_t ws_generation = 0;
     // options
-    int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76;
+    int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
     double prof_ms[kStages] = {};
@@ -99,6 +102,8 @@ struct hawkes_ctx {
     double prof_pairs[kStages] = {};
     int64_t launches_own = 0, launches_lib = 0;
     HmcGraph hmc;
+    cudaStream_t side[kMaxD + 1] = {};  // forked streams for concurrent per-dimension launches
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxD + 1] = {};
     int occ[kMaxD + 1][4][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..3][warps]
     static constexpr int kBuckets = 32;
     int tune_warps[kMaxD + 1][kBuckets] = {};  // 0: no entry
@@ -116,8 +121,8 @@ struct hawkes_ctx {
     size_t sort_bytes = 0;
     // HMC state (sorted rows, stride kMaxD)
     double *hp = nullptr, *hg = nullptr, *hlo = nullptr, *hhi = nullptr;
-    double *hscal = nullptr;  // [0] eps, [1] log_u, [2] H0, [3] H1
-    int32_t *hint = nullptr;  // [0] accepted, [1] reflection failure
+    double *hscal = nullptr;  // per set: [0, ns) eps, [ns, 2ns) log u, [2ns, 3ns) H0, [3ns, 4ns) H1
+    int32_t *hint = nullptr;  // per set: [0, ns) accepted, [ns, 2ns) reflection failure
 };
 
 namespace {
@@ -349,8 +354,8 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
     c.take<char>(sort_bytes);
     for (int k = 0; k < 4; ++k)
         c.take<double>(pl.total_rows * kMaxD);
-    c.take<double>(8);
-    c.take<int32_t>(8);
+    c.take<double>(4 * ns + 8);
+    c.take<int32_t>(2 * ns + 8);
     return c.off + 256;
 }
 
@@ -378,8 +383,8 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
         HK_TRY(cudaDeviceSynchronize(), "synchronize before growing the control block");
         int32_t *ctl = nullptr;
         const int32_t cap = (int32_t)std::max<size_t>(ns, 64);
-        HK_TRY(cudaMalloc(&ctl, sizeof(int32_t) * (kCtlSetFlags + cap)), "control block");
-        HK_TRY(cudaMemset(ctl, 0, sizeof(int32_t) * (kCtlSetFlags + cap)), "control block");
+        HK_TRY(cudaMalloc(&ctl, sizeof(int32_t) * (kCtlSetFlags + 2 * cap)), "control block");
+        HK_TRY(cudaMemset(ctl, 0, sizeof(int32_t) * (kCtlSetFlags + 2 * cap)), "control block");
         if (ctx->ctl) {
             HK_TRY(cudaMemcpy(ctl, ctx->ctl, sizeof(int32_t) * kCtlSetFlags, cudaMemcpyDeviceToDevice), "control");
             cudaFree(ctx->ctl);
@@ -426,9 +431,11 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     ctx->hg = c.take<double>(pl.total_rows * kMaxD);
     ctx->hlo = c.take<double>(pl.total_rows * kMaxD);
     ctx->hhi = c.take<double>(pl.total_rows * kMaxD);
-    ctx->hscal = c.take<double>(8);
-    ctx->hint = c.take<int32_t>(8);
+    ctx->hscal = c.take<double>(4 * ns + 8);
+    ctx->hint = c.take<int32_t>(2 * ns + 8);
     w.set_flags = ctx->ctl + kCtlSetFlags;
+    w.set_cmmax = ctx->ctl + kCtlSetFlags + ctx->ctl_sets;
+    w.skip_far = ctx->opt_skip;
     w.counters = ctx->ctl + kCtlCounters;
     w.status = reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus);
     // Upload the plan, unless the device already holds exactly this plan at
@@ -497,10 +504,11 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
     ProfEvent pe{};
     if (ctx->opt_profile)
         prof_begin(ctx, s, pe, 2, 0.0);
-    // per-evaluation control words: flagged-row count, fixup counter, set flags
+    // per-evaluation control words: flagged-row count, fixup counter, set flags and bounds
     HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0, sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + ns),
                            s),
            "reset control words");
+    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlSetFlags + ctx->ctl_sets, 0, sizeof(int32_t) * ns, s), "reset bounds");
     HK_TRY(launch_validate_keys(t, X, pl.n_total, pl.x_total, ctx->keys_a, ctx->vals_a, ctx->d_set_ev0, ns,
                                 w.status, s),
            "validate");
@@ -527,6 +535,57 @@ hawkes_status enqueue_eval_reset(hawkes_ctx *ctx, const Plan &pl, cudaStream_t s
     HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0,
                            sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + pl.sets.size()), s),
            "reset control words");
+    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlSetFlags + ctx->ctl_sets, 0, sizeof(int32_t) * pl.sets.size(), s),
+           "reset bounds");
+    return HAWKES_OK;
+}
+
+// One pair pass (1 rates, 2 gradient, 3 rates with Theta sums) over every
+// dimension of the plan.  Each dimension is one persistent launch with its
+// own work counter; with several dimensions the launches run concurrently
+// on forked streams (joined back into s), so that the GPU fills one
+// dimension's tail with another's blocks.
+hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaStream_t s)
+{
+    int ndims = 0;
+    for (int d = 1; d <= kMaxD; ++d)
+        ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
+    const bool fork = ndims > 1;
+    if (fork) {
+        if (!ctx->fork_ev) {
+            HK_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+            for (int d = 1; d <= kMaxD; ++d) {
+                HK_TRY(cudaStreamCreateWithFlags(&ctx->side[d], cudaStreamNonBlocking), "side stream");
+                HK_TRY(cudaEventCreateWithFlags(&ctx->join_ev[d], cudaEventDisableTiming), "join event");
+            }
+        }
+        HK_TRY(cudaEventRecord(ctx->fork_ev, s), "fork");
+    }
+    for (int d = 1; d <= kMaxD; ++d) {
+        const auto rg = pl.item_range_by_d[d];
+        if (rg.second == 0)
+            continue;
+        const int warps = pl.warps_by_d[d];
+        const int grid = persistent_grid(ctx, d, pass, warps, rg.second);
+        Work wd = ctx->w;
+        wd.counters = ctx->ctl + kCtlDimCounters + 2 * d;  // [0] work taken, [1] CTAs done
+        cudaStream_t ls = s;
+        if (fork) {
+            ls = ctx->side[d];
+            HK_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev, 0), "fork wait");
+        }
+        const WorkItem *items = ctx->d_items + rg.first;
+        if (pass == 1)
+            HK_TRY(launch_pass1_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
+        else if (pass == 3)
+            HK_TRY(launch_pass1_theta_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
+        else
+            HK_TRY(launch_pass2_mixed(d, wd, items, rg.second, grid, warps, ls), "gradient pass");
+        if (fork) {
+            HK_TRY(cudaEventRecord(ctx->join_ev[d], ls), "join");
+            HK_TRY(cudaStreamWaitEvent(s, ctx->join_ev[d], 0), "join wait");
+        }
+    }
     return HAWKES_OK;
 }
 
@@ -559,19 +618,13 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         }
         return HAWKES_OK;
     }
-    for (int d = 1; d <= kMaxD; ++d) {
-        const auto rg = pl.item_range_by_d[d];
-        if (rg.second == 0)
-            continue;
-        const int warps = pl.warps_by_d[d];
-        const int grid = persistent_grid(ctx, d, theta ? 3 : 1, warps, rg.second);
+    {
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 0, pl.pairs);
-        if (theta)
-            HK_TRY(launch_pass1_theta_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
-        else
-            HK_TRY(launch_pass1_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "rate pass");
+        hawkes_status st = enqueue_pair_pass(ctx, pl, theta ? 3 : 1, s);
+        if (st != HAWKES_OK)
+            return st;
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
@@ -588,16 +641,13 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     }
     if (!want_grad)
         return HAWKES_OK;
-    for (int d = 1; d <= kMaxD; ++d) {
-        const auto rg = pl.item_range_by_d[d];
-        if (rg.second == 0)
-            continue;
-        const int warps = pl.warps_by_d[d];
-        const int grid = persistent_grid(ctx, d, 2, warps, rg.second);
+    {
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 1, pl.pairs);
-        HK_TRY(launch_pass2_mixed(d, w, ctx->d_items + rg.first, rg.second, grid, warps, s), "gradient pass");
+        hawkes_status st = enqueue_pair_pass(ctx, pl, 2, s);
+        if (st != HAWKES_OK)
+            return st;
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
@@ -691,8 +741,8 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     // control block and a workspace sized for one set of max_n events
-    if (cudaMalloc(&ctx->ctl, sizeof(int32_t) * (kCtlSetFlags + 64)) != cudaSuccess ||
-        cudaMemset(ctx->ctl, 0, sizeof(int32_t) * (kCtlSetFlags + 64)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->ctl, sizeof(int32_t) * (kCtlSetFlags + 2 * 64)) != cudaSuccess ||
+        cudaMemset(ctx->ctl, 0, sizeof(int32_t) * (kCtlSetFlags + 2 * 64)) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         set_err("hawkes_ctx_create: control block allocation failed");
@@ -730,6 +780,13 @@ void hawkes_ctx_destroy(hawkes_ctx *ctx)
     }
     if (ctx->hmc.exec)
         cudaGraphExecDestroy(ctx->hmc.exec);
+    if (ctx->fork_ev) {
+        cudaEventDestroy(ctx->fork_ev);
+        for (int d = 1; d <= kMaxD; ++d) {
+            cudaStreamDestroy(ctx->side[d]);
+            cudaEventDestroy(ctx->join_ev[d]);
+        }
+    }
     if (ctx->ws.ptr)
         cudaFree(ctx->ws.ptr);
     if (ctx->ctl)
@@ -788,6 +845,9 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
         return HAWKES_OK;
     case HAWKES_OPT_TIMES_SORTED:
         ctx->opt_sorted = value ? 1 : 0;
+        return HAWKES_OK;
+    case HAWKES_OPT_SKIP_FAR_BLOCKS:
+        ctx->opt_skip = value ? 1 : 0;
         return HAWKES_OK;
     case HAWKES_OPT_MIXED_FIXUP_EXP:
         if (value < -120 || value > 0)
@@ -904,6 +964,43 @@ static hawkes_status loglik_common(hawkes_ctx *ctx, const double *t, const doubl
     return theta ? enqueue_nan_on_invalid(ctx, out_grad_params, 6, nullptr, 0, s) : HAWKES_OK;
 }
 
+hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
+                                          const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
+                                          double *out_prob)
+{
+    hawkes_status st = check_common(ctx, t, X, n, d, params, prec);
+    if (st != HAWKES_OK)
+        return st;
+    if (!out_prob)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "out_prob must be a device pointer");
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == HAWKES_PREC_FP64;
+    Plan pl;
+    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64, true)) != HAWKES_OK)
+        return st;
+    if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
+        return st;
+    if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
+        return st;
+    // the rate pass with the parameter-gradient sums carries sum_n' xi_nn'
+    const bool theta = true;
+    const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
+    if (fp64) {
+        HK_TRY(launch_pass1_fp64(ctx->w, 0, 1, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, theta, s), "finalize rows");
+        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, 1, nullptr, false, s), "log-likelihood");
+    } else {
+        if ((st = enqueue_pair_pass(ctx, pl, 3, s)) != HAWKES_OK)
+            return st;
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, theta, s), "finalize rows");
+        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, fix_grid, nullptr, theta, s), "FP64 rate fixup");
+    }
+    HK_TRY(launch_self_excitation(ctx->w, pl.total_segs, out_prob, s), "self-excitation");
+    ctx->launches_own += 4;
+    return enqueue_nan_on_invalid(ctx, out_prob, n, nullptr, 0, s);
+}
+
 hawkes_status hawkes_loglik(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
                             const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
                             double *out_loglik)
@@ -940,9 +1037,8 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
         if (pass_smem_bytes(d, 2, wv) > 200 * 1024)
             continue;
         const int max_c = std::max(1, ctx->occ[d][2][wv]);
-        for (int cv = 0; cv <= max_c; ++cv) {
-            if (cv > 0 && cv == max_c)
-                continue;  // the same as "as many as fit"
+        // caps: as many as fit (0), then powers of two below that
+        for (int cv = 0; cv < max_c; cv = cv == 0 ? 1 : 2 * cv) {
             ctx->opt_warps = wv;
             ctx->opt_ctas = cv;
             float ms = 0.0f, tot = 0.0f;
@@ -990,46 +1086,55 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
     return HAWKES_OK;
 }
 
-hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
-                                      const double *box_lo, const double *box_hi, int64_t n, int32_t d,
-                                      const hawkes_params *params, double eps, int32_t n_steps, const double *log_u,
-                                      hawkes_precision prec, hawkes_stream stream, double *out_H0, double *out_H1,
-                                      int32_t *out_accepted)
+// One HMC proposal per set (Section 3), all sets advanced together; the
+// trajectory after the prologue is one CUDA graph cached per shape.
+static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *counts, const int32_t *dims,
+                                const double *t, double *X_inout, const double *p0, const double *box_lo,
+                                const double *box_hi, const hawkes_params *params, const double *eps,
+                                int32_t n_steps, const double *log_u, hawkes_precision prec, hawkes_stream stream,
+                                double *out_H0, double *out_H1, int32_t *out_accepted)
 {
-    hawkes_status st = check_common(ctx, t, X_inout, n, d, params, prec);
-    if (st != HAWKES_OK)
-        return st;
+    hawkes_status st;
     if (!p0 || !log_u || !out_H0 || !out_H1 || !out_accepted)
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "p0, log_u and the outputs must be device pointers");
     if ((box_lo == nullptr) != (box_hi == nullptr))
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "box_lo and box_hi must both be given or both be NULL");
-    if (!(eps > 0.0) || !std::isfinite(eps))
-        return fail(ctx, HAWKES_ERR_INVALID_ARG, "eps must be finite and > 0");
+    for (int k = 0; k < nsets; ++k)
+        if (!(eps[k] > 0.0) || !std::isfinite(eps[k]))
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (n_steps < 0 || n_steps > 100000)
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "n_steps must be in [0, 100000]");
     HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = prec == HAWKES_PREC_FP64;
     Plan pl;
-    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64)) != HAWKES_OK)
+    if ((st = build_plan(ctx, pl, nsets, counts, dims, params, fp64)) != HAWKES_OK)
         return st;
     if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
         return st;
     if ((st = enqueue_prep(ctx, pl, t, X_inout, s)) != HAWKES_OK)
         return st;
     Work &w = ctx->w;
+    const int ns = nsets;
+    double *d_eps = ctx->hscal, *d_logu = ctx->hscal + ns, *d_H0 = ctx->hscal + 2 * ns, *d_H1 = ctx->hscal + 3 * ns;
+    int32_t *d_acc = ctx->hint, *d_bad = ctx->hint + ns;
     HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, p0, ctx->hp, pl.total_rows, 0.0, s), "gather momenta");
     const bool box = box_lo != nullptr;
     if (box) {
         HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, box_lo, ctx->hlo, pl.total_rows, 0.0, s), "gather box");
         HK_TRY(launch_gather_sorted(w, ctx->d_set_row0, box_hi, ctx->hhi, pl.total_rows, 0.0, s), "gather box");
     }
-    HK_TRY(launch_set_scalar(ctx->hscal + 0, eps, s), "step size");
-    HK_TRY(cudaMemcpyAsync(ctx->hscal + 1, log_u, sizeof(double), cudaMemcpyDeviceToDevice, s), "log u");
-    HK_TRY(cudaMemsetAsync(ctx->hint, 0, sizeof(int32_t) * 2, s), "flags");
+    HK_TRY(cudaMemcpyAsync(d_eps, eps, sizeof(double) * ns, cudaMemcpyHostToDevice, s), "step sizes");
+    HK_TRY(cudaMemcpyAsync(d_logu, log_u, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s), "log u");
+    HK_TRY(cudaMemsetAsync(ctx->hint, 0, sizeof(int32_t) * 2 * ns, s), "flags");
 
     // the trajectory itself: captured once per shape, replayed as a graph
-    const auto key = std::make_tuple((int64_t)n, d, n_steps, (int32_t)prec, box, ctx->ws_generation);
+    std::vector<int64_t> key = {n_steps, (int64_t)prec, box ? 1 : 0, (int64_t)ctx->ws_generation, ns};
+    for (int k = 0; k < ns; ++k) {
+        key.push_back(counts[k]);
+        key.push_back(dims[k]);
+        key.push_back(pl.sets[k].B);
+    }
     if (!ctx->hmc.exec || ctx->hmc.key != key || ctx->opt_profile) {
         if (ctx->hmc.exec) {
             cudaGraphExecDestroy(ctx->hmc.exec);
@@ -1041,18 +1146,17 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
         cudaStream_t es = capture ? cs : s;
         if (capture)
             HK_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-        hawkes_status st2 = HAWKES_OK;
         auto body = [&]() -> hawkes_status {
             hawkes_status r;
             if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                 return r;
             if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
                 return r;
-            HK_TRY(launch_energy(w, ctx->hp, ctx->hscal + 2, es), "H0");
+            HK_TRY(launch_energy(w, ctx->hp, d_H0, es), "H0");
             for (int32_t k = 0; k < n_steps; ++k) {
                 HK_TRY(launch_kick_drift(w, ctx->d_set_row0, ctx->hp, ctx->hg, box ? ctx->hlo : nullptr,
-                                         box ? ctx->hhi : nullptr, ctx->hscal, pl.total_rows, k == 0 ? 1 : 2, !fp64,
-                                         ctx->hint + 1, es),
+                                         box ? ctx->hhi : nullptr, d_eps, pl.total_rows, k == 0 ? 1 : 2, !fp64,
+                                         d_bad, es),
                        "leapfrog drift");
                 if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                     return r;
@@ -1060,17 +1164,15 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
                     return r;
             }
             if (n_steps > 0)
-                HK_TRY(launch_kick(w, ctx->d_set_row0, ctx->hp, ctx->hg, ctx->hscal, pl.total_rows, es),
-                       "leapfrog kick");
-            HK_TRY(launch_energy(w, ctx->hp, ctx->hscal + 3, es), "H1");
-            HK_TRY(launch_accept(ctx->hscal + 2, ctx->hscal + 3, ctx->hscal + 1, ctx->hint + 1, ctx->hint, es),
-                   "accept");
+                HK_TRY(launch_kick(w, ctx->d_set_row0, ctx->hp, ctx->hg, d_eps, pl.total_rows, es), "leapfrog kick");
+            HK_TRY(launch_energy(w, ctx->hp, d_H1, es), "H1");
+            HK_TRY(launch_accept(d_H0, d_H1, d_logu, d_bad, d_acc, ns, es), "accept");
             return HAWKES_OK;
         };
         if (capture) {
             // capture only records; the graph later runs on s after the prologue
             cudaGraph_t graph = nullptr;
-            st2 = body();
+            hawkes_status st2 = body();
             cudaError_t ce = cudaStreamEndCapture(cs, &graph);
             if (st2 != HAWKES_OK) {
                 if (graph)
@@ -1092,17 +1194,60 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
             ctx->hmc.key = key;
         } else {
             cudaStreamDestroy(cs);
-            if ((st2 = body()) != HAWKES_OK)
+            hawkes_status st2 = body();
+            if (st2 != HAWKES_OK)
                 return st2;
         }
     }
     if (ctx->hmc.exec && !ctx->opt_profile)
         HK_TRY(cudaGraphLaunch(ctx->hmc.exec, s), "launch trajectory graph");
-    HK_TRY(launch_scatter(w, ctx->d_set_row0, w.x64, X_inout, ctx->hint, pl.total_rows, s), "write back");
-    HK_TRY(cudaMemcpyAsync(out_H0, ctx->hscal + 2, sizeof(double), cudaMemcpyDeviceToDevice, s), "H0 out");
-    HK_TRY(cudaMemcpyAsync(out_H1, ctx->hscal + 3, sizeof(double), cudaMemcpyDeviceToDevice, s), "H1 out");
-    HK_TRY(cudaMemcpyAsync(out_accepted, ctx->hint, sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "accept out");
+    HK_TRY(launch_scatter(w, ctx->d_set_row0, w.x64, X_inout, d_acc, pl.total_rows, s), "write back");
+    HK_TRY(cudaMemcpyAsync(out_H0, d_H0, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s), "H0 out");
+    HK_TRY(cudaMemcpyAsync(out_H1, d_H1, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s), "H1 out");
+    HK_TRY(cudaMemcpyAsync(out_accepted, d_acc, sizeof(int32_t) * ns, cudaMemcpyDeviceToDevice, s), "accept out");
     return HAWKES_OK;
+}
+
+hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
+                                      const double *box_lo, const double *box_hi, int64_t n, int32_t d,
+                                      const hawkes_params *params, double eps, int32_t n_steps, const double *log_u,
+                                      hawkes_precision prec, hawkes_stream stream, double *out_H0, double *out_H1,
+                                      int32_t *out_accepted)
+{
+    hawkes_status st = check_common(ctx, t, X_inout, n, d, params, prec);
+    if (st != HAWKES_OK)
+        return st;
+    return hmc_common(ctx, 1, &n, &d, t, X_inout, p0, box_lo, box_hi, params, &eps, n_steps, log_u, prec, stream,
+                      out_H0, out_H1, out_accepted);
+}
+
+hawkes_status hawkes_batch_hmc_trajectory(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets,
+                                          const int32_t *dims, const double *t, double *X_inout, const double *p0,
+                                          const double *box_lo, const double *box_hi, const hawkes_params *params,
+                                          const double *eps, int32_t n_steps, const double *log_u,
+                                          hawkes_precision prec, hawkes_stream stream, double *out_H0,
+                                          double *out_H1, int32_t *out_accepted)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (n_sets < 1 || !offsets || !dims || !params || !eps || !t || !X_inout)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "invalid batch arguments");
+    if (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "unknown precision");
+    if (offsets[0] != 0)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "offsets[0] must be 0");
+    std::vector<int64_t> counts(n_sets);
+    for (int k = 0; k < n_sets; ++k) {
+        counts[k] = offsets[k + 1] - offsets[k];
+        if (counts[k] < 1 || counts[k] > (int64_t)1 << 30)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "every set needs at least one event");
+        if (dims[k] < 1 || dims[k] > kMaxD)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "dims must be in [1, 8]");
+        if (!params_ok(&params[k]))
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "every parameter must be finite and > 0");
+    }
+    return hmc_common(ctx, n_sets, counts.data(), dims, t, X_inout, p0, box_lo, box_hi, params, eps, n_steps, log_u,
+                      prec, stream, out_H0, out_H1, out_accepted);
 }
 
 hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets, const int32_t *dims,

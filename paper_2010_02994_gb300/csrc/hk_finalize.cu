@@ -184,6 +184,15 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
                 atomicOr(&w.set_flags[s], 1);
         }
     }
+    // bound on the gradient pass's column constants (for block skipping)
+    if (!fp64) {
+        float cmv = (active && !flagged) ? fmaxf(w.cm32[S.row0 + i], 0.0f) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            cmv = fmaxf(cmv, __shfl_xor_sync(0xffffffffu, cmv, o));
+        if ((threadIdx.x & 31) == 0 && cmv > 0.0f)
+            atomicMax(&w.set_cmmax[s], __float_as_int(cmv));
+    }
     // flagged rows of this segment, in row order
     const unsigned ball = __ballot_sync(0xffffffffu, flagged);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -498,6 +507,21 @@ __global__ void __launch_bounds__(kT) theta_grad_kernel(Work w, double *out6)
     }
 }
 
+// xi_n / lambda_n per event in the caller's order (the self-excitation
+// probability of an event under the current state).
+__global__ void self_excitation_kernel(Work w, double *out)
+{
+    const int g = blockIdx.x;
+    const int s = set_of_segment(w, g);
+    const SetDesc &S = w.sets[s];
+    const int i = (g - S.seg0) * kT + threadIdx.x;
+    if (i >= S.n)
+        return;
+    const int64_t r = S.row0 + i;
+    const double lam = w.lam64[r];
+    out[S.ev0 + w.perm[r]] = lam > 0.0 ? w.theta_rows[r * kPass1ThetaVals + 1] / lam : nan("");
+}
+
 __global__ void fill_nan_kernel(double *p, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -536,6 +560,12 @@ cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, d
 cudaError_t launch_theta_grad(const Work &w, double *out6, cudaStream_t s)
 {
     theta_grad_kernel<<<1, kT, 0, s>>>(w, out6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_self_excitation(const Work &w, int32_t total_segs, double *out, cudaStream_t s)
+{
+    self_excitation_kernel<<<total_segs, kT, 0, s>>>(w, out);
     return cudaGetLastError();
 }
 

@@ -77,15 +77,16 @@ __global__ void kick_drift_kernel(Work w, const int64_t *set_row0, double *__res
                                   const double *__restrict__ hi, const double *__restrict__ eps_dev,
                                   int64_t total_rows, int kicks, int repack, int32_t *refl_bad)
 {
-    const double eps = *eps_dev;
-    const double half = __dmul_rn(0.5, eps);
-    bool bad = false;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const SetDesc &S = w.sets[set_of_row(w, set_row0, r)];
+        const int set = set_of_row(w, set_row0, r);
+        const SetDesc &S = w.sets[set];
         const int64_t i = r - S.row0;
         if (i >= S.n)
             continue;
+        const double eps = eps_dev[set];
+        const double half = __dmul_rn(0.5, eps);
+        bool bad = false;
         float f[2 * kMaxD];
         for (int k = 0; k < S.d; ++k) {
             const int64_t e = r * kMaxD + k;
@@ -111,20 +112,21 @@ __global__ void kick_drift_kernel(Work w, const int64_t *set_row0, double *__res
                 w.rec[S.rec0 + (int64_t)pl * S.npad + i] = v;
             }
         }
+        if (bad)
+            atomicOr(&refl_bad[set], 1);
     }
-    if (bad)
-        atomicOr(refl_bad, 1);
 }
 
 __global__ void kick_kernel(Work w, const int64_t *set_row0, double *__restrict__ p, const double *__restrict__ g,
                             const double *__restrict__ eps_dev, int64_t total_rows)
 {
-    const double half = __dmul_rn(0.5, *eps_dev);
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const SetDesc &S = w.sets[set_of_row(w, set_row0, r)];
+        const int set = set_of_row(w, set_row0, r);
+        const SetDesc &S = w.sets[set];
         if (r - S.row0 >= S.n)
             continue;
+        const double half = __dmul_rn(0.5, eps_dev[set]);
         for (int k = 0; k < S.d; ++k) {
             const int64_t e = r * kMaxD + k;
             p[e] = __dadd_rn(p[e], __dmul_rn(half, g[e]));
@@ -132,11 +134,11 @@ __global__ void kick_kernel(Work w, const int64_t *set_row0, double *__restrict_
     }
 }
 
-// H = -ell + sum p^2/2 for set 0 (one CTA, fixed-order reduction).
+// H = -ell + sum p^2/2 of every set (one CTA per set, fixed-order reduction).
 __global__ void __launch_bounds__(1024) energy_kernel(Work w, const double *__restrict__ p, double *H_out)
 {
     __shared__ double sh[1024];
-    const SetDesc &S = w.sets[0];
+    const SetDesc &S = w.sets[blockIdx.x];
     double s = 0.0, c = 0.0;
     for (int64_t i = threadIdx.x; i < (int64_t)S.n * S.d; i += blockDim.x) {
         const int64_t r = S.row0 + i / S.d;
@@ -154,26 +156,28 @@ __global__ void __launch_bounds__(1024) energy_kernel(Work w, const double *__re
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        *H_out = -w.set_loglik[0] + sh[0];
+        H_out[blockIdx.x] = -w.set_loglik[blockIdx.x] + sh[0];
 }
 
 __global__ void accept_kernel(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
-                              int32_t *accepted)
+                              int32_t *accepted, int nsets)
 {
-    const double h0 = *H0, h1 = *H1;
-    *accepted = (*refl_bad == 0 && isfinite(h0) && isfinite(h1) && *log_u < h0 - h1) ? 1 : 0;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsets)
+        return;
+    const double h0 = H0[s], h1 = H1[s];
+    accepted[s] = (refl_bad[s] == 0 && isfinite(h0) && isfinite(h1) && log_u[s] < h0 - h1) ? 1 : 0;
 }
 
 __global__ void scatter_kernel(Work w, const int64_t *set_row0, const double *__restrict__ Xs,
                                double *__restrict__ X_out, const int32_t *__restrict__ accepted, int64_t total_rows)
 {
-    if (*accepted == 0)
-        return;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const SetDesc &S = w.sets[set_of_row(w, set_row0, r)];
+        const int set = set_of_row(w, set_row0, r);
+        const SetDesc &S = w.sets[set];
         const int64_t i = r - S.row0;
-        if (i >= S.n)
+        if (i >= S.n || accepted[set] == 0)
             continue;
         for (int k = 0; k < S.d; ++k)
             X_out[S.x0 + (int64_t)w.perm[r] * S.d + k] = Xs[r * kMaxD + k];
@@ -219,14 +223,14 @@ cudaError_t launch_kick(const Work &w, const int64_t *set_row0, double *p, const
 
 cudaError_t launch_energy(const Work &w, const double *p, double *H_out, cudaStream_t s)
 {
-    energy_kernel<<<1, 1024, 0, s>>>(w, p, H_out);
+    energy_kernel<<<w.nsets, 1024, 0, s>>>(w, p, H_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_accept(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
-                          int32_t *accepted, cudaStream_t s)
+                          int32_t *accepted, int nsets, cudaStream_t s)
 {
-    accept_kernel<<<1, 1, 0, s>>>(H0, H1, log_u, refl_bad, accepted);
+    accept_kernel<<<(nsets + 127) / 128, 128, 0, s>>>(H0, H1, log_u, refl_bad, accepted, nsets);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,8 @@ struct Work {
     double *seg_sum;     // each finalize CTA's sum of lnl over its unflagged rows
     double *set_loglik;  // ell per set
     int32_t *set_flags;  // bit 0: some rate of the set is zero
+    int32_t *set_cmmax;  // per set: max(0, max_n cm32[n]) as float bits (gradient-pass skip bound)
+    int32_t skip_far;    // skip pair blocks whose kernel values all underflow
     int32_t *counters;   // [0] work items taken, [1] CTAs done, [2] flagged rows, [3] fixup CTAs done
     unsigned *status;    // sticky device status
 };
@@ -152,6 +154,7 @@ cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, d
 cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,
                               cudaStream_t s);
 cudaError_t launch_fill_nan(double *p, int64_t n, cudaStream_t s);
+cudaError_t launch_self_excitation(const Work &w, int32_t total_segs, double *out, cudaStream_t s);
 
 // hk_hmc.cu
 cudaError_t launch_gather_sorted(const Work &w, const int64_t *set_row0, const double *src, double *dst,
@@ -163,7 +166,7 @@ cudaError_t launch_kick(const Work &w, const int64_t *set_row0, double *p, const
                         int64_t total_rows, cudaStream_t s);
 cudaError_t launch_energy(const Work &w, const double *p, double *H_out, cudaStream_t s);
 cudaError_t launch_accept(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
-                          int32_t *accepted, cudaStream_t s);
+                          int32_t *accepted, int nsets, cudaStream_t s);
 cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s);
 cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s);

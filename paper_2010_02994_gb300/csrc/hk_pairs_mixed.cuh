@@ -229,6 +229,30 @@ __global__ void __launch_bounds__(256) pair_kernel(Work w, const WorkItem *__res
             oh = c[(2 * D) % 4];
             ol = c[(2 * D) % 4 + 1];
         }
+        // Optional skip of a block that is far apart in time: if even its
+        // closest pair has both exponents <= -130, every kernel value of the
+        // block flushes to zero in FP32 and its partials are exactly zero.
+        if (w.skip_far && I != J) {
+            const int il = min(I * B + B - 1, n - 1), jf = J * B;
+            const float4 vl = rec[(int64_t)((2 * D) / 4) * npad + il];
+            const float4 vf = rec[(int64_t)((2 * D) / 4) * npad + jf];
+            const float *cl = reinterpret_cast<const float *>(&vl);
+            const float *cf0 = reinterpret_cast<const float *>(&vf);
+            const float dtmin = ((cf0[(2 * D) % 4] - oh) + (cf0[(2 * D) % 4 + 1] - ol)) -
+                                ((cl[(2 * D) % 4] - oh) + (cl[(2 * D) % 4 + 1] - ol));
+            const float cmax = KIND == kGrad ? __int_as_float(w.set_cmmax[wi.set]) : kc.cxi;
+            if (dtmin * dtmin >= 130.0f && cmax - kc.kappa * dtmin <= -130.0f) {
+                float *P = (KIND == kGrad ? w.P2 + S.part2_0 : w.P1 + S.part0);
+                for (int c = threadIdx.x; c < B; c += blockDim.x)
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        P[((int64_t)J * VC + v) * npad + (int64_t)I * B + c] = 0.0f;
+                        P[((int64_t)I * VC + v) * npad + (int64_t)J * B + c] = 0.0f;
+                    }
+                __syncthreads();
+                continue;
+            }
+        }
         // this lane's rows
         float rx[R][2 * D], rt[R], rw[R], part[R][VR], rs[R][VR], rc[R][VR];
         const int rbase = I * B + warp * 32 * R;

@@ -70,3 +70,43 @@ def save(entries: list, device: int = 0, path: str = DEFAULT_PATH) -> None:
     with open(tmp, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
     os.replace(tmp, path)
+
+
+def _random_events(n: int, d: int, seed: int, device):
+    """Uniform events: the pair kernels' cost does not depend on the values."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    t = torch.sort(torch.rand(n, generator=g, dtype=torch.float64) * 365.0).values
+    X = torch.rand(n, d, generator=g, dtype=torch.float64) * 20.0
+    return t.to(device), X.to(device)
+
+
+def main(argv=None) -> int:
+    """Tune every (dimension, size) pair given and merge the results into a table:
+        python -m paper_2010_02994_gb300.tuning --d 1 2 4 8 --n 1000 10000 100000 --out tuning.json"""
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--d", type=int, nargs="+", default=[1, 2, 3, 4, 5, 6, 7, 8])
+    ap.add_argument("--n", type=int, nargs="+",
+                    default=[600, 1000, 2000, 4000, 8000, 16000, 32000, 64000, 100000])
+    ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--out", default=DEFAULT_PATH)
+    args = ap.parse_args(argv)
+    params = {"mu0": 0.5, "tau_x": 1.0, "tau_t": 14.0, "theta": 0.5, "omega": 0.5, "h": 0.1}
+    ctx = HawkesContext(device=args.device, max_n=max(args.n), max_d=max(args.d), tuning=False)
+    entries = []
+    dev = torch.device("cuda", args.device)
+    for d in args.d:
+        for n in args.n:
+            t, X = _random_events(n, d, 17 * d + n, dev)
+            e = autotune(ctx, t, X, params)
+            entries.append(e)
+            print(f"d={d} n={n} bucket={e['bucket']}: warps={e['warps']} ctas/SM={e['ctas_per_sm']} "
+                  f"{e['ms']:.4f} ms", flush=True)
+    save(entries, args.device, args.out)
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

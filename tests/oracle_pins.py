@@ -44,9 +44,10 @@ def _rel(a, b):
 
 # ------------------------------------------------------------ brute force --
 
-def free_point_rate(x, t, T_ev, X_ev, P):
+def free_point_rate(x, t, T_ev, X_ev, P, parts=False):
     """lambda(x, t) = mu(x, t) + xi(x, t) evaluated at a free point, with the
-    sums of Section 2.1 and scipy's standard normal densities."""
+    sums of Section 2.1 and scipy's standard normal densities (parts=True
+    returns (mu, xi))."""
     D = X_ev.shape[1]
     mvn = stats.multivariate_normal(mean=np.zeros(D), cov=np.eye(D))
     mu = 0.0
@@ -56,7 +57,9 @@ def free_point_rate(x, t, T_ev, X_ev, P):
             mu += mvn.pdf((x - X_ev[n]) / P["tau_x"]) * stats.norm.pdf((t - T_ev[n]) / P["tau_t"])
         if T_ev[n] < t:
             xi += math.exp(-P["omega"] * (t - T_ev[n])) * mvn.pdf((x - X_ev[n]) / P["h"])
-    return (P["mu0"] / (P["tau_x"] ** D * P["tau_t"])) * mu + (P["theta"] * P["omega"] / P["h"] ** D) * xi
+    mu_v = (P["mu0"] / (P["tau_x"] ** D * P["tau_t"])) * mu
+    xi_v = (P["theta"] * P["omega"] / P["h"] ** D) * xi
+    return (mu_v, xi_v) if parts else mu_v + xi_v
 
 
 def quad_Lambda_time(T_ev, P):
@@ -111,6 +114,18 @@ def pin_brute_force(o):
         worst = max(worst, abs(ell - ref_ell) / abs(ref_ell))
     ok = worst_rate < 1e-13 and worst < 1e-9 and zero_ok
     return ok, f"rates {worst_rate:.3e}, Lambda/ell {worst:.3e}, zero-rate case ok={zero_ok}"
+
+
+def pin_rate_parts(o):
+    """The background and self-excitation parts of lambda_n separately (they
+    give the self-excitation probability xi / (xi + mu) of an event)."""
+    worst = 0.0
+    for seed, n, d, ties in ((30, 7, 2, 1), (31, 6, 1, 0), (32, 8, 3, 2)):
+        w = synth.random_case(seed, n, d, ties=ties, shuffle=True, extent=2.0, t_end=4.0)
+        lam, mu, xi = o.rates(w.t, w.X, w.params, parts=True)
+        ref = np.array([free_point_rate(w.X[i], w.t[i], w.t, w.X, w.params, parts=True) for i in range(n)])
+        worst = max(worst, _rel(mu, ref[:, 0]), _rel(xi, ref[:, 1]), _rel(lam, mu + xi))
+    return worst < 1e-13, f"max rel err {worst:.3e}"
 
 
 def pin_space_time_quadrature(o):
@@ -359,6 +374,7 @@ def pin_hmc_accept_rule(o):
 ALL_PINS = {
     "brute_force": pin_brute_force,
     "space_time_quadrature": pin_space_time_quadrature,
+    "rate_parts": pin_rate_parts,
     "symbolic_pair": pin_symbolic_pair,
     "finite_diff_locations": pin_finite_diff_locations,
     "finite_diff_params": pin_finite_diff_params,

@@ -129,3 +129,44 @@ def test_batch_matches_per_set_oracle(ctx, prec):
         off += w.n * w.d
         assert abs(ell[i] - e_ref) <= tl * abs(e_ref)
         assert np.linalg.norm(gi - g_ref) <= tg * np.linalg.norm(g_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_hmc_matches_per_set_oracle(ctx, prec):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_batch_hmc_trajectory
+
+    specs = [(200, 2), (350, 4), (120, 8), (500, 2), (90, 3)]
+    sets, p0s, los, his = [], [], [], []
+    for i, (n, d) in enumerate(specs):
+        w, lo, hi, p0 = hmc_case(300 + i, n, d, True)
+        sets.append(w)
+        p0s.append(p0)
+        los.append(lo)
+        his.append(hi)
+    eps = [0.01, 0.008, 0.012, 0.01, 0.009]
+    refs = [oracle.hmc_trajectory(w.t, w.X, p0, w.params, e, 12, -np.inf, lo, hi)
+            for w, p0, lo, hi, e in zip(sets, p0s, los, his, eps)]
+    # set 3 gets a log u above its energy gain: it must be rejected
+    log_u = [-np.inf, -np.inf, -np.inf, refs[3]["H0"] - refs[3]["H1"] + 1.0, -np.inf]
+    cat = lambda arrs: torch.tensor(np.concatenate([a.reshape(-1) for a in arrs]), device="cuda")
+    t = torch.tensor(np.concatenate([w.t for w in sets]), device="cuda")
+    X = cat([w.X for w in sets])
+    H0, H1, acc = hawkes_batch_hmc_trajectory(ctx, [w.n for w in sets], [w.d for w in sets], t, X, cat(p0s),
+                                              [w.params for w in sets], eps, 12,
+                                              torch.tensor(log_u, dtype=torch.float64, device="cuda"), cat(los),
+                                              cat(his), precision=prec)
+    H0, H1, acc, X = H0.cpu().numpy(), H1.cpu().numpy(), acc.cpu().numpy(), X.cpu().numpy()
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    off = 0
+    for i, (w, ref) in enumerate(zip(sets, refs)):
+        Xi = X[off:off + w.n * w.d].reshape(w.n, w.d)
+        off += w.n * w.d
+        assert abs(H0[i] - ref["H0"]) <= tol * abs(ref["H0"])
+        assert abs(H1[i] - ref["H1"]) <= tol * abs(ref["H1"])
+        if i == 3:
+            assert acc[i] == 0 and np.array_equal(Xi, w.X)
+        else:
+            assert acc[i] == 1
+            assert np.max(np.abs(Xi - ref["X"])) <= tol * max(1.0, np.max(np.abs(ref["X"])))

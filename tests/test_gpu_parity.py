@@ -231,3 +231,18 @@ def test_times_sorted_option(ctx):
             gpu_eval(ctx, ws, "mixed")
     finally:
         ctx.set_option("times_sorted", 0)
+
+
+@pytest.mark.parametrize("make", [synth.make_c5, synth.make_c3])
+def test_far_block_skipping_is_exact(ctx, make):
+    """Blocks whose closest pair already underflows FP32 contribute exactly
+    zero, so skipping them must reproduce the dense result bit for bit."""
+    w = make()
+    dense = gpu_eval(ctx, w, "mixed")
+    ctx.set_option("skip_far_blocks", 1)
+    try:
+        skipped = gpu_eval(ctx, w, "mixed")
+    finally:
+        ctx.set_option("skip_far_blocks", 0)
+    assert skipped[0] == dense[0]
+    assert np.array_equal(skipped[1], dense[1])

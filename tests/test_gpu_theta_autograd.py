@@ -107,3 +107,19 @@ def test_location_gradient_against_finite_differences_of_gpu_loglik(ctx):
                 vals.append(hawkes_loglik(ctx, t, torch.tensor(X, device="cuda"), w.params, precision="fp64").item())
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - g[i, k]) <= 1e-5 * max(1.0, abs(g[i, k]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_self_excitation_probability(ctx, prec):
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_self_excitation_prob
+
+    for w in (synth.random_case(71, 1200, 2, ties=2, shuffle=True), synth.make_c3()):
+        lam, mu, xi = oracle.rates(w.t, w.X, w.params, parts=True)
+        ref = xi / lam
+        got = hawkes_self_excitation_prob(ctx, torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"),
+                                          w.params, precision=prec).cpu().numpy()
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert np.max(np.abs(got - ref)) <= tol
+        assert np.all((got >= 0) & (got <= 1))
