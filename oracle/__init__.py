@@ -71,6 +71,8 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_hmc_trajectory.argtypes = [i64, i32, dp, dp, dp, dp, dp, pp, ctypes.c_double, i32,
                                           ctypes.c_double, dp, dp, dp, dp,
                                           ctypes.POINTER(ctypes.c_int32), i32]
+    lib.oracle_bmds.argtypes = [i64, i32, dp, dp, ctypes.c_double, dp, dp, dp, i32]
+    lib.oracle_bmds.restype = ctypes.c_int
     lib.oracle_max_threads.restype = i32
     for name in ("oracle_rates", "oracle_rates_rows", "oracle_loglik", "oracle_grad_locations",
                  "oracle_grad_rows", "oracle_grad_params", "oracle_hmc_trajectory"):
@@ -228,6 +230,21 @@ class Oracle:
                                               _dp(H0), _dp(H1), ctypes.byref(acc), nthreads), "hmc_trajectory")
         return {"X": Xo, "p": po, "H0": float(H0[0]), "H1": float(H1[0]), "accepted": int(acc.value)}
 
+    def bmds(self, Y, X, sigma2, nthreads: int = 0):
+        """BMDS log-likelihood of Eq. (4) (up to a constant), its gradient in X
+        and in sigma2: (ell, grad (N, D), d ell / d sigma2)."""
+        X = _as_f64(X)
+        if X.ndim == 1:
+            X = X.reshape(-1, 1)
+        n, d = X.shape
+        Y = _as_f64(Y).reshape(n, n)
+        out = np.empty(1)
+        g = np.empty((n, d))
+        gs = np.empty(1)
+        _check(self.lib.oracle_bmds(n, d, _dp(Y), _dp(X), float(sigma2), _dp(out), _dp(g), _dp(gs), nthreads),
+               "bmds")
+        return float(out[0]), g, float(gs[0])
+
     def max_threads(self) -> int:
         """Threads an OpenMP region of the oracle uses by default."""
         return int(self.lib.oracle_max_threads())
@@ -279,6 +296,10 @@ def loglik_and_grad(*a, **k):
 
 def hmc_trajectory(*a, **k):
     return default().hmc_trajectory(*a, **k)
+
+
+def bmds(*a, **k):
+    return default().bmds(*a, **k)
 
 
 def max_threads() -> int:

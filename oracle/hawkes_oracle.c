@@ -532,6 +532,90 @@ int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
     return ORACLE_OK;
 }
 
+/* ----------------------------------------------------------------- BMDS -- */
+
+/*
+ * Bayesian multidimensional scaling likelihood of Section 2.2.3, Eq. (4):
+ * observed distances y_nn' (n > n') are truncated normals around the latent
+ * distances delta_nn' = |x_n - x_n'| with variance sigma2, so up to an
+ * additive constant
+ *   ell_B = N (1 - N) / 4 log(sigma2) - sum_{n > n'} r_nn',
+ *   r_nn' = (y_nn' - delta_nn')^2 / (2 sigma2) + log Phi(delta_nn' / sigma).
+ * Y is N x N row-major; only the entries below the diagonal (n > n') are
+ * read.  grad (nullable) receives d ell_B / d x_n:
+ *   -sum_{n' != n} dr/d delta (x_n - x_n') / delta,
+ *   dr/d delta = -(y - delta)/sigma2 + phi(delta/sigma) / (sigma Phi(delta/sigma)),
+ * and grad_sigma2 (nullable) d ell_B / d sigma2:
+ *   N (1 - N) / (4 sigma2) + sum (y - delta)^2 / (2 sigma2^2)
+ *   + sum phi(delta/sigma) delta / (2 sigma^3 Phi(delta/sigma)).
+ */
+static double bmds_y(const double *Y, int64_t n, int64_t a, int64_t b)
+{
+    return a > b ? Y[a * n + b] : Y[b * n + a];
+}
+
+int oracle_bmds(int64_t n, int32_t d, const double *Y, const double *X, double sigma2, double *out_loglik,
+                double *grad, double *grad_sigma2, int32_t nthreads)
+{
+    if (n < 1 || d < 1 || d > 64 || !Y || !X || !out_loglik || !(sigma2 > 0) || !isfinite(sigma2))
+        return ORACLE_ERR_ARG;
+    const double sigma = sqrt(sigma2);
+    double *row_r = (double *)malloc(sizeof(double) * n);
+    double *row_s = (double *)malloc(sizeof(double) * n);
+    if (!row_r || !row_s) {
+        free(row_r);
+        free(row_s);
+        return ORACLE_ERR_ARG;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        nsum r = {0, 0}, ss = {0, 0};
+        nsum g[64];
+        for (int k = 0; k < d; ++k)
+            g[k].s = g[k].c = 0.0;
+        for (int64_t m = 0; m < n; ++m) {
+            if (m == i)
+                continue;
+            const double delta = sqrt(sqdist(d, X + i * d, X + m * d));
+            const double y = bmds_y(Y, n, i, m);
+            const double z = delta / sigma;
+            const double Phi_z = Phi(z);
+            const double ratio = phi_d(z * z, 1) / Phi_z;
+            if (m < i) {  /* each unordered pair once for the value */
+                nadd(&r, (y - delta) * (y - delta) / (2.0 * sigma2) + log(Phi_z));
+                nadd(&ss, (y - delta) * (y - delta) / (2.0 * sigma2 * sigma2) + ratio * delta / (2.0 * sigma2 * sigma));
+            }
+            if (grad) {
+                const double drdd = -(y - delta) / sigma2 + ratio / sigma;
+                for (int k = 0; k < d; ++k)
+                    nadd(&g[k], -drdd * (X[i * d + k] - X[m * d + k]) / delta);
+            }
+        }
+        row_r[i] = nval(&r);
+        row_s[i] = nval(&ss);
+        if (grad)
+            for (int k = 0; k < d; ++k)
+                grad[i * d + k] = nval(&g[k]);
+    }
+    (void)nthreads;
+    nsum tot = {0, 0}, tots = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        nadd(&tot, row_r[i]);
+        nadd(&tots, row_s[i]);
+    }
+    const double c = (double)n * (1.0 - (double)n) / 4.0;
+    *out_loglik = c * log(sigma2) - nval(&tot);
+    if (grad_sigma2)
+        *grad_sigma2 = c / sigma2 + nval(&tots);
+    free(row_r);
+    free(row_s);
+    return ORACLE_OK;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int32_t oracle_max_threads(void)
 {

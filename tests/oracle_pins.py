@@ -371,6 +371,89 @@ def pin_hmc_accept_rule(o):
     return ok, f"dH={dh:.3e} acc={a['accepted']} rej={r['accepted']}"
 
 
+# ----------------------------------------------------------------- BMDS --
+
+def bmds_case(seed, n, d, noise=0.2):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, d))
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    Y = np.abs(D + noise * rng.normal(size=(n, n))) + 0.05
+    Y = np.tril(Y, -1) + np.tril(Y, -1).T
+    Xl = X + 0.1 * rng.normal(size=X.shape)   # latent locations differ from the truth
+    return Y, Xl
+
+
+def pin_bmds_symbolic_pair(o):
+    """Two points written out by hand (Eq. (4) with N = 2) and differentiated by sympy."""
+    import sympy as sp
+
+    y, s2 = sp.symbols("y sigma2", positive=True)
+    xs = sp.symbols("a0 a1 b0 b1", real=True)
+    delta = sp.sqrt((xs[0] - xs[2]) ** 2 + (xs[1] - xs[3]) ** 2)
+    sigma = sp.sqrt(s2)
+    Phi = lambda z: sp.erfc(-z / sp.sqrt(2)) / 2
+    ell = sp.Rational(2 * (1 - 2), 4) * sp.log(s2) - ((y - delta) ** 2 / (2 * s2) + sp.log(Phi(delta / sigma)))
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(2, 2))
+    yv, s2v = 0.9, 0.35
+    subs = {y: yv, s2: s2v, xs[0]: X[0, 0], xs[1]: X[0, 1], xs[2]: X[1, 0], xs[3]: X[1, 1]}
+    ev = lambda e: float(sp.N(e.subs(subs), 40))
+    val = ev(ell)
+    gX = np.array([ev(sp.diff(ell, v)) for v in xs]).reshape(2, 2)
+    gs = ev(sp.diff(ell, s2))
+    Y = np.array([[0.0, yv], [yv, 0.0]])
+    e, g, gso = o.bmds(Y, X, s2v)
+    err = max(abs(e - val) / abs(val), _rel(g, gX), abs(gso - gs) / abs(gs))
+    return err < 1e-12, f"max rel err {err:.3e}"
+
+
+def pin_bmds_pair_density(o):
+    """With N = 2, exp(ell) as a function of the observed distance y is
+    sqrt(2 pi) times a normalized truncated normal density on y > 0."""
+    X = np.array([[0.0, 0.0], [0.7, 0.2]])
+    worst = 0.0
+    for s2v in (0.05, 0.4, 2.0):
+        f = lambda yv: math.exp(o.bmds(np.array([[0.0, yv], [yv, 0.0]]), X, s2v)[0])
+        val, _ = integrate.quad(f, 0.0, np.inf, limit=200, epsabs=1e-13, epsrel=1e-12)
+        worst = max(worst, abs(val - math.sqrt(2 * math.pi)) / math.sqrt(2 * math.pi))
+    return worst < 1e-9, f"max rel err {worst:.3e}"
+
+
+def pin_bmds_finite_diff(o):
+    worst = 0.0
+    for seed, n, d in ((1, 9, 2), (2, 7, 3), (3, 8, 1)):
+        Y, X = bmds_case(seed, n, d)
+        s2v = 0.3
+        e, g, gs = o.bmds(Y, X, s2v)
+        fd = np.zeros_like(g)
+        for i in range(n):
+            for k in range(d):
+                def f(v, i=i, k=k):
+                    Xp = X.copy()
+                    Xp[i, k] = v
+                    return o.bmds(Y, Xp, s2v)[0]
+                fd[i, k] = _fd4(f, X[i, k], 1e-5)
+        fds = _fd4(lambda v: o.bmds(Y, X, v)[0], s2v, 1e-5)
+        worst = max(worst, float(np.linalg.norm(g - fd) / np.linalg.norm(fd)), abs(gs - fds) / abs(fds))
+    return worst < 1e-7, f"max rel err {worst:.3e}"
+
+
+def pin_bmds_invariances(o):
+    """Translation and rotation leave every distance unchanged (gradient sums
+    and torques vanish); scaling X, Y by c and sigma2 by c^2 shifts ell by
+    N (1 - N)/2 log c."""
+    Y, X = bmds_case(4, 11, 2)
+    n = 11
+    e, g, _ = o.bmds(Y, X, 0.25)
+    worst = float(np.max(np.abs(g.sum(axis=0))) / np.abs(g).sum())
+    torque = float(np.sum(X[:, 0] * g[:, 1] - X[:, 1] * g[:, 0]))
+    worst = max(worst, abs(torque) / float(np.abs(X).max() * np.abs(g).sum()))
+    for c in (0.5, 3.0):
+        ec = o.bmds(c * Y, c * X, 0.25 * c * c)[0]
+        worst = max(worst, abs(ec - (e + n * (1 - n) / 2 * math.log(c))) / abs(e))
+    return worst < 1e-12, f"max {worst:.3e}"
+
+
 ALL_PINS = {
     "brute_force": pin_brute_force,
     "space_time_quadrature": pin_space_time_quadrature,
@@ -387,4 +470,8 @@ ALL_PINS = {
     "hmc_reversible": pin_hmc_reversible,
     "hmc_energy_order": pin_hmc_energy_order,
     "hmc_accept_rule": pin_hmc_accept_rule,
+    "bmds_symbolic_pair": pin_bmds_symbolic_pair,
+    "bmds_pair_density": pin_bmds_pair_density,
+    "bmds_finite_diff": pin_bmds_finite_diff,
+    "bmds_invariances": pin_bmds_invariances,
 }

@@ -32,6 +32,10 @@ MUTANTS = {
     "omega_grad_sign": ("nadd(&a[4], xi * (1.0 / w - dt));", "nadd(&a[4], xi * (1.0 / w + dt));"),
     "tau_t_grad_boundary_term_dropped": ("phi_d(t[i] * t[i] / (tt * tt), 1) * t[i]) /", "0.0) /"),
     "rate_parts_swapped": ("nadd(&s_mu, mu);\n        nadd(&s_xi, xi);", "nadd(&s_mu, xi);\n        nadd(&s_xi, mu);"),
+    "bmds_normalizer_sign": ("*out_loglik = c * log(sigma2) - nval(&tot);", "*out_loglik = -c * log(sigma2) - nval(&tot);"),
+    "bmds_log_Phi_dropped": ("(2.0 * sigma2) + log(Phi_z));", "(2.0 * sigma2));"),
+    "bmds_gradient_ratio_unscaled": ("ratio / sigma;", "ratio;"),
+    "bmds_sigma_derivative_halved": ("ratio * delta / (2.0 * sigma2 * sigma));", "ratio * delta / (4.0 * sigma2 * sigma));"),
     "hmc_full_step_kicks": ("double half = 0.5 * eps;", "double half = eps;"),
     "hmc_reflection_keeps_momentum": ("            *x = 2.0 * lo - *x;\n            *pm = -*pm;", "            *x = 2.0 * lo - *x;"),
     "hmc_accept_inequality_reversed": ("log_u < H0 - H1) ? 1 : 0", "log_u > H0 - H1) ? 1 : 0"),
