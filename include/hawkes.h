@@ -40,6 +40,7 @@
 #ifndef HAWKES_H
 #define HAWKES_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -60,6 +61,12 @@ typedef enum {
     /* Every operation in FP64. */
     HAWKES_PREC_FP64 = 1
 } hawkes_precision;
+
+/* Element type of an input array that may be given in either precision. */
+typedef enum {
+    HAWKES_F64 = 0, /* double */
+    HAWKES_F32 = 1  /* float */
+} hawkes_dtype;
 
 typedef enum {
     HAWKES_OK = 0,
@@ -188,6 +195,47 @@ hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, con
 hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
                                           const hawkes_params *params, hawkes_precision prec, hawkes_stream stream,
                                           double *out_prob);
+
+/* ----------------------------------------------------------------- BMDS -- */
+
+/* Bayesian multidimensional scaling likelihood of Section 2.2.3, Eq. (4):
+ * observed distances y_nn' are truncated-normal around the latent distances
+ * delta_nn' = |x_n - x_n'| with variance sigma2, truncated to y > 0,
+ *   ell_B = N (1 - N) / 4 log(sigma2)
+ *           - sum_{n > n'} [ (y_nn' - delta_nn')^2 / (2 sigma2) + log Phi(delta_nn' / sigma) ],
+ * and its gradients with respect to every location and to sigma2.  With
+ * ell of Eq. (1) it forms the BMDS-Hawkes log-posterior whose HMC over the
+ * locations (Section 3) needs both gradients.
+ *   Y:  device [n*n] row-major, of type y_type (HAWKES_F64: double,
+ *       HAWKES_F32: float); only the entries below the diagonal
+ *       (Y[n*N + n'], n > n') are read, the rest may hold anything.  Each
+ *       must be finite and >= 0 (else the device status records
+ *       HAWKES_ERR_INVALID_DATA and every output is NaN).  The mixed
+ *       precision rounds FP64 distances to FP32 as it reads them, so a float
+ *       copy of Y (made once by the caller, Y being data) gives the same
+ *       results from half the memory traffic; HAWKES_PREC_FP64 widens float
+ *       distances exactly.
+ *   X:  device [n*d] locations, row-major; 1 <= d <= 8, 1 <= n <= 2^30.
+ *   sigma2 > 0, finite.
+ *   out_loglik: device [1];  out_grad_X: device [n*d] row-major or NULL;
+ *   out_grad_sigma2: device [1] or NULL.
+ * Coincident locations (delta = 0) contribute their value terms and no
+ * gradient term (|x_n - x_n'| has no derivative there; 0 is the symmetric
+ * subgradient).  HAWKES_PREC_MIXED evaluates each pair in FP32 (locations
+ * split into FP32 hi/lo parts) and adds the partial sums in FP64;
+ * HAWKES_PREC_FP64 does every operation in FP64.  Results are
+ * deterministic.  The call uses a workspace of
+ * hawkes_bmds_workspace_bytes(n, d, prec) bytes (about n^2 (d + 1) / 32
+ * bytes in the mixed precision for n >= 8192), which the context allocates
+ * on first use and keeps at the largest size seen. */
+hawkes_status hawkes_bmds_loglik_grad(hawkes_ctx *ctx, const void *Y, hawkes_dtype y_type, const double *X, int64_t n,
+                                      int32_t d, double sigma2, hawkes_precision prec, hawkes_stream stream,
+                                      double *out_loglik, double *out_grad_X, double *out_grad_sigma2);
+
+/* Device workspace (bytes) that hawkes_bmds_loglik_grad needs for (n, d,
+ * prec): one partial-sum slot per tile pair and a few per-CTA sums.
+ * Returns 0 for arguments outside the ranges above. */
+size_t hawkes_bmds_workspace_bytes(int64_t n, int32_t d, hawkes_precision prec);
 
 /* ------------------------------------------------------------------ HMC -- */
 

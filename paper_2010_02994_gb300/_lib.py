@@ -33,6 +33,7 @@ EXPORTED = (
     "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
     "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc", "hawkes_ctx_set_tuning",
     "hawkes_ctx_get_tuning", "hawkes_autotune", "hawkes_batch_hmc_trajectory", "hawkes_self_excitation_prob",
+    "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -76,6 +77,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_ctx_reset_stats.restype = st
     lib.hawkes_self_excitation_prob.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
     lib.hawkes_self_excitation_prob.restype = st
+    lib.hawkes_bmds_loglik_grad.argtypes = [vp, dp, i32, dp, i64, i32, ctypes.c_double, i32, vp, dp, dp, dp]
+    lib.hawkes_bmds_loglik_grad.restype = st
+    lib.hawkes_bmds_workspace_bytes.argtypes = [i64, i32, i32]
+    lib.hawkes_bmds_workspace_bytes.restype = ctypes.c_size_t
     lib.hawkes_loglik.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
     lib.hawkes_loglik.restype = st
     lib.hawkes_loglik_grad_locations.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp, dp, dp]

@@ -172,6 +172,36 @@ def hawkes_loglik_grad_locations(ctx: HawkesContext, t, X, params, precision="mi
     return (ell, g, gp) if grad_params else (ell, g)
 
 
+def hawkes_bmds_loglik_grad(ctx: HawkesContext, Y, X, sigma2: float, precision="mixed", grad: bool = True,
+                            check: bool = True, out=None):
+    """BMDS likelihood of Eq. (4) with its gradients: (ell_B, d ell_B/d X,
+    d ell_B/d sigma2) as device tensors (the gradients None when grad is
+    False).  Y is the (N, N) distance matrix, float64 or float32 (a float32
+    copy halves the memory traffic of the mixed precision and gives the same
+    results); only its entries below the diagonal are read."""
+    if not isinstance(Y, torch.Tensor) or not Y.is_cuda or Y.dtype not in (torch.float64, torch.float32):
+        raise TypeError("Y must be a float64 or float32 CUDA tensor")
+    Y = Y.contiguous()
+    y_type = 1 if Y.dtype == torch.float32 else 0
+    X = _dev_f64(X, "X")
+    if X.dim() == 1:
+        X = X.reshape(-1, 1)
+    n, d = X.shape
+    if Y.shape != (n, n):
+        raise ValueError("Y must be (N, N) with N = X.shape[0]")
+    if out is None:
+        ell = torch.empty((), dtype=torch.float64, device=X.device)
+        g = torch.empty((n, d), dtype=torch.float64, device=X.device) if grad else None
+        gs = torch.empty((), dtype=torch.float64, device=X.device) if grad else None
+    else:
+        ell, g, gs = out
+    ctx.check(ctx.lib.hawkes_bmds_loglik_grad(ctx.handle, _ptr(Y), y_type, _ptr(X), n, d, float(sigma2),
+                                              _precision(precision), ctx.stream(), _ptr(ell), _ptr(g), _ptr(gs)))
+    if check:
+        ctx.sync_status()
+    return ell, g, gs
+
+
 def hmc_leapfrog_trajectory(ctx: HawkesContext, t, X, p0, params, eps: float, n_steps: int, log_u,
                             box_lo=None, box_hi=None, precision="mixed", check: bool = True):
     """One HMC proposal (Section 3).  X is updated in place when accepted.

@@ -93,6 +93,7 @@ struct hawkes_ctx {
     int32_t ctl_sets = 0;
     DeviceBuffer ws;
     size_t ws_generation = 0;
+    DeviceBuffer bmds_ws;  // BMDS partial-sum slots
     // options
     int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
     std::vector<ProfEvent> prof_pending;
@@ -789,6 +790,8 @@ void hawkes_ctx_destroy(hawkes_ctx *ctx)
     }
     if (ctx->ws.ptr)
         cudaFree(ctx->ws.ptr);
+    if (ctx->bmds_ws.ptr)
+        cudaFree(ctx->bmds_ws.ptr);
     if (ctx->ctl)
         cudaFree(ctx->ctl);
     delete ctx;
@@ -999,6 +1002,55 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
     HK_TRY(launch_self_excitation(ctx->w, pl.total_segs, out_prob, s), "self-excitation");
     ctx->launches_own += 4;
     return enqueue_nan_on_invalid(ctx, out_prob, n, nullptr, 0, s);
+}
+
+size_t hawkes_bmds_workspace_bytes(int64_t n, int32_t d, hawkes_precision prec)
+{
+    if (n < 1 || n > (int64_t)1 << 30 || d < 1 || d > kMaxD ||
+        (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64))
+        return 0;
+    return bmds_workspace_bytes(n, d, prec == HAWKES_PREC_FP64);
+}
+
+hawkes_status hawkes_bmds_loglik_grad(hawkes_ctx *ctx, const void *Y, hawkes_dtype y_type, const double *X, int64_t n,
+                                      int32_t d, double sigma2, hawkes_precision prec, hawkes_stream stream,
+                                      double *out_loglik, double *out_grad_X, double *out_grad_sigma2)
+{
+    if (!ctx)
+        return HAWKES_ERR_INVALID_ARG;
+    if (!Y || !X || !out_loglik)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "Y, X and out_loglik must be device pointers");
+    if (n < 1 || n > (int64_t)1 << 30)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "n must be in [1, 2^30]");
+    if (d < 1 || d > kMaxD)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (!(sigma2 > 0.0) || !std::isfinite(sigma2))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "sigma2 must be finite and > 0");
+    if (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "unknown precision");
+    if (y_type != HAWKES_F64 && y_type != HAWKES_F32)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "y_type must be HAWKES_F64 or HAWKES_F32");
+    HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == HAWKES_PREC_FP64;
+    const size_t need = bmds_workspace_bytes(n, d, fp64);
+    if (need > ctx->bmds_ws.bytes) {
+        HK_TRY(cudaDeviceSynchronize(), "synchronize before growing the BMDS workspace");
+        if (ctx->bmds_ws.ptr)
+            cudaFree(ctx->bmds_ws.ptr);
+        ctx->bmds_ws.ptr = nullptr;
+        ctx->bmds_ws.bytes = 0;
+        if (cudaMalloc(&ctx->bmds_ws.ptr, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HAWKES_ERR_OOM, "BMDS workspace of " + std::to_string(need) + " bytes");
+        }
+        ctx->bmds_ws.bytes = need;
+        HK_TRY(cudaMemset(ctx->bmds_ws.ptr, 0, 256), "clear the BMDS ticket");
+    }
+    HK_TRY(launch_bmds(Y, y_type == HAWKES_F32, X, n, d, sigma2, fp64, ctx->bmds_ws.ptr, reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus),
+                       out_loglik, out_grad_X, out_grad_sigma2, s, &ctx->launches_own),
+           "BMDS kernels");
+    return HAWKES_OK;  // the finalize kernel writes NaN itself on invalid data
 }
 
 hawkes_status hawkes_loglik(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,

@@ -171,4 +171,10 @@ cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double 
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s);
 cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s);
 
+// hk_bmds.cu (BMDS likelihood of Eq. (4) and its gradients)
+size_t bmds_workspace_bytes(int64_t n, int d, bool fp64);
+cudaError_t launch_bmds(const void *Y, bool y_f32, const double *X, int64_t n, int d, double sigma2, bool fp64, void *ws,
+                        unsigned *status, double *out_loglik, double *out_grad, double *out_grad_sigma2,
+                        cudaStream_t s, int64_t *launches);
+
 }  // namespace hk

@@ -216,3 +216,51 @@ def random_case(seed: int, n: int, d: int, *, ties: int = 0, shuffle: bool = Tru
 
 
 CONFIGS = {"c1": make_c1, "c2": make_c2, "c3": make_c3, "c5": make_c5}
+
+
+@dataclass
+class BmdsWorkload:
+    """Inputs of the BMDS likelihood of Eq. (4): the (N, N) observed distance
+    matrix Y (symmetric, zero diagonal), latent locations X (N, D) at which it
+    is evaluated, and the variance sigma2."""
+
+    name: str
+    Y: np.ndarray
+    X: np.ndarray
+    sigma2: float
+    country: np.ndarray = field(default=None)
+
+
+def make_bmds(seed: int = 5, n: int = 4733, d: int = 6, n_countries: int = 150, sigma2: float = 0.25,
+              spread: float = 2.0, jitter: float = 0.1) -> BmdsWorkload:
+    """Shaped like the global influenza application (Section 4.3): cases
+    carry a country label, and the distance between two cases is the
+    effective air-traffic distance between their countries, so Y is blocky
+    and zero within a country.  Country sizes follow a Zipf(1.1) law; country
+    positions are N(0, spread^2 I_D); between-country distances are the
+    positions' distances plus N(0, sigma2) noise, folded to be >= 0; the
+    latent locations sit at their country's position plus N(0, jitter^2 I_D)."""
+    rng = np.random.default_rng(seed)
+    w = 1.0 / np.arange(1, n_countries + 1) ** 1.1
+    country = rng.choice(n_countries, size=n, p=w / w.sum())
+    Z = rng.normal(scale=spread, size=(n_countries, d))
+    Dc = np.sqrt(((Z[:, None, :] - Z[None, :, :]) ** 2).sum(-1))
+    noise = rng.normal(scale=np.sqrt(sigma2), size=(n_countries, n_countries))
+    noise = np.triu(noise, 1) + np.triu(noise, 1).T
+    Yc = np.abs(Dc + noise)
+    np.fill_diagonal(Yc, 0.0)
+    Y = Yc[country][:, country]
+    X = Z[country] + rng.normal(scale=jitter, size=(n, d))
+    return BmdsWorkload(f"bmds_influenza_like_n{n}_d{d}", np.ascontiguousarray(Y), X, float(sigma2), country)
+
+
+def bmds_random(seed: int, n: int, d: int, noise: float = 0.2, sigma2: float = 0.3) -> BmdsWorkload:
+    """Unstructured BMDS case: Y = |true distances + N(0, noise^2)| + 0.05
+    (symmetric), latent locations the true ones plus N(0, 0.1^2)."""
+    rng = np.random.default_rng(seed)
+    Xt = rng.normal(size=(n, d))
+    D = np.sqrt(((Xt[:, None, :] - Xt[None, :, :]) ** 2).sum(-1))
+    Y = np.abs(D + noise * rng.normal(size=(n, n))) + 0.05
+    Y = np.tril(Y, -1) + np.tril(Y, -1).T
+    X = Xt + 0.1 * rng.normal(size=Xt.shape)
+    return BmdsWorkload(f"bmds_random_n{n}_d{d}", np.ascontiguousarray(Y), X, float(sigma2))
