@@ -589,7 +589,7 @@ int oracle_bmds(int64_t n, int32_t d, const double *Y, const double *X, double s
                 nadd(&r, (y - delta) * (y - delta) / (2.0 * sigma2) + log(Phi_z));
                 nadd(&ss, (y - delta) * (y - delta) / (2.0 * sigma2 * sigma2) + ratio * delta / (2.0 * sigma2 * sigma));
             }
-            if (grad) {
+            if (grad && delta > 0.0) {  /* coincident points: no derivative, symmetric subgradient 0 */
                 const double drdd = -(y - delta) / sigma2 + ratio / sigma;
                 for (int k = 0; k < d; ++k)
                     nadd(&g[k], -drdd * (X[i * d + k] - X[m * d + k]) / delta);

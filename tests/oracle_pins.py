@@ -454,6 +454,29 @@ def pin_bmds_invariances(o):
     return worst < 1e-12, f"max {worst:.3e}"
 
 
+def pin_bmds_coincident(o):
+    """Two coincident latent points: |x_n - x_n'| has no derivative there, and
+    its central differences vanish, so the symmetric central difference of
+    ell_B equals the gradient with that pair's term taken as 0; the value
+    stays finite."""
+    Y, X = bmds_case(6, 6, 2)
+    X[3] = X[0]
+    s2v = 0.3
+    e, g, _ = o.bmds(Y, X, s2v)
+    if not (np.isfinite(e) and np.all(np.isfinite(g))):
+        return False, "non-finite value or gradient"
+    fd = np.zeros_like(g)
+    for i in range(X.shape[0]):
+        for k in range(X.shape[1]):
+            def f(v, i=i, k=k):
+                Xp = X.copy()
+                Xp[i, k] = v
+                return o.bmds(Y, Xp, s2v)[0]
+            fd[i, k] = _fd4(f, X[i, k], 1e-5)
+    err = float(np.linalg.norm(g - fd) / np.linalg.norm(fd))
+    return err < 1e-7, f"rel err {err:.3e}"
+
+
 ALL_PINS = {
     "brute_force": pin_brute_force,
     "space_time_quadrature": pin_space_time_quadrature,
@@ -474,4 +497,5 @@ ALL_PINS = {
     "bmds_pair_density": pin_bmds_pair_density,
     "bmds_finite_diff": pin_bmds_finite_diff,
     "bmds_invariances": pin_bmds_invariances,
+    "bmds_coincident": pin_bmds_coincident,
 }

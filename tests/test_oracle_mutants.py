@@ -36,6 +36,7 @@ MUTANTS = {
     "bmds_log_Phi_dropped": ("(2.0 * sigma2) + log(Phi_z));", "(2.0 * sigma2));"),
     "bmds_gradient_ratio_unscaled": ("ratio / sigma;", "ratio;"),
     "bmds_sigma_derivative_halved": ("ratio * delta / (2.0 * sigma2 * sigma));", "ratio * delta / (4.0 * sigma2 * sigma));"),
+    "bmds_coincident_guard_dropped": ("if (grad && delta > 0.0) {", "if (grad) {"),
     "hmc_full_step_kicks": ("double half = 0.5 * eps;", "double half = eps;"),
     "hmc_reflection_keeps_momentum": ("            *x = 2.0 * lo - *x;\n            *pm = -*pm;", "            *x = 2.0 * lo - *x;"),
     "hmc_accept_inequality_reversed": ("log_u < H0 - H1) ? 1 : 0", "log_u > H0 - H1) ? 1 : 0"),
