@@ -62,6 +62,15 @@ def pass_bound_cycles(d: int, which: str, fma_rate: float, ex2_rate: float) -> f
     return max((f1 + f2) / fma_rate, (e1 + e2) / ex2_rate)
 
 
+def bmds_bound_cycles(d: int, fma_rate: float, ex2_rate: float) -> float:
+    """SM cycles per unordered pair of the BMDS pair term (Eq. (4)) with its
+    location and variance gradients: 4D+40 FP32 ops (difference, square,
+    row and column gradient per dimension; distance, the normal tail as a
+    degree-(4,5) rational, Phi, phi/Phi, log Phi, the value and sigma2
+    terms) and four MUFU ops (rsqrt, ex2, rcp, lg2), no hi/lo overhead."""
+    return max((4 * d + 40) / fma_rate, 4 / ex2_rate)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -206,17 +215,72 @@ def flush_l2(buf):
     buf.zero_()
 
 
-def other_workloads(dev, stream, l2) -> dict:
-    """Batched 64-set latent-space workload (one call, mixed path) and one
-    20-step HMC trajectory at N=1e4 (mixed path, CUDA graph), timed with
-    CUDA events; L2 flushed before each timed call."""
+def timed_calls(fn, stream, l2, reps: int = 10, warm: int = 2) -> float:
+    """Median CUDA-event time (ms) of fn() on `stream`, L2 flushed before each call."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush_l2(l2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def bmds_workload(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: float, sms: int) -> dict:
+    """BMDS likelihood and gradients (Eq. (4)) on the influenza-shaped input:
+    N = 4,733 cases, D = 6, block-structured Y (synth.make_bmds)."""
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_bmds_loglik_grad
+
+    w = synth.make_bmds()
+    n, d = w.X.shape
+    ctx = HawkesContext(device=dev.index or 0, max_n=n, max_d=d)
+    Y64 = torch.tensor(w.Y, device=dev)
+    Y32 = Y64.float()
+    X = torch.tensor(w.X, device=dev)
+    out_t = (torch.empty((), dtype=torch.float64, device=dev), torch.empty((n, d), dtype=torch.float64, device=dev),
+             torch.empty((), dtype=torch.float64, device=dev))
+    res = {"workload": w.name, "n": n, "d": d}
+    pairs = n * (n - 1) / 2
+    bound_s = pairs * bmds_bound_cycles(d, fma_rate, ex2_rate) / (sms * clock_mhz * 1e6)
+    for key, Y, prec, reps in (("mixed_y_f32", Y32, "mixed", 20), ("mixed_y_f64", Y64, "mixed", 20),
+                               ("fp64", Y64, "fp64", 3)):
+        m = timed_calls(lambda: hawkes_bmds_loglik_grad(ctx, Y, X, w.sigma2, prec, check=False, out=out_t),
+                        stream, l2, reps=reps, warm=2)
+        res[key] = {"ms_per_eval": m, "evals_per_s": 1e3 / m, "unordered_pairs_per_s": pairs / (m * 1e-3),
+                    "y_bytes_per_eval": int(pairs * Y.element_size())}
+        if prec == "mixed":
+            res[key]["roofline"] = {"bound": "alu", "unit": "evals/s", "achieved": 1e3 / m,
+                                    "peak": 1.0 / bound_s, "frac": bound_s / (m * 1e-3),
+                                    "basis": (f"(4D+40)/{fma_rate:.1f} FP32 and 4/{ex2_rate:.1f} MUFU SM-cycles per "
+                                              f"unordered pair at {clock_mhz:.0f} MHz, {sms} SMs (measured rates)")}
+    ctx.sync_status()
+    ctx.close()
+    return res
+
+
+def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: float, sms: int) -> dict:
+    """Batched 64-set latent-space workload (one call, mixed path), one
+    20-step HMC trajectory at N=1e4 (mixed path, CUDA graph) and the BMDS
+    likelihood at the influenza size, timed with CUDA events; L2 flushed
+    before each timed call."""
     import numpy as np
     import torch
 
     import synth
     from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad, hmc_leapfrog_trajectory
 
-    out = {}
+    out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms)}
     sets = synth.make_c4()
     sizes = [w.n for w in sets]
     dims = [w.d for w in sets]
@@ -461,7 +525,7 @@ def main():
     # --- the other paper-shaped workloads (reported beside the headline) -----
     extra = {}
     if not args.no_extra:
-        extra = other_workloads(dev, stream, l2)
+        extra = other_workloads(dev, stream, l2, fma_rate, ex2_rate, MAX_SM_MHZ_NOMINAL, sms)
 
     # --- CPU baseline: the oracle on the host cores ---------------------------
     cpu = None
