@@ -237,6 +237,65 @@ hawkes_status hawkes_bmds_loglik_grad(hawkes_ctx *ctx, const void *Y, hawkes_dty
  * Returns 0 for arguments outside the ranges above. */
 size_t hawkes_bmds_workspace_bytes(int64_t n, int32_t d, hawkes_precision prec);
 
+/* ------------------------------------------------ Metropolis-within-Gibbs -- */
+
+/* Incremental log-likelihood changes for the block-wise Metropolis-Hastings
+ * updates of the event locations (Section 3).  A state holds copies of t and
+ * X and the rates lambda_n of Eq. (1) in FP64.  Moving a block B of events to
+ * new locations changes only the pair terms that involve B, so
+ *   Delta ell = ell(X with x_b -> x*_b, b in B) - ell(X)
+ *             = sum_n [log lambda*_n - log lambda_n]
+ * costs O(|B| N) pair evaluations instead of the O(N^2) of a full evaluation
+ * (the integrated rate does not depend on X).  Everything is FP64; calls
+ * enqueue on `stream`, allocate nothing after hawkes_mwg_create and read
+ * nothing back to the host (the accept decision and the commit happen on the
+ * device), so a sequence of steps may be captured in a CUDA graph.  Use one
+ * stream per state.  Device-side data errors (an index out of range or
+ * repeated within a block, a non-finite proposal, invalid t or X at
+ * creation) make Delta ell NaN, reject every step, and are reported and
+ * cleared by hawkes_mwg_sync_status. */
+typedef struct hawkes_mwg hawkes_mwg;
+
+/* Create a state on `device` from device arrays t [n] (>= 0, finite) and X
+ * [n*d] (row-major, finite), copying both; computes every lambda_n in FP64
+ * (O(n^2), enqueued on `stream`).  max_block (1..256) bounds the block size of
+ * later proposals.  Returns HAWKES_ERR_INVALID_ARG for bad sizes or
+ * parameters, HAWKES_ERR_OOM if device memory runs out. */
+hawkes_status hawkes_mwg_create(int32_t device, const double *t, const double *X, int64_t n, int32_t d,
+                                const hawkes_params *params, int32_t max_block, hawkes_stream stream,
+                                hawkes_mwg **out);
+void hawkes_mwg_destroy(hawkes_mwg *s);
+const char *hawkes_mwg_last_error(const hawkes_mwg *s);
+
+/* Delta ell of moving events idx[0..nb) (device int64, distinct, in [0, n))
+ * to X_new (device [nb*d]); the state is not changed.  out_delta: device [1].
+ * Delta ell is +inf when the move makes a zero rate positive, and a rate that
+ * stays zero contributes 0.  0 <= nb <= max_block. */
+hawkes_status hawkes_mwg_delta(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new,
+                               hawkes_stream stream, double *out_delta);
+
+/* One Metropolis-Hastings step with the same proposal: accept iff
+ * log_u < Delta ell + log_q_ratio (device scalars; log_q_ratio =
+ * log q(x|x*) - log q(x*|x) of the caller's proposal, NULL for a symmetric
+ * one; a NaN on either side rejects).  On accept the moved locations, the
+ * rates and the running ell are updated.  out_delta (device [1]) and
+ * out_accepted (device int32 [1]) may be NULL. */
+hawkes_status hawkes_mwg_step(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new,
+                              const double *log_q_ratio, const double *log_u, hawkes_stream stream,
+                              double *out_delta, int32_t *out_accepted);
+
+/* Recompute every rate and ell from the current locations (O(n^2)); the
+ * incremental updates accumulate rounding over many accepted steps. */
+hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream);
+
+/* Copy the current locations (device [n*d]), rates (device [n]) and running
+ * ell (device [1]) out; any pointer may be NULL. */
+hawkes_status hawkes_mwg_read(hawkes_mwg *s, hawkes_stream stream, double *X_out, double *lam_out,
+                              double *out_loglik);
+
+/* Synchronize `stream`, then report and clear the state's device status. */
+hawkes_status hawkes_mwg_sync_status(hawkes_mwg *s, hawkes_stream stream);
+
 /* ------------------------------------------------------------------ HMC -- */
 
 /* One Hamiltonian Monte Carlo proposal over all locations (Section 3: HMC

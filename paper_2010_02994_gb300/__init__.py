@@ -5,7 +5,7 @@ its location and parameter gradients, and HMC over event locations
 The computation lives in libhawkes.so (C ABI: include/hawkes.h); this package
 only marshals torch tensors into it.
 """
-from .api import (HawkesContext, HawkesError, hawkes_batch_hmc_trajectory, hawkes_batch_loglik_grad,  # noqa: F401
+from .api import (HawkesContext, HawkesError, HawkesMwG, hawkes_batch_hmc_trajectory, hawkes_batch_loglik_grad,  # noqa: F401
                   hawkes_loglik,
                   hawkes_bmds_loglik_grad, hawkes_loglik_grad_locations, hawkes_loglik_noalloc,
                   hawkes_self_excitation_prob,

@@ -33,7 +33,9 @@ EXPORTED = (
     "hawkes_loglik_grad_locations", "hmc_leapfrog_trajectory", "hawkes_batch_loglik_grad", "hawkes_version",
     "hawkes_ctx_launch_count", "hawkes_probe_pipe_rates", "hawkes_loglik_noalloc", "hawkes_ctx_set_tuning",
     "hawkes_ctx_get_tuning", "hawkes_autotune", "hawkes_batch_hmc_trajectory", "hawkes_self_excitation_prob",
-    "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes",
+    "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
+    "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
+    "hawkes_mwg_sync_status",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -81,6 +83,22 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_bmds_loglik_grad.restype = st
     lib.hawkes_bmds_workspace_bytes.argtypes = [i64, i32, i32]
     lib.hawkes_bmds_workspace_bytes.restype = ctypes.c_size_t
+    lib.hawkes_mwg_create.argtypes = [i32, dp, dp, i64, i32, pp, i32, vp, ctypes.POINTER(vp)]
+    lib.hawkes_mwg_create.restype = st
+    lib.hawkes_mwg_destroy.argtypes = [vp]
+    lib.hawkes_mwg_destroy.restype = None
+    lib.hawkes_mwg_last_error.argtypes = [vp]
+    lib.hawkes_mwg_last_error.restype = ctypes.c_char_p
+    lib.hawkes_mwg_delta.argtypes = [vp, i32, dp, dp, vp, dp]
+    lib.hawkes_mwg_delta.restype = st
+    lib.hawkes_mwg_step.argtypes = [vp, i32, dp, dp, dp, dp, vp, dp, dp]
+    lib.hawkes_mwg_step.restype = st
+    lib.hawkes_mwg_refresh.argtypes = [vp, vp]
+    lib.hawkes_mwg_refresh.restype = st
+    lib.hawkes_mwg_read.argtypes = [vp, vp, dp, dp, dp]
+    lib.hawkes_mwg_read.restype = st
+    lib.hawkes_mwg_sync_status.argtypes = [vp, vp]
+    lib.hawkes_mwg_sync_status.restype = st
     lib.hawkes_loglik.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]
     lib.hawkes_loglik.restype = st
     lib.hawkes_loglik_grad_locations.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp, dp, dp]

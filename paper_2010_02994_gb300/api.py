@@ -319,3 +319,91 @@ def hawkes_batch_hmc_trajectory(ctx: HawkesContext, sizes, dims, t, X, p0, param
 
 def version() -> str:
     return _lib.load().hawkes_version().decode()
+
+
+class HawkesMwG:
+    """Incremental Metropolis-within-Gibbs state over the event locations
+    (hawkes_mwg_* in the C ABI): FP64 rates cached on the device, block moves
+    evaluated in O(|B| N), accept and commit on the device."""
+
+    def __init__(self, t, X, params, max_block: int = 64, device: int | None = None):
+        self.lib = _lib.load()
+        t = _dev_f64(t, "t")
+        X = _dev_f64(X, "X")
+        n, d, X = _shape(t, X)
+        self.n, self.d = n, d
+        self.device = t.device.index if device is None else int(device)
+        self.max_block = int(max_block)
+        p = params_struct(params)
+        h = ctypes.c_void_p()
+        st = self.lib.hawkes_mwg_create(self.device, _ptr(t), _ptr(X), n, d, ctypes.byref(p), self.max_block,
+                                        self.stream(), ctypes.byref(h))
+        if st != 0:
+            raise HawkesError(st, "hawkes_mwg_create failed")
+        self.handle = h
+        self._dev = t.device
+
+    def stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def check(self, status: int):
+        if status != 0:
+            raise HawkesError(status, self.lib.hawkes_mwg_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hawkes_mwg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self):
+        self.check(self.lib.hawkes_mwg_sync_status(self.handle, self.stream()))
+
+    def _block(self, idx, X_new):
+        idx = torch.as_tensor(idx, dtype=torch.int64, device=self._dev).contiguous()
+        X_new = torch.as_tensor(X_new, dtype=torch.float64, device=self._dev).reshape(-1, self.d).contiguous()
+        if X_new.shape[0] != idx.numel():
+            raise ValueError("X_new must have one row per index")
+        return idx, X_new
+
+    def delta(self, idx, X_new, out=None, check: bool = True):
+        """Delta ell of moving events idx to X_new (device tensor, state unchanged)."""
+        idx, X_new = self._block(idx, X_new)
+        out = torch.empty((), dtype=torch.float64, device=self._dev) if out is None else out
+        self.check(self.lib.hawkes_mwg_delta(self.handle, idx.numel(), _ptr(idx), _ptr(X_new), self.stream(),
+                                             _ptr(out)))
+        if check:
+            self.sync_status()
+        return out
+
+    def step(self, idx, X_new, log_u, log_q_ratio=None, out=None, check: bool = True):
+        """One Metropolis-Hastings step; returns (Delta ell, accepted) as device tensors."""
+        idx, X_new = self._block(idx, X_new)
+        if not isinstance(log_u, torch.Tensor):
+            log_u = torch.tensor(float(log_u), dtype=torch.float64, device=self._dev)
+        if log_q_ratio is not None and not isinstance(log_q_ratio, torch.Tensor):
+            log_q_ratio = torch.tensor(float(log_q_ratio), dtype=torch.float64, device=self._dev)
+        if out is None:
+            out = (torch.empty((), dtype=torch.float64, device=self._dev),
+                   torch.empty((), dtype=torch.int32, device=self._dev))
+        self.check(self.lib.hawkes_mwg_step(self.handle, idx.numel(), _ptr(idx), _ptr(X_new), _ptr(log_q_ratio),
+                                            _ptr(log_u), self.stream(), _ptr(out[0]), _ptr(out[1])))
+        if check:
+            self.sync_status()
+        return out
+
+    def refresh(self):
+        self.check(self.lib.hawkes_mwg_refresh(self.handle, self.stream()))
+
+    def read(self):
+        """(X, lambda, ell) of the current state as device tensors."""
+        X = torch.empty((self.n, self.d), dtype=torch.float64, device=self._dev)
+        lam = torch.empty(self.n, dtype=torch.float64, device=self._dev)
+        ell = torch.empty((), dtype=torch.float64, device=self._dev)
+        self.check(self.lib.hawkes_mwg_read(self.handle, self.stream(), _ptr(X), _ptr(lam), _ptr(ell)))
+        return X, lam, ell

@@ -1,0 +1,587 @@
+// Incremental Metropolis-within-Gibbs over event locations (Section 3: the
+// location variables are updated block-wise by Metropolis-Hastings).
+//
+// Moving a block B of events from x_b to x*_b changes only the pair terms
+// that involve some b in B.  Given the current rates lambda_m (Eq. (1),
+// cached in FP64), the new rates are
+//   m not in B:  lambda*_m = lambda_m + sum_{b in B} [k(m <- b at x*_b) - k(m <- b at x_b)],
+//   m in B:      lambda*_m = sum_{m' != m} k(m <- m'), every m' at its new place,
+// where k(m <- m') = mu_{mm'} + xi_{mm'} is event m' 's contribution to the rate
+// at event m (Section 2.1).  The integrated rate does not depend on X, so
+//   Delta ell = sum_m [log lambda*_m - log lambda_m],
+// an O(|B| N) computation instead of the O(N^2) of a full evaluation.
+//
+// Three launches per proposal: a column kernel (every m: block membership,
+// the |B| column updates, log1p(Delta_m / lambda_m) summed per CTA), a row
+// kernel (one CTA per moved event: its new rate over all events), and a
+// one-CTA finish kernel (Delta ell in a fixed order; in step mode the accept
+// decision log u < Delta ell + log q-ratio and, on accept, the commit).  The
+// rates live in two buffers; the device-side index of the current one flips
+// on accept, so no call reads anything back to the host and a sequence of
+// steps can be captured in a CUDA graph.  Everything is FP64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "hawkes.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxDim = 8;
+constexpr int kMaxBlock = 256;  // events moved together at most
+constexpr int kRateTile = 128;
+constexpr int kRateSplit = 16;
+
+// status bits of the state
+constexpr int kBadData = 1;      // non-finite input location or time, negative time
+constexpr int kBadBlock = 2;     // index out of range or repeated in a block
+constexpr int kBadProposal = 4;  // non-finite proposed location
+
+struct Consts {
+    double a, b, c;  // 1/(2 tau_x^2), 1/(2 tau_t^2), 1/(2 h^2)
+    double Cmu, Cxi, omega, mu0, tau_t, theta;
+};
+
+// Contribution of event (xs, ts) to the rate at event (xm, tm): the
+// background term (both Gaussians, I[t != t_m]) and the self-excitation term
+// (I[t < t_m]) of Section 2.1.
+__device__ __forceinline__ double contrib(const double *xm, double tm, const double *xs, double ts, int d,
+                                          const Consts &k)
+{
+    double r2 = 0.0;
+    for (int q = 0; q < d; ++q) {
+        const double df = xm[q] - xs[q];
+        r2 += df * df;
+    }
+    const double dt = tm - ts;
+    double v = 0.0;
+    if (tm != ts)
+        v += k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+    if (ts < tm)
+        v += k.Cxi * exp(-(k.omega * dt + r2 * k.c));
+    return v;
+}
+
+__device__ double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// log(lam_new / lam) with the extended-real convention for zero rates.
+__device__ __forceinline__ double log_ratio(double lam, double lam_new, double delta)
+{
+    if (lam > 0.0)
+        return log1p(delta / lam);
+    return lam_new > 0.0 ? INFINITY : 0.0;
+}
+
+// ------------------------------------------------------------ full rates --
+
+// Partial rate sums over one column split (ordered pairs), as in the FP64
+// rate pass.
+__global__ void __launch_bounds__(kRateTile) rates_kernel(const double *__restrict__ t, const double *__restrict__ X,
+                                                          int64_t n, int d, Consts k, int fsplit,
+                                                          double *__restrict__ part, int *status)
+{
+    __shared__ double st[kRateTile];
+    __shared__ double sx[kRateTile * kMaxDim];
+    const int64_t row = (int64_t)blockIdx.x * kRateTile + threadIdx.x;
+    const int sp = blockIdx.y;
+    const bool valid = row < n;
+    double tn = 0.0, xn[kMaxDim];
+    for (int q = 0; q < kMaxDim; ++q)
+        xn[q] = 0.0;
+    if (valid) {
+        tn = t[row];
+        bool bad = !(tn >= 0.0) || !isfinite(tn);
+        for (int q = 0; q < d; ++q) {
+            xn[q] = X[row * d + q];
+            bad |= !isfinite(xn[q]);
+        }
+        if (bad && sp == 0)
+            atomicOr(status, kBadData);
+    }
+    const int64_t tiles = (n + kRateTile - 1) / kRateTile;
+    const int64_t per = (tiles + fsplit - 1) / fsplit;
+    const int64_t lo = min(sp * per * kRateTile, n), hi = min((sp + 1) * per * kRateTile, n);
+    double s = 0.0, c = 0.0;
+    for (int64_t c0 = lo; c0 < hi; c0 += kRateTile) {
+        const int cnt = (int)min((int64_t)kRateTile, hi - c0);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            st[threadIdx.x] = t[c0 + threadIdx.x];
+            for (int q = 0; q < d; ++q)
+                sx[threadIdx.x * kMaxDim + q] = X[(c0 + threadIdx.x) * d + q];
+        }
+        __syncthreads();
+        if (!valid)
+            continue;
+        double acc = 0.0;
+        for (int j = 0; j < cnt; ++j)
+            acc += contrib(xn, tn, sx + j * kMaxDim, st[j], d, k);
+        const double y = acc - c;  // compensated across tiles
+        const double tt = s + y;
+        c = (tt - s) - y;
+        s = tt;
+    }
+    if (valid)
+        part[(int64_t)sp * n + row] = s;
+}
+
+// lambda_m from the splits (fixed order) into the current buffer, and
+// ell = sum log lambda - sum Lambda in one CTA.
+__global__ void __launch_bounds__(kThreads) rates_finish_kernel(const double *__restrict__ t, int64_t n, Consts k,
+                                                                int fsplit, const double *__restrict__ part,
+                                                                double *lam0, double *lam1, const int *active,
+                                                                double *loglik)
+{
+    __shared__ double sh[kThreads];
+    double *lam = *active ? lam1 : lam0;
+    double tmax = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads)
+        tmax = fmax(tmax, t[i]);
+    sh[threadIdx.x] = tmax;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double T = sh[0];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        double l = 0.0;
+        for (int sp = 0; sp < fsplit; ++sp)
+            l += part[(int64_t)sp * n + i];
+        lam[i] = l;
+        const double a = T - t[i];
+        const double Lam = k.mu0 * (normcdf(a / k.tau_t) - normcdf(-t[i] / k.tau_t)) - k.theta * expm1(-k.omega * a);
+        acc += log(l) - Lam;
+    }
+    const double ell = block_sum(acc, sh);
+    if (threadIdx.x == 0)
+        *loglik = ell;
+}
+
+// ------------------------------------------------------------- proposal --
+
+struct Block {
+    int nb;
+    const int64_t *idx;   // caller's device indices
+    const double *xnew;   // caller's device proposals, nb x d
+};
+
+// Every m: its position in the block (or -1), and for m outside the block
+// the change of its rate and log1p(Delta_m / lambda_m), summed per CTA.
+__global__ void __launch_bounds__(kThreads) columns_kernel(const double *__restrict__ t, const double *__restrict__ X,
+                                                           int64_t n, int d, Consts k, Block B, double *lam0,
+                                                           double *lam1, const int *active, int *pos,
+                                                           double *part, int *status)
+{
+    __shared__ double sh[kThreads];
+    __shared__ double sxo[kMaxBlock * kMaxDim], sxn[kMaxBlock * kMaxDim], stb[kMaxBlock];
+    __shared__ int64_t sid[kMaxBlock];
+    const double *lam = *active ? lam1 : lam0;
+    double *lam_new = *active ? lam0 : lam1;
+    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
+        const int64_t m = B.idx[b];
+        const bool ok = m >= 0 && m < n;
+        sid[b] = ok ? m : -1;
+        stb[b] = ok ? t[m] : 0.0;
+        bool bad = false;
+        for (int q = 0; q < d; ++q) {
+            sxo[b * kMaxDim + q] = ok ? X[m * d + q] : 0.0;
+            const double v = B.xnew[(int64_t)b * d + q];
+            bad |= !isfinite(v);
+            sxn[b * kMaxDim + q] = v;
+        }
+        if (blockIdx.x == 0) {
+            if (!ok)
+                atomicOr(status, kBadBlock);
+            if (bad)
+                atomicOr(status, kBadProposal);
+        }
+    }
+    __syncthreads();
+    double term = 0.0;
+    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (m < n) {
+        int p = -1;
+        for (int b = 0; b < B.nb; ++b)
+            if (sid[b] == m) {
+                if (p >= 0)
+                    atomicOr(status, kBadBlock);  // repeated index
+                p = b;
+            }
+        pos[m] = p;
+        if (p < 0) {
+            double xm[kMaxDim];
+            for (int q = 0; q < d; ++q)
+                xm[q] = X[m * d + q];
+            const double tm = t[m];
+            double delta = 0.0;
+            for (int b = 0; b < B.nb; ++b)
+                delta += contrib(xm, tm, sxn + b * kMaxDim, stb[b], d, k) -
+                         contrib(xm, tm, sxo + b * kMaxDim, stb[b], d, k);
+            const double l = lam[m];
+            const double ln = l + delta;
+            lam_new[m] = ln;
+            term = log_ratio(l, ln, delta);
+        }
+    }
+    term = block_sum(term, sh);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = term;
+}
+
+// One CTA per moved event b: its new rate over all events (moved ones at
+// their proposed places), and log lambda*_b - log lambda_b.
+__global__ void __launch_bounds__(kThreads) rows_kernel(const double *__restrict__ t, const double *__restrict__ X,
+                                                        int64_t n, int d, Consts k, Block B, double *lam0,
+                                                        double *lam1, const int *active, const int *pos,
+                                                        double *rowterm)
+{
+    __shared__ double sh[kThreads];
+    const double *lam = *active ? lam1 : lam0;
+    double *lam_new = *active ? lam0 : lam1;
+    const int b = blockIdx.x;
+    const int64_t mb = B.idx[b];
+    if (mb < 0 || mb >= n) {  // reported by the column kernel
+        if (threadIdx.x == 0)
+            rowterm[b] = 0.0;
+        return;
+    }
+    double xb[kMaxDim];
+    for (int q = 0; q < d; ++q)
+        xb[q] = B.xnew[(int64_t)b * d + q];
+    const double tb = t[mb];
+    double s = 0.0;
+    for (int64_t m = threadIdx.x; m < n; m += kThreads) {
+        if (m == mb)
+            continue;
+        const int p = pos[m];
+        const double *xm = p >= 0 ? B.xnew + (int64_t)p * d : X + m * d;
+        s += contrib(xb, tb, xm, t[m], d, k);
+    }
+    const double lnew = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double l = lam[mb];
+        lam_new[mb] = lnew;
+        rowterm[b] = (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
+    }
+}
+
+// Delta ell in a fixed order; in step mode the accept decision and, on
+// accept, the commit (moved locations, running ell, current-buffer flip).
+__global__ void __launch_bounds__(kThreads) finish_kernel(int ncta, const double *__restrict__ part, Block B,
+                                                          const double *__restrict__ rowterm, const int *status,
+                                                          double *out_delta, bool step, const double *log_q_ratio,
+                                                          const double *log_u, int *accepted_out, double *X, int d,
+                                                          int *active, double *loglik)
+{
+    __shared__ double sh[kThreads];
+    __shared__ int acc;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < ncta; i += kThreads)
+        v += part[i];
+    for (int b = threadIdx.x; b < B.nb; b += kThreads)
+        v += rowterm[b];
+    const double delta = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        const bool bad = *(volatile const int *)status != 0;
+        const double dl = bad ? nan("") : delta;
+        if (out_delta)
+            *out_delta = dl;
+        int a = 0;
+        if (step && !bad) {
+            const double lhs = *log_u, rhs = dl + (log_q_ratio ? *log_q_ratio : 0.0);
+            a = (lhs < rhs) ? 1 : 0;  // NaN on either side rejects
+        }
+        acc = a;
+        if (accepted_out)
+            *accepted_out = a;
+        if (a) {
+            *loglik += dl;
+            *active ^= 1;
+        }
+    }
+    __syncthreads();
+    if (acc)
+        for (int e = threadIdx.x; e < B.nb * d; e += kThreads) {
+            const int b = e / d, q = e % d;
+            X[B.idx[b] * d + q] = B.xnew[e];
+        }
+}
+
+__global__ void copy_rates_kernel(const double *lam0, const double *lam1, const int *active, int64_t n, double *out)
+{
+    const double *lam = *active ? lam1 : lam0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = lam[i];
+}
+
+bool params_ok(const hawkes_params *p)
+{
+    if (!p)
+        return false;
+    const double v[6] = {p->mu0, p->tau_x, p->tau_t, p->theta, p->omega, p->h};
+    for (double x : v)
+        if (!(x > 0.0) || !std::isfinite(x))
+            return false;
+    return true;
+}
+
+Consts make_consts(const hawkes_params &p, int d)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    Consts k;
+    k.a = 0.5 / (p.tau_x * p.tau_x);
+    k.b = 0.5 / (p.tau_t * p.tau_t);
+    k.c = 0.5 / (p.h * p.h);
+    k.Cmu = p.mu0 / (std::pow(p.tau_x, d) * p.tau_t * std::pow(two_pi, 0.5 * (d + 1)));
+    k.Cxi = p.theta * p.omega / (std::pow(p.h, d) * std::pow(two_pi, 0.5 * d));
+    k.omega = p.omega;
+    k.mu0 = p.mu0;
+    k.tau_t = p.tau_t;
+    k.theta = p.theta;
+    return k;
+}
+
+int grid_for(int64_t n) { return (int)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+struct hawkes_mwg {
+    int device = 0;
+    int sms = 0;
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t max_block = 0;
+    Consts k{};
+    std::string err;
+    // device buffers
+    double *t = nullptr, *X = nullptr, *lam0 = nullptr, *lam1 = nullptr;
+    double *part = nullptr;     // max(kRateSplit * n, column-kernel CTAs)
+    double *rowterm = nullptr;  // max_block
+    double *loglik = nullptr;   // running ell
+    int *ctl = nullptr;         // [0] current rate buffer, [1] status
+    int *pos = nullptr;         // n
+};
+
+namespace {
+
+hawkes_status fail(hawkes_mwg *s, hawkes_status st, const std::string &msg)
+{
+    if (s)
+        s->err = msg;
+    return st;
+}
+
+hawkes_status cuda_fail(hawkes_mwg *s, cudaError_t e, const char *where)
+{
+    cudaGetLastError();
+    return fail(s, HAWKES_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define MWG_TRY(expr, where)                    \
+    do {                                        \
+        cudaError_t e_ = (expr);                \
+        if (e_ != cudaSuccess)                  \
+            return cuda_fail(s, e_, where);     \
+    } while (0)
+
+hawkes_status enqueue_rates(hawkes_mwg *s, cudaStream_t st)
+{
+    const int64_t tiles = (s->n + kRateTile - 1) / kRateTile;
+    int fsplit = (int)std::min<int64_t>(kRateSplit, std::max<int64_t>(1, (4 * s->sms + tiles - 1) / tiles));
+    if (fsplit > tiles)
+        fsplit = (int)tiles;
+    rates_kernel<<<dim3((unsigned)tiles, fsplit), kRateTile, 0, st>>>(s->t, s->X, s->n, s->d, s->k, fsplit, s->part,
+                                                                      s->ctl + 1);
+    MWG_TRY(cudaGetLastError(), "rate kernel");
+    rates_finish_kernel<<<1, kThreads, 0, st>>>(s->t, s->n, s->k, fsplit, s->part, s->lam0, s->lam1, s->ctl,
+                                                s->loglik);
+    MWG_TRY(cudaGetLastError(), "rate finish kernel");
+    return HAWKES_OK;
+}
+
+hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new, bool step,
+                               const double *log_q_ratio, const double *log_u, cudaStream_t st, double *out_delta,
+                               int32_t *out_accepted)
+{
+    if (nb < 0 || nb > s->max_block)
+        return fail(s, HAWKES_ERR_INVALID_ARG, "block size must be in [0, max_block]");
+    if (nb > 0 && (!idx || !X_new))
+        return fail(s, HAWKES_ERR_INVALID_ARG, "idx and X_new must be device pointers");
+    if (step && !log_u)
+        return fail(s, HAWKES_ERR_INVALID_ARG, "log_u must be a device pointer");
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    const Block B{nb, idx, X_new};
+    const int ncta = grid_for(s->n);
+    columns_kernel<<<ncta, kThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
+                                              s->part, s->ctl + 1);
+    MWG_TRY(cudaGetLastError(), "column kernel");
+    if (nb > 0) {
+        rows_kernel<<<nb, kThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
+                                             s->rowterm);
+        MWG_TRY(cudaGetLastError(), "row kernel");
+    }
+    finish_kernel<<<1, kThreads, 0, st>>>(ncta, s->part, B, s->rowterm, s->ctl + 1, out_delta, step, log_q_ratio,
+                                          log_u, out_accepted, s->X, s->d, s->ctl, s->loglik);
+    MWG_TRY(cudaGetLastError(), "finish kernel");
+    return HAWKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hawkes_status hawkes_mwg_create(int32_t device, const double *t, const double *X, int64_t n, int32_t d,
+                                const hawkes_params *params, int32_t max_block, hawkes_stream stream,
+                                hawkes_mwg **out)
+{
+    if (!out)
+        return HAWKES_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!t || !X || n < 1 || n > ((int64_t)1 << 30) || d < 1 || d > kMaxDim || !params_ok(params) ||
+        max_block < 1 || max_block > kMaxBlock)
+        return HAWKES_ERR_INVALID_ARG;
+    hawkes_mwg *s = new hawkes_mwg();
+    s->device = device;
+    s->n = n;
+    s->d = d;
+    s->max_block = max_block;
+    s->k = make_consts(*params, d);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto bail = [&](hawkes_status code) {
+        hawkes_mwg_destroy(s);
+        return code;
+    };
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(HAWKES_ERR_CUDA);
+    }
+    const size_t part_n = std::max<size_t>((size_t)kRateSplit * n, (size_t)grid_for(n));
+    if (cudaMalloc(&s->t, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&s->X, sizeof(double) * n * d) != cudaSuccess ||
+        cudaMalloc(&s->lam0, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&s->lam1, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&s->part, sizeof(double) * part_n) != cudaSuccess ||
+        cudaMalloc(&s->rowterm, sizeof(double) * max_block) != cudaSuccess ||
+        cudaMalloc(&s->loglik, sizeof(double)) != cudaSuccess || cudaMalloc(&s->ctl, sizeof(int) * 2) != cudaSuccess ||
+        cudaMalloc(&s->pos, sizeof(int) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(HAWKES_ERR_OOM);
+    }
+    if (cudaMemcpyAsync(s->t, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->X, X, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(s->ctl, 0, sizeof(int) * 2, st) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(HAWKES_ERR_CUDA);
+    }
+    if (enqueue_rates(s, st) != HAWKES_OK)
+        return bail(HAWKES_ERR_CUDA);
+    *out = s;
+    return HAWKES_OK;
+}
+
+void hawkes_mwg_destroy(hawkes_mwg *s)
+{
+    if (!s)
+        return;
+    cudaSetDevice(s->device);
+    cudaFree(s->t);
+    cudaFree(s->X);
+    cudaFree(s->lam0);
+    cudaFree(s->lam1);
+    cudaFree(s->part);
+    cudaFree(s->rowterm);
+    cudaFree(s->loglik);
+    cudaFree(s->ctl);
+    cudaFree(s->pos);
+    delete s;
+}
+
+const char *hawkes_mwg_last_error(const hawkes_mwg *s) { return s ? s->err.c_str() : "null state"; }
+
+hawkes_status hawkes_mwg_delta(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new,
+                               hawkes_stream stream, double *out_delta)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    if (!out_delta)
+        return fail(s, HAWKES_ERR_INVALID_ARG, "out_delta must be a device pointer");
+    return enqueue_proposal(s, nb, idx, X_new, false, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream),
+                            out_delta, nullptr);
+}
+
+hawkes_status hawkes_mwg_step(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new,
+                              const double *log_q_ratio, const double *log_u, hawkes_stream stream,
+                              double *out_delta, int32_t *out_accepted)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    return enqueue_proposal(s, nb, idx, X_new, true, log_q_ratio, log_u, reinterpret_cast<cudaStream_t>(stream),
+                            out_delta, out_accepted);
+}
+
+hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    return enqueue_rates(s, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hawkes_status hawkes_mwg_read(hawkes_mwg *s, hawkes_stream stream, double *X_out, double *lam_out,
+                              double *out_loglik)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (X_out)
+        MWG_TRY(cudaMemcpyAsync(X_out, s->X, sizeof(double) * s->n * s->d, cudaMemcpyDeviceToDevice, st), "copy X");
+    if (lam_out) {
+        copy_rates_kernel<<<std::min(1024, grid_for(s->n)), kThreads, 0, st>>>(s->lam0, s->lam1, s->ctl, s->n,
+                                                                                lam_out);
+        MWG_TRY(cudaGetLastError(), "copy rates");
+    }
+    if (out_loglik)
+        MWG_TRY(cudaMemcpyAsync(out_loglik, s->loglik, sizeof(double), cudaMemcpyDeviceToDevice, st), "copy ell");
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_mwg_sync_status(hawkes_mwg *s, hawkes_stream stream)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    MWG_TRY(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "stream synchronize");
+    int st = 0;
+    MWG_TRY(cudaMemcpy(&st, s->ctl + 1, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    MWG_TRY(cudaMemset(s->ctl + 1, 0, sizeof(int)), "clear status");
+    if (st & kBadData)
+        return fail(s, HAWKES_ERR_INVALID_DATA, "non-finite location or time, or a negative time");
+    if (st & kBadBlock)
+        return fail(s, HAWKES_ERR_INVALID_DATA, "a block index is out of range or repeated");
+    if (st & kBadProposal)
+        return fail(s, HAWKES_ERR_INVALID_DATA, "a proposed location is not finite");
+    s->err.clear();
+    return HAWKES_OK;
+}
+
+}  // extern "C"
