@@ -73,6 +73,12 @@ def load_library(path: str) -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_int32), i32]
     lib.oracle_bmds.argtypes = [i64, i32, dp, dp, ctypes.c_double, dp, dp, dp, i32]
     lib.oracle_bmds.restype = ctypes.c_int
+    lib.oracle_lens_area.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.oracle_lens_area.restype = ctypes.c_double
+    lib.oracle_circle_proposals.argtypes = [i32, dp, dp, dp, ctypes.c_double, i32, dp, dp, dp]
+    lib.oracle_circle_proposals.restype = ctypes.c_int
+    lib.oracle_box_proposals.argtypes = [i32, i32, dp, dp, dp, ctypes.c_double, dp, dp, dp]
+    lib.oracle_box_proposals.restype = ctypes.c_int
     lib.oracle_max_threads.restype = i32
     for name in ("oracle_rates", "oracle_rates_rows", "oracle_loglik", "oracle_grad_locations",
                  "oracle_grad_rows", "oracle_grad_params", "oracle_hmc_trajectory"):
@@ -245,6 +251,39 @@ class Oracle:
                "bmds")
         return float(out[0]), g, float(gs[0])
 
+    def lens_area(self, R, rho, c) -> float:
+        """Area of the intersection of discs of radii R and rho, centres c apart."""
+        return float(self.lib.oracle_lens_area(float(R), float(rho), float(c)))
+
+    def circle_proposals(self, X, centers, radii, eps, tries, u):
+        """Lens proposals of Eq. (6) for the D = 2 rows of X: (X_new, log q-ratio).
+        u has shape (nb, tries, 2)."""
+        X = _as_f64(X).reshape(-1, 2)
+        nb = X.shape[0]
+        C = _as_f64(centers).reshape(nb, 2)
+        r = _as_f64(radii).reshape(nb)
+        u = _as_f64(u).reshape(nb, int(tries), 2)
+        Xn = np.empty((nb, 2))
+        lq = np.empty(1)
+        _check(self.lib.oracle_circle_proposals(nb, _dp(X), _dp(C), _dp(r), float(eps), int(tries), _dp(u), _dp(Xn),
+                                                _dp(lq)), "circle_proposals")
+        return Xn, float(lq[0])
+
+    def box_proposals(self, X, lo, hi, s, u):
+        """Truncated-normal proposals inside the boxes [lo, hi]: (X_new, log q-ratio)."""
+        X = _as_f64(X)
+        if X.ndim == 1:
+            X = X.reshape(-1, 1)
+        nb, d = X.shape
+        lo = _as_f64(lo).reshape(nb, d)
+        hi = _as_f64(hi).reshape(nb, d)
+        u = _as_f64(u).reshape(nb, d)
+        Xn = np.empty((nb, d))
+        lq = np.empty(1)
+        _check(self.lib.oracle_box_proposals(nb, d, _dp(X), _dp(lo), _dp(hi), float(s), _dp(u), _dp(Xn), _dp(lq)),
+               "box_proposals")
+        return Xn, float(lq[0])
+
     def max_threads(self) -> int:
         """Threads an OpenMP region of the oracle uses by default."""
         return int(self.lib.oracle_max_threads())
@@ -300,6 +339,18 @@ def hmc_trajectory(*a, **k):
 
 def bmds(*a, **k):
     return default().bmds(*a, **k)
+
+
+def lens_area(*a, **k):
+    return default().lens_area(*a, **k)
+
+
+def circle_proposals(*a, **k):
+    return default().circle_proposals(*a, **k)
+
+
+def box_proposals(*a, **k):
+    return default().box_proposals(*a, **k)
 
 
 def max_threads() -> int:

@@ -616,6 +616,163 @@ int oracle_bmds(int64_t n, int32_t d, const double *Y, const double *X, double s
     return ORACLE_OK;
 }
 
+/* ---------------------------------------------------- MwG proposals -- */
+
+/* x - sin(x) for x in [0, 2 pi], by its Taylor series where the difference
+ * would cancel (x < 0.5: terms to x^15, error below 1e-17 x^3). */
+static double x_minus_sin(double x)
+{
+    if (x >= 0.5)
+        return x - sin(x);
+    const double x2 = x * x;
+    double term = x * x2 / 6.0, sum = 0.0;
+    for (int k = 1; k <= 7; ++k) {
+        sum += term;
+        term *= -x2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+    return sum;
+}
+
+/*
+ * Area of the intersection of two discs with radii R and rho whose centres
+ * are c apart (the "asymmetric lens" of the circle proposal, Section 3,
+ * Eq. (6)): zero when the discs are apart, the smaller disc when one lies in
+ * the other, otherwise the two circular segments cut off by the common
+ * chord.  The chord lies at signed distances d1 = (c^2 + R^2 - rho^2)/(2c)
+ * and d2 = c - d1 from the centres with half-length h; a segment of a disc
+ * of radius r whose chord subtends 2 theta at the centre has area
+ * r^2 (2 theta - sin 2 theta) / 2 (sector minus triangle), with
+ * theta = atan2(h, d), written so that nothing cancels when one disc is
+ * much larger than the other.
+ */
+double oracle_lens_area(double R, double rho, double c)
+{
+    if (!(R > 0) || !(rho > 0) || !(c >= 0))
+        return NAN;
+    if (c >= R + rho)
+        return 0.0;
+    if (c <= fabs(R - rho)) {
+        const double m = R < rho ? R : rho;
+        return kPi * m * m;
+    }
+    const double d1 = (c * c + R * R - rho * rho) / (2.0 * c);
+    const double d2 = c - d1;
+    double h2 = (R - d1) * (R + d1);
+    if (h2 < 0.0)
+        h2 = 0.0;
+    const double h = sqrt(h2);
+    const double th1 = atan2(h, d1), th2 = atan2(h, d2);
+    return 0.5 * R * R * x_minus_sin(2.0 * th1) + 0.5 * rho * rho * x_minus_sin(2.0 * th2);
+}
+
+/* log of the probability that at least one of `tries` uniform draws from a
+ * disc of radius rho lands in a region of area A inside it. */
+static double log_success(double A, double rho, int32_t tries)
+{
+    const double p = A / (kPi * rho * rho);
+    if (p >= 1.0)
+        return 0.0;
+    return log(-expm1((double)tries * log1p(-p)));
+}
+
+/*
+ * Circle proposals for the D = 2 locations of Eq. (3) (Section 3, Eq. (6)):
+ * event b at x_b with prior circle (centre m_b, radius r_b) proposes x*
+ * uniform on {|x* - m_b| < r_b, |x* - x_b| < r_b eps}, by rejection from the
+ * disc around x_b: try k draws radius r_b eps sqrt(u1) and angle 2 pi u2 from
+ * u[(b*tries + k)*2 + {0,1}]; the first draw inside the circle is the
+ * proposal.  If all tries miss, the proposal is x_b itself.  Accepted draws
+ * are uniform on the lens L(x_b) of area A(x_b), so for x* != x_b
+ *   q(x*|x) = (1 - (1 - A(x)/(pi (r eps)^2))^tries) / A(x),
+ * and the proposal's log ratio log q(x|x*) - log q(x*|x), summed over the
+ * block, is written to *log_q_ratio (0 for events that stay).
+ */
+int oracle_circle_proposals(int32_t nb, const double *X, const double *centers, const double *radii,
+                            double eps, int32_t tries, const double *u, double *X_new, double *log_q_ratio)
+{
+    if (nb < 0 || tries < 1 || !(eps > 0) || (nb > 0 && (!X || !centers || !radii || !u || !X_new)) ||
+        !log_q_ratio)
+        return ORACLE_ERR_ARG;
+    nsum lq = {0, 0};
+    for (int32_t b = 0; b < nb; ++b) {
+        const double *x = X + 2 * b, *m = centers + 2 * b;
+        const double R = radii[b], rho = R * eps;
+        X_new[2 * b] = x[0];
+        X_new[2 * b + 1] = x[1];
+        for (int32_t k = 0; k < tries; ++k) {
+            const double r = rho * sqrt(u[(b * tries + k) * 2]);
+            const double ang = 2.0 * kPi * u[(b * tries + k) * 2 + 1];
+            const double y0 = x[0] + r * cos(ang), y1 = x[1] + r * sin(ang);
+            const double dx = y0 - m[0], dy = y1 - m[1];
+            if (dx * dx + dy * dy < R * R) {
+                X_new[2 * b] = y0;
+                X_new[2 * b + 1] = y1;
+                const double A_x = oracle_lens_area(R, rho, hypot(x[0] - m[0], x[1] - m[1]));
+                const double A_y = oracle_lens_area(R, rho, hypot(dx, dy));
+                nadd(&lq, (log_success(A_y, rho, tries) - log(A_y)) - (log_success(A_x, rho, tries) - log(A_x)));
+                break;
+            }
+        }
+    }
+    *log_q_ratio = nval(&lq);
+    return ORACLE_OK;
+}
+
+/* Inverse of the standard normal CDF by bisection on Phi (exact to the last
+ * bisection step; slow and plain). */
+static double Phi_inv(double p)
+{
+    if (!(p > 0.0 && p < 1.0))
+        return p == 0.0 ? -INFINITY : (p == 1.0 ? INFINITY : NAN);
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi)
+            break;
+        if (Phi(mid) < p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/*
+ * Box proposals for the square priors of Eq. (2) (Section 3: truncated
+ * normal proposals): each coordinate k of event b draws
+ *   x*_k = x_k + s Phi^{-1}(Phi(a) + u (Phi(b) - Phi(a))),
+ *   a = (lo_k - x_k)/s,  b = (hi_k - x_k)/s,
+ * from u[b*d + k], i.e. N(x_k, s^2) truncated to [lo_k, hi_k].  The normal
+ * parts of q(x|x*) and q(x*|x) cancel, leaving
+ *   log q(x|x*) - log q(x*|x) = sum log Z(x) - log Z(x*),
+ *   Z(y) = Phi((hi_k - y_k)/s) - Phi((lo_k - y_k)/s),
+ * summed over the block into *log_q_ratio.
+ */
+int oracle_box_proposals(int32_t nb, int32_t d, const double *X, const double *lo, const double *hi, double s,
+                         const double *u, double *X_new, double *log_q_ratio)
+{
+    if (nb < 0 || d < 1 || !(s > 0) || (nb > 0 && (!X || !lo || !hi || !u || !X_new)) || !log_q_ratio)
+        return ORACLE_ERR_ARG;
+    nsum lq = {0, 0};
+    for (int32_t b = 0; b < nb; ++b)
+        for (int32_t k = 0; k < d; ++k) {
+            const int64_t e = (int64_t)b * d + k;
+            const double x = X[e];
+            const double Pa = Phi((lo[e] - x) / s), Pb = Phi((hi[e] - x) / s);
+            double y = x + s * Phi_inv(Pa + u[e] * (Pb - Pa));
+            if (y < lo[e])
+                y = lo[e];
+            if (y > hi[e])
+                y = hi[e];
+            X_new[e] = y;
+            const double Zx = Pb - Pa;
+            const double Zy = Phi((hi[e] - y) / s) - Phi((lo[e] - y) / s);
+            nadd(&lq, log(Zx) - log(Zy));
+        }
+    *log_q_ratio = nval(&lq);
+    return ORACLE_OK;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int32_t oracle_max_threads(void)
 {

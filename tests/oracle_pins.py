@@ -477,6 +477,98 @@ def pin_bmds_coincident(o):
     return err < 1e-7, f"rel err {err:.3e}"
 
 
+def _lens_quad(R, rho, c):
+    """Lens area by quadrature of the overlap of the two chords along the
+    line of centres (first circle at 0, second at c)."""
+    lo, hi = max(-R, c - rho), min(R, c + rho)
+    if hi <= lo:
+        return 0.0
+    f = lambda x: 2.0 * max(0.0, min(math.sqrt(max(R * R - x * x, 0.0)),
+                                     math.sqrt(max(rho * rho - (x - c) ** 2, 0.0))))
+    # the chords cross at the discs' common chord, x = (c^2 + R^2 - rho^2) / (2c)
+    x_cross = (c * c + R * R - rho * rho) / (2 * c) if c > 0 else lo
+    pts = [p for p in (c - rho, c + rho, -R, R, x_cross) if lo < p < hi]
+    val, _ = integrate.quad(f, lo, hi, points=pts or None, limit=400, epsabs=1e-14, epsrel=1e-13)
+    return val
+
+
+def pin_lens_area(o):
+    """The lens area of Eq. (6) against quadrature, the equal-circle closed
+    form 2R^2 acos(c/2R) - (c/2) sqrt(4R^2 - c^2), and the limiting cases."""
+    worst = 0.0
+    for R, rho, c in ((1.0, 0.5, 0.9), (1.0, 0.5, 1.2), (2.0, 0.3, 1.85), (1.0, 3.0, 2.5), (0.7, 0.7, 0.2),
+                      (5.0, 0.01, 4.995), (1.0, 1.0, 1.999)):
+        a = o.lens_area(R, rho, c)
+        worst = max(worst, abs(a - _lens_quad(R, rho, c)) / max(a, 1e-300))
+    for c in (0.1, 0.8, 1.5, 1.9):
+        ref = 2 * math.acos(c / 2) - (c / 2) * math.sqrt(4 - c * c)
+        worst = max(worst, abs(o.lens_area(1.0, 1.0, c) - ref) / ref)
+    ok = o.lens_area(1.0, 0.5, 1.6) == 0.0 and abs(o.lens_area(1.0, 0.5, 0.3) - math.pi * 0.25) < 1e-15
+    ok = ok and abs(o.lens_area(0.4, 2.0, 1.0) - math.pi * 0.16) < 1e-15
+    return ok and worst < 1e-10, f"max rel err {worst:.3e}"
+
+
+def pin_circle_proposals(o):
+    """The rejection sampler of Eq. (6) by simulation: with `tries` draws from
+    the disc of radius r eps, a proposal succeeds with probability
+    1 - (1 - A/(pi (r eps)^2))^tries (A from quadrature), successful proposals
+    lie in both discs and are uniform on the lens (the share in the half-plane
+    y > 0 is 1/2 by symmetry, the share within distance r eps / 2 of x is the
+    quadrature area of that smaller lens over A); the log q-ratio of a
+    successful single move equals the one built from those pinned pieces."""
+    rng = np.random.default_rng(7)
+    R, eps, tries = 1.0, 0.6, 2
+    x = np.array([0.75, 0.0])
+    rho = R * eps
+    A = _lens_quad(R, rho, 0.75)
+    M = 200_000
+    X = np.tile(x, (M, 1))
+    u = rng.uniform(size=(M, tries, 2))
+    # one event per row: call the oracle in chunks (all rows share the same prior circle)
+    Xn, _ = o.circle_proposals(X, np.zeros((M, 2)), np.full(M, R), eps, tries, u)
+    moved = np.any(Xn != X, axis=1)
+    p_ref = 1.0 - (1.0 - A / (math.pi * rho * rho)) ** tries
+    se = math.sqrt(p_ref * (1 - p_ref) / M)
+    ok = abs(moved.mean() - p_ref) < 5 * se
+    Y = Xn[moved]
+    ok = ok and bool(np.all(np.hypot(Y[:, 0], Y[:, 1]) < R)) and bool(np.all(np.hypot(*(Y - x).T) < rho))
+    half = (Y[:, 1] > 0).mean()
+    near = (np.hypot(*(Y - x).T) < rho / 2).mean()
+    near_ref = _lens_quad(R, rho / 2, 0.75) / A
+    ok = ok and abs(half - 0.5) < 5 * math.sqrt(0.25 / len(Y)) and abs(near - near_ref) < 5 * math.sqrt(
+        near_ref * (1 - near_ref) / len(Y))
+    # log q-ratio of one successful move, from the pinned pieces
+    u1 = np.array([[[0.3, 0.1], [0.5, 0.5]]])
+    y, lq = o.circle_proposals(x[None, :], np.zeros((1, 2)), np.array([R]), eps, tries, u1)
+    Ay = _lens_quad(R, rho, float(np.hypot(*y[0])))
+    Ps = lambda a: 1.0 - (1.0 - a / (math.pi * rho * rho)) ** tries
+    ref = (math.log(Ps(Ay)) - math.log(Ay)) - (math.log(Ps(A)) - math.log(A))
+    ok = ok and abs(lq - ref) < 1e-10
+    return ok, f"success {moved.mean():.4f} vs {p_ref:.4f}, half {half:.4f}, near {near:.4f} vs {near_ref:.4f}"
+
+
+def pin_box_proposals(o):
+    """Truncated-normal box proposals against scipy: the draw is
+    x + s ndtri(Phi(a) + u (Phi(b) - Phi(a))) (scipy's inverse normal CDF),
+    stays in the box, and the log q-ratio equals
+    truncnorm.logpdf(x | x*) - truncnorm.logpdf(x* | x) summed over coordinates."""
+    from scipy import special, stats
+
+    rng = np.random.default_rng(8)
+    nb, d, s = 6, 2, 0.03
+    X = rng.uniform(0, 1, size=(nb, d))
+    lo, hi = X - rng.uniform(0.01, 0.06, size=X.shape), X + rng.uniform(0.01, 0.06, size=X.shape)
+    u = rng.uniform(size=(nb, d))
+    Xn, lq = o.box_proposals(X, lo, hi, s, u)
+    Pa, Pb = special.ndtr((lo - X) / s), special.ndtr((hi - X) / s)
+    ref = X + s * special.ndtri(Pa + u * (Pb - Pa))
+    err = float(np.max(np.abs(Xn - ref)))
+    lp = lambda y, c: stats.truncnorm.logpdf(y, (lo - c) / s, (hi - c) / s, loc=c, scale=s)
+    lq_ref = float(np.sum(lp(X, Xn) - lp(Xn, X)))
+    ok = err < 1e-12 and bool(np.all((Xn >= lo) & (Xn <= hi))) and abs(lq - lq_ref) < 1e-9
+    return ok, f"draw err {err:.2e}, ratio {lq:.6f} vs {lq_ref:.6f}"
+
+
 ALL_PINS = {
     "brute_force": pin_brute_force,
     "space_time_quadrature": pin_space_time_quadrature,
@@ -498,4 +590,7 @@ ALL_PINS = {
     "bmds_finite_diff": pin_bmds_finite_diff,
     "bmds_invariances": pin_bmds_invariances,
     "bmds_coincident": pin_bmds_coincident,
+    "lens_area": pin_lens_area,
+    "circle_proposals": pin_circle_proposals,
+    "box_proposals": pin_box_proposals,
 }

@@ -37,6 +37,12 @@ MUTANTS = {
     "bmds_gradient_ratio_unscaled": ("ratio / sigma;", "ratio;"),
     "bmds_sigma_derivative_halved": ("ratio * delta / (2.0 * sigma2 * sigma));", "ratio * delta / (4.0 * sigma2 * sigma));"),
     "bmds_coincident_guard_dropped": ("if (grad && delta > 0.0) {", "if (grad) {"),
+    "lens_segment_sign": ("x_minus_sin(2.0 * th1) + 0.5 * rho * rho", "x_minus_sin(2.0 * th1) - 0.5 * rho * rho"),
+    "circle_success_factor_dropped": ("nadd(&lq, (log_success(A_y, rho, tries) - log(A_y)) - (log_success(A_x, rho, tries) - log(A_x)));",
+                                      "nadd(&lq, log(A_x) - log(A_y));"),
+    "circle_radius_not_sqrt": ("const double r = rho * sqrt(u[(b * tries + k) * 2]);",
+                               "const double r = rho * u[(b * tries + k) * 2];"),
+    "box_ratio_inverted": ("nadd(&lq, log(Zx) - log(Zy));", "nadd(&lq, log(Zy) - log(Zx));"),
     "hmc_full_step_kicks": ("double half = 0.5 * eps;", "double half = eps;"),
     "hmc_reflection_keeps_momentum": ("            *x = 2.0 * lo - *x;\n            *pm = -*pm;", "            *x = 2.0 * lo - *x;"),
     "hmc_accept_inequality_reversed": ("log_u < H0 - H1) ? 1 : 0", "log_u > H0 - H1) ? 1 : 0"),
