@@ -284,6 +284,35 @@ hawkes_status hawkes_mwg_step(hawkes_mwg *s, int32_t nb, const int64_t *idx, con
                               const double *log_q_ratio, const double *log_u, hawkes_stream stream,
                               double *out_delta, int32_t *out_accepted);
 
+/* Proposals for the block idx[0..nb) from the state's current locations,
+ * written to X_new (device [nb*d]) with the block's log q-ratio
+ * log q(x|x*) - log q(x*|x) in *log_q_ratio (device [1]), ready for
+ * hawkes_mwg_step.  Random numbers are the caller's uniforms in (0, 1).
+ *
+ * Circle priors (Eq. (3), D = 2 only): event m has prior centre
+ * centers[2m..2m+1] and radius radii[m] (device arrays over all n events).
+ * The proposal of Eq. (6) is uniform on the lens between the prior circle and
+ * the disc of radius radii[m]*eps around the current point, drawn by
+ * rejection: try k takes radius r eps sqrt(u[(b*tries+k)*2]) and angle
+ * 2 pi u[(b*tries+k)*2+1] (u: device [nb*tries*2]); the first draw inside the
+ * circle is the proposal, and if every try misses the event stays.  With
+ * A(x) the lens area (closed form) and P(x) = 1 - (1 - A/(pi (r eps)^2))^tries
+ * the chance that some try lands, the ratio sums
+ * log(P(x*)/A(x*)) - log(P(x)/A(x)) over the events that move, which keeps
+ * the chain exact for any number of tries. */
+hawkes_status hawkes_mwg_propose_circle(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *centers,
+                                        const double *radii, double eps, int32_t tries, const double *u,
+                                        hawkes_stream stream, double *X_new, double *log_q_ratio);
+
+/* Box priors (Eq. (2)): coordinate k of event m lies in [lo[m*d+k],
+ * hi[m*d+k]] (device arrays over all n events); the proposal is N(x_k, sd^2)
+ * truncated to the box, drawn by inverse CDF from u[b*d+k] (device
+ * [nb*d]); the ratio is sum log Z(x) - log Z(x*) with
+ * Z(y) = Phi((hi - y)/sd) - Phi((lo - y)/sd). */
+hawkes_status hawkes_mwg_propose_box(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *lo,
+                                     const double *hi, double sd, const double *u, hawkes_stream stream,
+                                     double *X_new, double *log_q_ratio);
+
 /* Recompute every rate and ell from the current locations (O(n^2)); the
  * incremental updates accumulate rounding over many accepted steps. */
 hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream);

@@ -35,7 +35,7 @@ EXPORTED = (
     "hawkes_ctx_get_tuning", "hawkes_autotune", "hawkes_batch_hmc_trajectory", "hawkes_self_excitation_prob",
     "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
     "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
-    "hawkes_mwg_sync_status",
+    "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -97,6 +97,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_mwg_refresh.restype = st
     lib.hawkes_mwg_read.argtypes = [vp, vp, dp, dp, dp]
     lib.hawkes_mwg_read.restype = st
+    lib.hawkes_mwg_propose_circle.argtypes = [vp, i32, dp, dp, dp, ctypes.c_double, i32, dp, vp, dp, dp]
+    lib.hawkes_mwg_propose_circle.restype = st
+    lib.hawkes_mwg_propose_box.argtypes = [vp, i32, dp, dp, dp, ctypes.c_double, dp, vp, dp, dp]
+    lib.hawkes_mwg_propose_box.restype = st
     lib.hawkes_mwg_sync_status.argtypes = [vp, vp]
     lib.hawkes_mwg_sync_status.restype = st
     lib.hawkes_loglik.argtypes = [vp, dp, dp, i64, i32, pp, i32, vp, dp]

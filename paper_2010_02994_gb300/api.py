@@ -397,6 +397,40 @@ class HawkesMwG:
             self.sync_status()
         return out
 
+    def propose_circle(self, idx, centers, radii, eps: float, tries: int, u, out=None, check: bool = True):
+        """Lens proposals of Eq. (6) (D = 2): (X_new, log q-ratio) as device tensors.
+        centers (N, 2) and radii (N,) cover every event; u has nb * tries * 2 uniforms."""
+        idx = torch.as_tensor(idx, dtype=torch.int64, device=self._dev).contiguous()
+        centers = _dev_f64(torch.as_tensor(centers, dtype=torch.float64, device=self._dev), "centers")
+        radii = _dev_f64(torch.as_tensor(radii, dtype=torch.float64, device=self._dev), "radii")
+        u = _dev_f64(torch.as_tensor(u, dtype=torch.float64, device=self._dev), "u")
+        nb = idx.numel()
+        if out is None:
+            out = (torch.empty((nb, self.d), dtype=torch.float64, device=self._dev),
+                   torch.empty((), dtype=torch.float64, device=self._dev))
+        self.check(self.lib.hawkes_mwg_propose_circle(self.handle, nb, _ptr(idx), _ptr(centers), _ptr(radii),
+                                                      float(eps), int(tries), _ptr(u), self.stream(), _ptr(out[0]),
+                                                      _ptr(out[1])))
+        if check:
+            self.sync_status()
+        return out
+
+    def propose_box(self, idx, lo, hi, sd: float, u, out=None, check: bool = True):
+        """Truncated-normal proposals inside the boxes of Eq. (2): (X_new, log q-ratio)."""
+        idx = torch.as_tensor(idx, dtype=torch.int64, device=self._dev).contiguous()
+        lo = _dev_f64(torch.as_tensor(lo, dtype=torch.float64, device=self._dev), "lo")
+        hi = _dev_f64(torch.as_tensor(hi, dtype=torch.float64, device=self._dev), "hi")
+        u = _dev_f64(torch.as_tensor(u, dtype=torch.float64, device=self._dev), "u")
+        nb = idx.numel()
+        if out is None:
+            out = (torch.empty((nb, self.d), dtype=torch.float64, device=self._dev),
+                   torch.empty((), dtype=torch.float64, device=self._dev))
+        self.check(self.lib.hawkes_mwg_propose_box(self.handle, nb, _ptr(idx), _ptr(lo), _ptr(hi), float(sd),
+                                                   _ptr(u), self.stream(), _ptr(out[0]), _ptr(out[1])))
+        if check:
+            self.sync_status()
+        return out
+
     def refresh(self):
         self.check(self.lib.hawkes_mwg_refresh(self.handle, self.stream()))
 

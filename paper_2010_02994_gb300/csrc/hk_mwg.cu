@@ -21,6 +21,8 @@
 // steps can be captured in a CUDA graph.  Everything is FP64.
 #include <cuda_runtime.h>
 
+#include <math_constants.h>
+
 #include <cmath>
 #include <string>
 
@@ -332,6 +334,128 @@ __global__ void copy_rates_kernel(const double *lam0, const double *lam1, const 
         out[i] = lam[i];
 }
 
+// ------------------------------------------------------------ proposals --
+
+// x - sin(x) on [0, 2 pi]; Taylor series below 0.5, where the difference
+// would cancel.
+__device__ double x_minus_sin(double x)
+{
+    if (x >= 0.5)
+        return x - sin(x);
+    const double x2 = x * x;
+    double term = x * x2 / 6.0, sum = 0.0;
+    for (int k = 1; k <= 7; ++k) {
+        sum += term;
+        term *= -x2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+    return sum;
+}
+
+// Area of the intersection of discs of radii R and rho, centres c apart:
+// the two circular segments cut off by the common chord, each
+// r^2 (2 theta - sin 2 theta) / 2 with theta = atan2(half-chord, signed
+// distance of the chord from the centre).
+__device__ double lens_area(double R, double rho, double c)
+{
+    if (c >= R + rho)
+        return 0.0;
+    if (c <= fabs(R - rho)) {
+        const double m = fmin(R, rho);
+        return CUDART_PI * m * m;
+    }
+    const double d1 = (c * c + R * R - rho * rho) / (2.0 * c);
+    const double d2 = c - d1;
+    const double h = sqrt(fmax((R - d1) * (R + d1), 0.0));
+    return 0.5 * R * R * x_minus_sin(2.0 * atan2(h, d1)) + 0.5 * rho * rho * x_minus_sin(2.0 * atan2(h, d2));
+}
+
+// log P(at least one of `tries` uniform draws from a disc of radius rho
+// lands in a region of area A inside it)
+__device__ double log_success(double A, double rho, int tries)
+{
+    const double p = A / (CUDART_PI * rho * rho);
+    return p >= 1.0 ? 0.0 : log(-expm1((double)tries * log1p(-p)));
+}
+
+// Lens proposals of Eq. (6) for a D = 2 block, one thread per moved event;
+// the block's log q-ratio is summed in a fixed order.
+__global__ void __launch_bounds__(kThreads) propose_circle_kernel(const double *__restrict__ X, int64_t n, Block B,
+                                                                  const double *__restrict__ centers,
+                                                                  const double *__restrict__ radii, double eps,
+                                                                  int tries, const double *__restrict__ u,
+                                                                  double *X_new, double *log_q_ratio, int *status)
+{
+    __shared__ double sh[kThreads];
+    double lq = 0.0;
+    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
+        const int64_t m = B.idx[b];
+        if (m < 0 || m >= n) {
+            atomicOr(status, kBadBlock);
+            continue;
+        }
+        const double x0 = X[m * 2], x1 = X[m * 2 + 1], c0 = centers[m * 2], c1 = centers[m * 2 + 1];
+        const double R = radii[m], rho = R * eps;
+        const double A_x = lens_area(R, rho, hypot(x0 - c0, x1 - c1));
+        if (!(R > 0.0) || !isfinite(R) || !(A_x > 0.0)) {
+            atomicOr(status, kBadProposal);
+            continue;
+        }
+        double y0 = x0, y1 = x1;
+        for (int k = 0; k < tries; ++k) {
+            const double r = rho * sqrt(u[((int64_t)b * tries + k) * 2]);
+            double sn, cs;
+            sincospi(2.0 * u[((int64_t)b * tries + k) * 2 + 1], &sn, &cs);
+            const double z0 = x0 + r * cs, z1 = x1 + r * sn;
+            const double dx = z0 - c0, dy = z1 - c1;
+            if (dx * dx + dy * dy < R * R) {
+                y0 = z0;
+                y1 = z1;
+                const double A_y = lens_area(R, rho, hypot(dx, dy));
+                lq += (log_success(A_y, rho, tries) - log(A_y)) - (log_success(A_x, rho, tries) - log(A_x));
+                break;
+            }
+        }
+        X_new[(int64_t)b * 2] = y0;
+        X_new[(int64_t)b * 2 + 1] = y1;
+    }
+    lq = block_sum(lq, sh);
+    if (threadIdx.x == 0)
+        *log_q_ratio = lq;
+}
+
+// Truncated-normal proposals inside the boxes of Eq. (2), one thread per
+// coordinate: x* = x + s Phi^{-1}(Phi(a) + u (Phi(b) - Phi(a))), and the
+// log q-ratio sum log Z(x) - log Z(x*), Z(y) = Phi((hi - y)/s) - Phi((lo - y)/s).
+__global__ void __launch_bounds__(kThreads) propose_box_kernel(const double *__restrict__ X, int64_t n, int d,
+                                                               Block B, const double *__restrict__ lo,
+                                                               const double *__restrict__ hi, double sd,
+                                                               const double *__restrict__ u, double *X_new,
+                                                               double *log_q_ratio, int *status)
+{
+    __shared__ double sh[kThreads];
+    double lq = 0.0;
+    for (int e = threadIdx.x; e < B.nb * d; e += kThreads) {
+        const int b = e / d, q = e % d;
+        const int64_t m = B.idx[b];
+        if (m < 0 || m >= n) {
+            atomicOr(status, kBadBlock);
+            continue;
+        }
+        const double x = X[m * d + q], l = lo[m * d + q], h = hi[m * d + q];
+        if (!(l <= x && x <= h) || !(sd > 0.0)) {
+            atomicOr(status, kBadProposal);
+            continue;
+        }
+        const double Pa = normcdf((l - x) / sd), Pb = normcdf((h - x) / sd);
+        const double y = fmin(fmax(x + sd * normcdfinv(Pa + u[e] * (Pb - Pa)), l), h);
+        X_new[e] = y;
+        lq += log(Pb - Pa) - log(normcdf((h - y) / sd) - normcdf((l - y) / sd));
+    }
+    lq = block_sum(lq, sh);
+    if (threadIdx.x == 0)
+        *log_q_ratio = lq;
+}
+
 bool params_ok(const hawkes_params *p)
 {
     if (!p)
@@ -536,6 +660,40 @@ hawkes_status hawkes_mwg_step(hawkes_mwg *s, int32_t nb, const int64_t *idx, con
         return HAWKES_ERR_INVALID_ARG;
     return enqueue_proposal(s, nb, idx, X_new, true, log_q_ratio, log_u, reinterpret_cast<cudaStream_t>(stream),
                             out_delta, out_accepted);
+}
+
+hawkes_status hawkes_mwg_propose_circle(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *centers,
+                                        const double *radii, double eps, int32_t tries, const double *u,
+                                        hawkes_stream stream, double *X_new, double *log_q_ratio)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    if (s->d != 2)
+        return fail(s, HAWKES_ERR_INVALID_ARG, "circle proposals need D = 2");
+    if (nb < 0 || nb > s->max_block || tries < 1 || !(eps > 0.0) || !std::isfinite(eps) || !log_q_ratio ||
+        (nb > 0 && (!idx || !centers || !radii || !u || !X_new)))
+        return fail(s, HAWKES_ERR_INVALID_ARG, "bad circle-proposal arguments");
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    propose_circle_kernel<<<1, kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        s->X, s->n, Block{nb, idx, nullptr}, centers, radii, eps, tries, u, X_new, log_q_ratio, s->ctl + 1);
+    MWG_TRY(cudaGetLastError(), "circle proposals");
+    return HAWKES_OK;
+}
+
+hawkes_status hawkes_mwg_propose_box(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *lo,
+                                     const double *hi, double sd, const double *u, hawkes_stream stream,
+                                     double *X_new, double *log_q_ratio)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    if (nb < 0 || nb > s->max_block || !(sd > 0.0) || !std::isfinite(sd) || !log_q_ratio ||
+        (nb > 0 && (!idx || !lo || !hi || !u || !X_new)))
+        return fail(s, HAWKES_ERR_INVALID_ARG, "bad box-proposal arguments");
+    MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+    propose_box_kernel<<<1, kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        s->X, s->n, s->d, Block{nb, idx, nullptr}, lo, hi, sd, u, X_new, log_q_ratio, s->ctl + 1);
+    MWG_TRY(cudaGetLastError(), "box proposals");
+    return HAWKES_OK;
 }
 
 hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream)

@@ -171,3 +171,94 @@ def test_mwg_edge_cases():
     with pytest.raises(HawkesError, match="INVALID_ARG"):
         s.delta(np.arange(9), np.zeros((9, 2)))
     s.close()
+
+
+def circle_case(seed, n):
+    """Wildfire-like circle priors: centres at the observed points, radii from
+    fire areas, latent points inside their circles."""
+    rng = np.random.default_rng(seed)
+    w = synth.random_case(seed, n, 2, shuffle=True)
+    radii = rng.choice([0.05, 0.5, 5.0], size=n, p=[0.5, 0.3, 0.2])
+    ang = rng.uniform(0, 2 * np.pi, size=n)
+    rr = radii * np.sqrt(rng.uniform(size=n)) * 0.999
+    centers = w.X - np.stack([rr * np.cos(ang), rr * np.sin(ang)], axis=1)
+    return w, centers, radii
+
+
+def test_mwg_circle_proposals_match_oracle():
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesMwG
+
+    w, centers, radii = circle_case(31, 500)
+    s = HawkesMwG(torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"), w.params, max_block=64)
+    rng = np.random.default_rng(2)
+    for nb, eps, tries in ((1, 0.3, 4), (17, 1.5, 3), (64, 0.8, 8), (64, 3.0, 1)):
+        idx = rng.choice(w.n, size=nb, replace=False)
+        u = rng.uniform(size=(nb, tries, 2))
+        Xn, lq = s.propose_circle(idx, centers, radii, eps, tries, u)
+        Xr, lqr = oracle.circle_proposals(w.X[idx], centers[idx], radii[idx], eps, tries, u)
+        Xn = Xn.cpu().numpy()
+        assert np.max(np.abs(Xn - Xr)) <= 1e-12 * (1 + np.max(np.abs(Xr)))
+        assert abs(lq.item() - lqr) <= 1e-10 * (1 + abs(lqr)), (lq.item(), lqr)
+        inside = np.hypot(*(Xn - centers[idx]).T) < radii[idx]
+        assert inside.all()
+    s.close()
+
+
+def test_mwg_box_proposals_match_oracle():
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesMwG
+
+    w = synth.make_c3()  # wildfire-like boxes of sides 0.1, 1, 10 km
+    s = HawkesMwG(torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"), w.params, max_block=128)
+    rng = np.random.default_rng(4)
+    for nb, sd in ((1, 0.05), (33, 0.5), (128, 2.0)):
+        idx = rng.choice(w.n, size=nb, replace=False)
+        u = rng.uniform(size=(nb, w.d))
+        Xn, lq = s.propose_box(idx, w.box_lo, w.box_hi, sd, u)
+        Xr, lqr = oracle.box_proposals(w.X[idx], w.box_lo[idx], w.box_hi[idx], sd, u)
+        Xn = Xn.cpu().numpy()
+        assert np.max(np.abs(Xn - Xr)) <= 1e-9 * (1 + np.max(np.abs(Xr)))
+        assert abs(lq.item() - lqr) <= 1e-8 * (1 + abs(lqr)), (lq.item(), lqr)
+        assert np.all((Xn >= w.box_lo[idx]) & (Xn <= w.box_hi[idx]))
+    s.close()
+
+
+def test_mwg_circle_chain_on_device():
+    """Propose on the device, step on the device: the chain's decisions match
+    the oracle's deltas and ratios, and every location stays in its circle."""
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesMwG
+
+    w, centers, radii = circle_case(32, 400)
+    s = HawkesMwG(torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"), w.params, max_block=8)
+    rng = np.random.default_rng(6)
+    X = w.X.copy()
+    ell = oracle.loglik(w.t, X, w.params)
+    n_acc = 0
+    for k in range(25):
+        idx = rng.choice(w.n, size=8, replace=False)
+        u = rng.uniform(size=(8, 4, 2))
+        Xn, lq = s.propose_circle(idx, centers, radii, 0.5, 4, u)
+        Xr, lqr = oracle.circle_proposals(X[idx], centers[idx], radii[idx], 0.5, 4, u)
+        X1 = X.copy()
+        X1[idx] = Xr
+        ell1 = oracle.loglik(w.t, X1, w.params)
+        log_u = math.log(rng.uniform())
+        if abs(log_u - (ell1 - ell + lqr)) < 1e-6:
+            log_u -= 1e-3
+        dl, acc = s.step(torch.as_tensor(idx, device="cuda"), Xn, log_u, lq)
+        expect = log_u < ell1 - ell + lqr
+        assert bool(acc.item()) == expect
+        if expect:
+            X, ell = X1, ell1
+            n_acc += 1
+    Xg, _, _ = s.read()
+    Xg = Xg.cpu().numpy()
+    assert np.max(np.abs(Xg - X)) <= 1e-12 * (1 + np.max(np.abs(X)))
+    assert np.all(np.hypot(*(Xg - centers).T) < radii)
+    assert 0 < n_acc < 25
+    s.close()
