@@ -269,6 +269,65 @@ def bmds_workload(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: 
     return res
 
 
+def mwg_workload(dev, stream, l2) -> dict:
+    """Metropolis-within-Gibbs over the locations of the gunfire-like
+    workload (c2: N = 10,000, D = 2, 100 m boxes): per iteration a truncated
+    normal proposal for a block of B events and the device-side MH step,
+    30 iterations captured in one CUDA graph, timed with CUDA events."""
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import HawkesMwG, hawkes_loglik, HawkesContext
+
+    w = synth.make_c2()
+    t = torch.tensor(w.t, device=dev)
+    X = torch.tensor(w.X, device=dev)
+    lo = torch.tensor(w.box_lo, device=dev)
+    hi = torch.tensor(w.box_hi, device=dev)
+    iters = 30
+    gen = torch.Generator(device=dev).manual_seed(12)
+    res = {"workload": "c2_gunfire_like_n10000_d2", "n": w.n, "d": w.d, "iterations_per_graph": iters}
+    for nb in (1, 32):
+        s = HawkesMwG(t, X, w.params, max_block=nb)
+        idx = torch.stack([torch.randperm(w.n, generator=gen, device=dev)[:nb] for _ in range(iters)])
+        u = torch.rand((iters, nb, w.d), generator=gen, device=dev, dtype=torch.float64)
+        log_u = torch.log(torch.rand(iters, generator=gen, device=dev, dtype=torch.float64))
+        props = [(torch.empty((nb, w.d), dtype=torch.float64, device=dev),
+                  torch.empty((), dtype=torch.float64, device=dev)) for _ in range(iters)]
+        outs = [(torch.empty((), dtype=torch.float64, device=dev), torch.empty((), dtype=torch.int32, device=dev))
+                for _ in range(iters)]
+
+        def run():
+            for k in range(iters):
+                s.propose_box(idx[k], lo, hi, 0.02, u[k], out=props[k], check=False)
+                s.step(idx[k], props[k][0], log_u[k], props[k][1], out=outs[k], check=False)
+
+        run()
+        torch.cuda.synchronize()
+        s.sync_status()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                run()
+        torch.cuda.synchronize()
+        m = timed_calls(g.replay, stream, l2, reps=10, warm=2)
+        s.sync_status()
+        acc = int(sum(o[1].item() for o in outs))
+        per = m / iters
+        res[f"block_{nb}"] = {"ms_per_iteration": per, "iterations_per_s": 1e3 / per,
+                              "location_updates_per_s": nb * 1e3 / per,
+                              "fp64_pair_evals_per_iteration": 3 * nb * w.n, "accepted_last_replay": acc}
+        s.close()
+    # the same proposal evaluated by a full log-likelihood instead (what the increments avoid)
+    ctx = HawkesContext(device=dev.index or 0, max_n=w.n, max_d=w.d)
+    full = timed_calls(lambda: hawkes_loglik(ctx, t, X, w.params, "fp64", check=False), stream, l2, reps=5, warm=1)
+    res["full_fp64_loglik_ms"] = full
+    ctx.close()
+    return res
+
+
 def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: float, sms: int) -> dict:
     """Batched 64-set latent-space workload (one call, mixed path), one
     20-step HMC trajectory at N=1e4 (mixed path, CUDA graph) and the BMDS
@@ -280,7 +339,8 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     import synth
     from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad, hmc_leapfrog_trajectory
 
-    out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms)}
+    out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms),
+           "mwg_gunfire_like": mwg_workload(dev, stream, l2)}
     sets = synth.make_c4()
     sizes = [w.n for w in sets]
     dims = [w.d for w in sets]

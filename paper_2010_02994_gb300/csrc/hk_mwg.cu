@@ -23,6 +23,7 @@
 
 #include <math_constants.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -66,11 +67,12 @@ __device__ __forceinline__ double contrib(const double *xm, double tm, const dou
     return v;
 }
 
+template <int NT = kThreads>
 __device__ double block_sum(double v, double *sh)
 {
     sh[threadIdx.x] = v;
     __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
+    for (int o = NT / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
             sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
@@ -187,17 +189,20 @@ struct Block {
 
 // Every m: its position in the block (or -1), and for m outside the block
 // the change of its rate and log1p(Delta_m / lambda_m), summed per CTA.
-__global__ void __launch_bounds__(kThreads) columns_kernel(const double *__restrict__ t, const double *__restrict__ X,
-                                                           int64_t n, int d, Consts k, Block B, double *lam0,
-                                                           double *lam1, const int *active, int *pos,
-                                                           double *part, int *status)
+// Small CTAs, so that the FP64 work spreads over every SM.
+constexpr int kColThreads = 64;
+
+__global__ void __launch_bounds__(kColThreads) columns_kernel(const double *__restrict__ t,
+                                                              const double *__restrict__ X, int64_t n, int d,
+                                                              Consts k, Block B, double *lam0, double *lam1,
+                                                              const int *active, int *pos, double *part, int *status)
 {
-    __shared__ double sh[kThreads];
+    __shared__ double sh[kColThreads];
     __shared__ double sxo[kMaxBlock * kMaxDim], sxn[kMaxBlock * kMaxDim], stb[kMaxBlock];
     __shared__ int64_t sid[kMaxBlock];
     const double *lam = *active ? lam1 : lam0;
     double *lam_new = *active ? lam0 : lam1;
-    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
+    for (int b = threadIdx.x; b < B.nb; b += kColThreads) {
         const int64_t m = B.idx[b];
         const bool ok = m >= 0 && m < n;
         sid[b] = ok ? m : -1;
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) columns_kernel(const double *__restr
     }
     __syncthreads();
     double term = 0.0;
-    const int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
     if (m < n) {
         int p = -1;
         for (int b = 0; b < B.nb; ++b)
@@ -243,63 +248,73 @@ __global__ void __launch_bounds__(kThreads) columns_kernel(const double *__restr
             term = log_ratio(l, ln, delta);
         }
     }
-    term = block_sum(term, sh);
+    term = block_sum<kColThreads>(term, sh);
     if (threadIdx.x == 0)
         part[blockIdx.x] = term;
 }
 
-// One CTA per moved event b: its new rate over all events (moved ones at
-// their proposed places), and log lambda*_b - log lambda_b.
-__global__ void __launch_bounds__(kThreads) rows_kernel(const double *__restrict__ t, const double *__restrict__ X,
-                                                        int64_t n, int d, Consts k, Block B, double *lam0,
-                                                        double *lam1, const int *active, const int *pos,
-                                                        double *rowterm)
+// Moved event b's new rate over all events (moved ones at their proposed
+// places), split over `splits` CTAs per event (grid b x split), each adding
+// one contiguous range of events; the finish kernel adds the splits in order.
+constexpr int kRowThreads = 64;
+
+__global__ void __launch_bounds__(kRowThreads) rows_kernel(const double *__restrict__ t,
+                                                           const double *__restrict__ X, int64_t n, int d, Consts k,
+                                                           Block B, const int *pos, int splits, double *rowpart)
 {
-    __shared__ double sh[kThreads];
-    const double *lam = *active ? lam1 : lam0;
-    double *lam_new = *active ? lam0 : lam1;
-    const int b = blockIdx.x;
+    __shared__ double sh[kRowThreads];
+    const int b = blockIdx.x, sp = blockIdx.y;
     const int64_t mb = B.idx[b];
-    if (mb < 0 || mb >= n) {  // reported by the column kernel
-        if (threadIdx.x == 0)
-            rowterm[b] = 0.0;
-        return;
-    }
-    double xb[kMaxDim];
-    for (int q = 0; q < d; ++q)
-        xb[q] = B.xnew[(int64_t)b * d + q];
-    const double tb = t[mb];
+    const int64_t per = (n + splits - 1) / splits;
+    const int64_t lo = min((int64_t)sp * per, n), hi = min(lo + per, n);
     double s = 0.0;
-    for (int64_t m = threadIdx.x; m < n; m += kThreads) {
-        if (m == mb)
-            continue;
-        const int p = pos[m];
-        const double *xm = p >= 0 ? B.xnew + (int64_t)p * d : X + m * d;
-        s += contrib(xb, tb, xm, t[m], d, k);
+    if (mb >= 0 && mb < n) {  // a bad index is reported by the column kernel
+        double xb[kMaxDim];
+        for (int q = 0; q < d; ++q)
+            xb[q] = B.xnew[(int64_t)b * d + q];
+        const double tb = t[mb];
+        for (int64_t m = lo + threadIdx.x; m < hi; m += kRowThreads) {
+            if (m == mb)
+                continue;
+            const int p = pos[m];
+            const double *xm = p >= 0 ? B.xnew + (int64_t)p * d : X + m * d;
+            s += contrib(xb, tb, xm, t[m], d, k);
+        }
     }
-    const double lnew = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-        const double l = lam[mb];
-        lam_new[mb] = lnew;
-        rowterm[b] = (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
-    }
+    s = block_sum<kRowThreads>(s, sh);
+    if (threadIdx.x == 0)
+        rowpart[(int64_t)b * splits + sp] = s;
 }
 
-// Delta ell in a fixed order; in step mode the accept decision and, on
-// accept, the commit (moved locations, running ell, current-buffer flip).
+// Delta ell in a fixed order: the moved events' new rates (their splits
+// added in order) and log ratios, then the column partials; in step mode
+// the accept decision and, on accept, the commit (moved locations, running
+// ell, current-buffer flip).
 __global__ void __launch_bounds__(kThreads) finish_kernel(int ncta, const double *__restrict__ part, Block B,
-                                                          const double *__restrict__ rowterm, const int *status,
+                                                          int64_t n, int splits, const double *__restrict__ rowpart,
+                                                          double *lam0, double *lam1, const int *status,
                                                           double *out_delta, bool step, const double *log_q_ratio,
                                                           const double *log_u, int *accepted_out, double *X, int d,
                                                           int *active, double *loglik)
 {
     __shared__ double sh[kThreads];
     __shared__ int acc;
+    const double *lam = *active ? lam1 : lam0;
+    double *lam_new = *active ? lam0 : lam1;
     double v = 0.0;
+    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
+        const int64_t mb = B.idx[b];
+        if (mb < 0 || mb >= n)
+            continue;
+        double lnew = 0.0;
+        for (int sp = 0; sp < splits; ++sp)
+            lnew += rowpart[(int64_t)b * splits + sp];
+        const double l = lam[mb];
+        lam_new[mb] = lnew;
+        v += (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
+    }
     for (int i = threadIdx.x; i < ncta; i += kThreads)
         v += part[i];
-    for (int b = threadIdx.x; b < B.nb; b += kThreads)
-        v += rowterm[b];
     const double delta = block_sum(v, sh);
     if (threadIdx.x == 0) {
         const bool bad = *(volatile const int *)status != 0;
@@ -498,7 +513,7 @@ struct hawkes_mwg {
     // device buffers
     double *t = nullptr, *X = nullptr, *lam0 = nullptr, *lam1 = nullptr;
     double *part = nullptr;     // max(kRateSplit * n, column-kernel CTAs)
-    double *rowterm = nullptr;  // max_block
+    double *rowterm = nullptr;  // row-kernel partials: max_block x (2 SMs + 1)
     double *loglik = nullptr;   // running ell
     int *ctl = nullptr;         // [0] current rate buffer, [1] status
     int *pos = nullptr;         // n
@@ -541,6 +556,16 @@ hawkes_status enqueue_rates(hawkes_mwg *s, cudaStream_t st)
     return HAWKES_OK;
 }
 
+// CTAs per moved event in the row kernel: about two per SM in total, each
+// with at least one event per thread.  (FP64 runs at 1/64 of the FP32 rate
+// on this GPU, so one event's O(N) row must spread over many SMs.)
+int row_splits(const hawkes_mwg *s, int nb)
+{
+    const int64_t want = (2 * (int64_t)s->sms + std::max(nb, 1) - 1) / std::max(nb, 1);
+    const int64_t most = std::max<int64_t>(1, s->n / kRowThreads);
+    return (int)std::max<int64_t>(1, std::min(want, most));
+}
+
 hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new, bool step,
                                const double *log_q_ratio, const double *log_u, cudaStream_t st, double *out_delta,
                                int32_t *out_accepted)
@@ -553,17 +578,19 @@ hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, co
         return fail(s, HAWKES_ERR_INVALID_ARG, "log_u must be a device pointer");
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
     const Block B{nb, idx, X_new};
-    const int ncta = grid_for(s->n);
-    columns_kernel<<<ncta, kThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
-                                              s->part, s->ctl + 1);
+    const int ncta = (int)((s->n + kColThreads - 1) / kColThreads);
+    columns_kernel<<<ncta, kColThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
+                                                 s->part, s->ctl + 1);
     MWG_TRY(cudaGetLastError(), "column kernel");
+    const int splits = row_splits(s, nb);
     if (nb > 0) {
-        rows_kernel<<<nb, kThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
-                                             s->rowterm);
+        rows_kernel<<<dim3(nb, splits), kRowThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->pos, splits,
+                                                           s->rowterm);
         MWG_TRY(cudaGetLastError(), "row kernel");
     }
-    finish_kernel<<<1, kThreads, 0, st>>>(ncta, s->part, B, s->rowterm, s->ctl + 1, out_delta, step, log_q_ratio,
-                                          log_u, out_accepted, s->X, s->d, s->ctl, s->loglik);
+    finish_kernel<<<1, kThreads, 0, st>>>(ncta, s->part, B, s->n, splits, s->rowterm, s->lam0, s->lam1, s->ctl + 1,
+                                          out_delta, step, log_q_ratio, log_u, out_accepted, s->X, s->d, s->ctl,
+                                          s->loglik);
     MWG_TRY(cudaGetLastError(), "finish kernel");
     return HAWKES_OK;
 }
@@ -598,13 +625,13 @@ hawkes_status hawkes_mwg_create(int32_t device, const double *t, const double *X
         cudaGetLastError();
         return bail(HAWKES_ERR_CUDA);
     }
-    const size_t part_n = std::max<size_t>((size_t)kRateSplit * n, (size_t)grid_for(n));
+    const size_t part_n = std::max<size_t>((size_t)kRateSplit * n, (size_t)((n + kColThreads - 1) / kColThreads));
     if (cudaMalloc(&s->t, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&s->X, sizeof(double) * n * d) != cudaSuccess ||
         cudaMalloc(&s->lam0, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&s->lam1, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&s->part, sizeof(double) * part_n) != cudaSuccess ||
-        cudaMalloc(&s->rowterm, sizeof(double) * max_block) != cudaSuccess ||
+        cudaMalloc(&s->rowterm, sizeof(double) * (size_t)max_block * (2 * s->sms + 1)) != cudaSuccess ||
         cudaMalloc(&s->loglik, sizeof(double)) != cudaSuccess || cudaMalloc(&s->ctl, sizeof(int) * 2) != cudaSuccess ||
         cudaMalloc(&s->pos, sizeof(int) * n) != cudaSuccess) {
         cudaGetLastError();
