@@ -71,6 +71,9 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_hmc_trajectory.argtypes = [i64, i32, dp, dp, dp, dp, dp, pp, ctypes.c_double, i32,
                                           ctypes.c_double, dp, dp, dp, dp,
                                           ctypes.POINTER(ctypes.c_int32), i32]
+    lib.oracle_bmds_hmc_trajectory.argtypes = [i64, i32, dp, dp, dp, pp, dp, ctypes.c_double, ctypes.c_double, i32,
+                                               ctypes.c_double, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32), i32]
+    lib.oracle_bmds_hmc_trajectory.restype = ctypes.c_int
     lib.oracle_bmds.argtypes = [i64, i32, dp, dp, ctypes.c_double, dp, dp, dp, i32]
     lib.oracle_bmds.restype = ctypes.c_int
     lib.oracle_lens_area.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -236,6 +239,25 @@ class Oracle:
                                               _dp(H0), _dp(H1), ctypes.byref(acc), nthreads), "hmc_trajectory")
         return {"X": Xo, "p": po, "H0": float(H0[0]), "H1": float(H1[0]), "accepted": int(acc.value)}
 
+    def bmds_hmc_trajectory(self, t, X0, p0, params, Y, sigma2, eps, n_steps, log_u, nthreads: int = 0):
+        """One HMC proposal over the locations of the BMDS-Hawkes model
+        (potential -ell_Hawkes - ell_BMDS, unconstrained); as hmc_trajectory."""
+        t, X0 = _prep(t, X0)
+        n, d = X0.shape
+        p0 = _as_f64(p0).reshape(n, d)
+        Y = _as_f64(Y).reshape(n, n)
+        Xo = np.empty((n, d))
+        po = np.empty((n, d))
+        H0 = np.empty(1)
+        H1 = np.empty(1)
+        acc = ctypes.c_int32(0)
+        p = params_struct(params)
+        _check(self.lib.oracle_bmds_hmc_trajectory(n, d, _dp(t), _dp(X0), _dp(p0), ctypes.byref(p), _dp(Y),
+                                                   float(sigma2), float(eps), int(n_steps), float(log_u), _dp(Xo),
+                                                   _dp(po), _dp(H0), _dp(H1), ctypes.byref(acc), nthreads),
+               "bmds_hmc_trajectory")
+        return {"X": Xo, "p": po, "H0": float(H0[0]), "H1": float(H1[0]), "accepted": int(acc.value)}
+
     def bmds(self, Y, X, sigma2, nthreads: int = 0):
         """BMDS log-likelihood of Eq. (4) (up to a constant), its gradient in X
         and in sigma2: (ell, grad (N, D), d ell / d sigma2)."""
@@ -339,6 +361,10 @@ def hmc_trajectory(*a, **k):
 
 def bmds(*a, **k):
     return default().bmds(*a, **k)
+
+
+def bmds_hmc_trajectory(*a, **k):
+    return default().bmds_hmc_trajectory(*a, **k)
 
 
 def lens_area(*a, **k):

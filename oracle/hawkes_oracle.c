@@ -52,6 +52,9 @@ typedef struct {
     double mu0, tau_x, tau_t, theta, omega, h;
 } oracle_params;
 
+int oracle_bmds(int64_t n, int32_t d, const double *Y, const double *X, double sigma2, double *out_loglik,
+                double *grad, double *grad_sigma2, int32_t nthreads);
+
 static const double kPi = 3.14159265358979323846;
 
 /* ---------------------------------------------------------------- sums -- */
@@ -466,13 +469,34 @@ static int ell_and_grad(int64_t n, int d, const double *t, const double *X,
  * or X0 on rejection); p_out (nullable) the final momenta of the proposal.
  * box_lo/box_hi are n*d arrays or both NULL (unconstrained).
  */
-int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
-                          const double *X0, const double *p0,
-                          const double *box_lo, const double *box_hi,
-                          const oracle_params *p, double eps, int32_t n_steps,
-                          double log_u, double *X_out, double *p_out,
-                          double *out_H0, double *out_H1, int32_t *out_accepted,
-                          int32_t nthreads)
+/*
+ * Potential energy -U = ell(X) and its gradient for the HMC below: the
+ * Hawkes log-likelihood of Eq. (1) alone, or, for the BMDS-Hawkes model of
+ * Section 2.2.3, plus the BMDS log-likelihood of Eq. (4) with distances Y
+ * and variance sigma2 (both terms' gradients in X add).
+ */
+static int hmc_potential(int64_t n, int32_t d, const double *t, const double *X, const oracle_params *p,
+                         const double *Y, double sigma2, double *lam, double *ell, double *g, int32_t nthreads)
+{
+    ell_and_grad(n, d, t, X, p, lam, ell, g, nthreads);
+    if (!Y)
+        return ORACLE_OK;
+    double *gb = (double *)malloc(sizeof(double) * n * d);
+    double lb = 0.0;
+    if (!gb)
+        return ORACLE_ERR_ARG;
+    int rc = oracle_bmds(n, d, Y, X, sigma2, &lb, gb, NULL, nthreads);
+    *ell += lb;
+    for (int64_t i = 0; i < n * d; ++i)
+        g[i] += gb[i];
+    free(gb);
+    return rc;
+}
+
+static int hmc_core(int64_t n, int32_t d, const double *t, const double *X0, const double *p0,
+                    const double *box_lo, const double *box_hi, const oracle_params *p, const double *Y,
+                    double sigma2, double eps, int32_t n_steps, double log_u, double *X_out, double *p_out,
+                    double *out_H0, double *out_H1, int32_t *out_accepted, int32_t nthreads)
 {
     if (n < 1 || d < 1 || !params_ok(p) || !t || !X0 || !p0 || !X_out ||
         n_steps < 0 || !(eps > 0) || ((box_lo == NULL) != (box_hi == NULL)))
@@ -492,14 +516,14 @@ int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
     memcpy(X, X0, sizeof(double) * nd);
     memcpy(pm, p0, sizeof(double) * nd);
     double ell;
-    ell_and_grad(n, d, t, X, p, lam, &ell, g, nthreads);
+    int rc = hmc_potential(n, d, t, X, p, Y, sigma2, lam, &ell, g, nthreads);
     nsum k0 = {0, 0};
     for (int64_t i = 0; i < nd; ++i)
         nadd(&k0, 0.5 * (pm[i] * pm[i]));
     double H0 = -ell + nval(&k0);
     double half = 0.5 * eps;
     int bad = 0;
-    for (int32_t s = 0; s < n_steps; ++s) {
+    for (int32_t s = 0; s < n_steps && rc == ORACLE_OK; ++s) {
         for (int64_t i = 0; i < nd; ++i)
             pm[i] = pm[i] + half * g[i];
         for (int64_t i = 0; i < nd; ++i) {
@@ -507,7 +531,7 @@ int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
             if (box_lo)
                 bad |= reflect(&X[i], &pm[i], box_lo[i], box_hi[i]);
         }
-        ell_and_grad(n, d, t, X, p, lam, &ell, g, nthreads);
+        rc = hmc_potential(n, d, t, X, p, Y, sigma2, lam, &ell, g, nthreads);
         for (int64_t i = 0; i < nd; ++i)
             pm[i] = pm[i] + half * g[i];
     }
@@ -529,7 +553,33 @@ int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
     free(pm);
     free(g);
     free(lam);
-    return ORACLE_OK;
+    return rc;
+}
+
+int oracle_hmc_trajectory(int64_t n, int32_t d, const double *t,
+                          const double *X0, const double *p0,
+                          const double *box_lo, const double *box_hi,
+                          const oracle_params *p, double eps, int32_t n_steps,
+                          double log_u, double *X_out, double *p_out,
+                          double *out_H0, double *out_H1, int32_t *out_accepted,
+                          int32_t nthreads)
+{
+    return hmc_core(n, d, t, X0, p0, box_lo, box_hi, p, NULL, 0.0, eps, n_steps, log_u, X_out, p_out, out_H0,
+                    out_H1, out_accepted, nthreads);
+}
+
+/* HMC over the latent locations of the BMDS-Hawkes model (Section 3:
+ * potential -ell_Hawkes - ell_BMDS, unconstrained locations as in the
+ * influenza application), otherwise as oracle_hmc_trajectory. */
+int oracle_bmds_hmc_trajectory(int64_t n, int32_t d, const double *t, const double *X0, const double *p0,
+                               const oracle_params *p, const double *Y, double sigma2, double eps,
+                               int32_t n_steps, double log_u, double *X_out, double *p_out, double *out_H0,
+                               double *out_H1, int32_t *out_accepted, int32_t nthreads)
+{
+    if (!Y || !(sigma2 > 0) || !isfinite(sigma2))
+        return ORACLE_ERR_ARG;
+    return hmc_core(n, d, t, X0, p0, NULL, NULL, p, Y, sigma2, eps, n_steps, log_u, X_out, p_out, out_H0, out_H1,
+                    out_accepted, nthreads);
 }
 
 /* ----------------------------------------------------------------- BMDS -- */

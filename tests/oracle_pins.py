@@ -569,6 +569,32 @@ def pin_box_proposals(o):
     return ok, f"draw err {err:.2e}, ratio {lq:.6f} vs {lq_ref:.6f}"
 
 
+def _bmds_hmc_case(seed=41, n=12, d=3):
+    w = synth.random_case(seed, n, d, shuffle=True, extent=2.0, t_end=5.0)
+    Y, _ = bmds_case(seed, n, d)
+    rng = np.random.default_rng(seed)
+    return w, Y, rng.standard_normal(size=w.X.shape)
+
+
+def pin_bmds_hmc_reversible_and_energy(o):
+    """HMC on the BMDS-Hawkes potential: the leapfrog is reversible (negated
+    final momenta retrace the path) and the energy error falls as eps^2, which
+    only holds when the gradient is that of the summed potential."""
+    w, Y, p0 = _bmds_hmc_case()
+    out = o.bmds_hmc_trajectory(w.t, w.X, p0, w.params, Y, 0.4, 0.005, 12, -np.inf)
+    back = o.bmds_hmc_trajectory(w.t, out["X"], -out["p"], w.params, Y, 0.4, 0.005, 12, -np.inf)
+    ex, moved = _rel(back["X"], w.X), _rel(out["X"], w.X)
+    errs = []
+    for eps in (0.002, 0.001, 0.0005):
+        r = o.bmds_hmc_trajectory(w.t, w.X, p0, w.params, Y, 0.4, eps, int(round(0.016 / eps)), -np.inf)
+        errs.append(abs(r["H1"] - r["H0"]))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    h0 = -(o.loglik(w.t, w.X, w.params) + o.bmds(Y, w.X, 0.4)[0]) + 0.5 * float(np.sum(p0 * p0))
+    ok = (out["accepted"] == 1 and ex < 1e-9 and moved > 1e-3 and 3.0 < r1 < 5.3 and 3.0 < r2 < 5.3
+          and abs(out["H0"] - h0) <= 1e-10 * abs(h0))
+    return ok, f"dX={ex:.2e} moved={moved:.2e} dH ratios {r1:.2f} {r2:.2f}"
+
+
 ALL_PINS = {
     "brute_force": pin_brute_force,
     "space_time_quadrature": pin_space_time_quadrature,
@@ -593,4 +619,5 @@ ALL_PINS = {
     "lens_area": pin_lens_area,
     "circle_proposals": pin_circle_proposals,
     "box_proposals": pin_box_proposals,
+    "bmds_hmc": pin_bmds_hmc_reversible_and_energy,
 }

@@ -43,6 +43,8 @@ MUTANTS = {
     "circle_radius_not_sqrt": ("const double r = rho * sqrt(u[(b * tries + k) * 2]);",
                                "const double r = rho * u[(b * tries + k) * 2];"),
     "box_ratio_inverted": ("nadd(&lq, log(Zx) - log(Zy));", "nadd(&lq, log(Zy) - log(Zx));"),
+    "bmds_hmc_gradient_sign": ("        g[i] += gb[i];", "        g[i] -= gb[i];"),
+    "bmds_hmc_potential_dropped": ("    *ell += lb;", "    *ell += 0.0 * lb;"),
     "hmc_full_step_kicks": ("double half = 0.5 * eps;", "double half = eps;"),
     "hmc_reflection_keeps_momentum": ("            *x = 2.0 * lo - *x;\n            *pm = -*pm;", "            *x = 2.0 * lo - *x;"),
     "hmc_accept_inequality_reversed": ("log_u < H0 - H1) ? 1 : 0", "log_u > H0 - H1) ? 1 : 0"),
