@@ -351,6 +351,21 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
                                       const double *log_u, hawkes_precision prec, hawkes_stream stream,
                                       double *out_H0, double *out_H1, int32_t *out_accepted);
 
+/* One HMC proposal over the latent locations of the BMDS-Hawkes model
+ * (Section 2.2.3 and Section 3, the influenza application): potential
+ * U = -ell (Eq. (1)) - ell_B (Eq. (4), distances Y of type y_type, variance
+ * sigma2; see hawkes_bmds_loglik_grad), unconstrained locations, otherwise
+ * as hmc_leapfrog_trajectory (same arguments, H = U + |p|^2/2, one CUDA
+ * graph per shape cached in the context; the cache key includes Y's address
+ * and sigma2).  Each leapfrog step evaluates both gradients: the BMDS
+ * kernels run on the locations in the caller's order and their gradient is
+ * added to the Hawkes gradient before the kicks.  Both terms use `prec`. */
+hawkes_status hawkes_bmds_hmc_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
+                                         int64_t n, int32_t d, const hawkes_params *params, const void *Y,
+                                         hawkes_dtype y_type, double sigma2, double eps, int32_t n_steps,
+                                         const double *log_u, hawkes_precision prec, hawkes_stream stream,
+                                         double *out_H0, double *out_H1, int32_t *out_accepted);
+
 /* One HMC proposal for each of n_sets independent sets (laid out as in
  * hawkes_batch_loglik_grad), all advanced by one CUDA graph per shape: the
  * leapfrog of hmc_leapfrog_trajectory with each set's own step size, box

@@ -7,7 +7,8 @@ only marshals torch tensors into it.
 """
 from .api import (HawkesContext, HawkesError, HawkesMwG, hawkes_batch_hmc_trajectory, hawkes_batch_loglik_grad,  # noqa: F401
                   hawkes_loglik,
-                  hawkes_bmds_loglik_grad, hawkes_loglik_grad_locations, hawkes_loglik_noalloc,
+                  hawkes_bmds_hmc_trajectory, hawkes_bmds_loglik_grad, hawkes_loglik_grad_locations,
+                  hawkes_loglik_noalloc,
                   hawkes_self_excitation_prob,
                   hmc_leapfrog_trajectory, params_struct,
                   probe_pipe_rates,

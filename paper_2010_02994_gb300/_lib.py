@@ -35,7 +35,7 @@ EXPORTED = (
     "hawkes_ctx_get_tuning", "hawkes_autotune", "hawkes_batch_hmc_trajectory", "hawkes_self_excitation_prob",
     "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
     "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
-    "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box",
+    "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box", "hawkes_bmds_hmc_trajectory",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -110,6 +110,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hmc_leapfrog_trajectory.argtypes = [vp, dp, dp, dp, dp, dp, i64, i32, pp, ctypes.c_double, i32, dp, i32,
                                             vp, dp, dp, dp]
     lib.hmc_leapfrog_trajectory.restype = st
+    lib.hawkes_bmds_hmc_trajectory.argtypes = [vp, dp, dp, dp, i64, i32, pp, dp, i32, ctypes.c_double,
+                                               ctypes.c_double, i32, dp, i32, vp, dp, dp, dp]
+    lib.hawkes_bmds_hmc_trajectory.restype = st
     lib.hawkes_batch_loglik_grad.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i32), dp, dp, pp, i32,
                                              vp, dp, dp]
     lib.hawkes_batch_loglik_grad.restype = st

@@ -172,6 +172,37 @@ def hawkes_loglik_grad_locations(ctx: HawkesContext, t, X, params, precision="mi
     return (ell, g, gp) if grad_params else (ell, g)
 
 
+def hawkes_bmds_hmc_trajectory(ctx: HawkesContext, t, X, p0, params, Y, sigma2: float, eps: float, n_steps: int,
+                               log_u, precision="mixed", check: bool = True):
+    """One HMC proposal over the locations of the BMDS-Hawkes model (potential
+    -ell - ell_B).  X is updated in place when accepted.  Y is (N, N), float64
+    or float32.  Returns (H0, H1, accepted) as device tensors."""
+    t = _dev_f64(t, "t")
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()):
+        raise TypeError("X must be a contiguous float64 CUDA tensor (it is updated in place)")
+    n, d, _ = _shape(t, X)
+    p0 = _dev_f64(p0, "p0")
+    if not isinstance(Y, torch.Tensor) or not Y.is_cuda or Y.dtype not in (torch.float64, torch.float32):
+        raise TypeError("Y must be a float64 or float32 CUDA tensor")
+    Y = Y.contiguous()
+    if Y.shape != (n, n):
+        raise ValueError("Y must be (N, N)")
+    if not isinstance(log_u, torch.Tensor):
+        log_u = torch.tensor(float(log_u), dtype=torch.float64, device=t.device)
+    log_u = _dev_f64(log_u, "log_u")
+    H0 = torch.empty((), dtype=torch.float64, device=t.device)
+    H1 = torch.empty((), dtype=torch.float64, device=t.device)
+    acc = torch.empty((), dtype=torch.int32, device=t.device)
+    p = params_struct(params)
+    ctx.check(ctx.lib.hawkes_bmds_hmc_trajectory(ctx.handle, _ptr(t), _ptr(X), _ptr(p0), n, d, ctypes.byref(p),
+                                                 _ptr(Y), 1 if Y.dtype == torch.float32 else 0, float(sigma2),
+                                                 float(eps), int(n_steps), _ptr(log_u), _precision(precision),
+                                                 ctx.stream(), _ptr(H0), _ptr(H1), _ptr(acc)))
+    if check:
+        ctx.sync_status()
+    return H0, H1, acc
+
+
 def hawkes_bmds_loglik_grad(ctx: HawkesContext, Y, X, sigma2: float, precision="mixed", grad: bool = True,
                             check: bool = True, out=None):
     """BMDS likelihood of Eq. (4) with its gradients: (ell_B, d ell_B/d X,

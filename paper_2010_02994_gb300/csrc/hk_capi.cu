@@ -94,6 +94,7 @@ struct hawkes_ctx {
     DeviceBuffer ws;
     size_t ws_generation = 0;
     DeviceBuffer bmds_ws;  // BMDS partial-sum slots
+    DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
     // options
     int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
     std::vector<ProfEvent> prof_pending;
@@ -792,6 +793,8 @@ void hawkes_ctx_destroy(hawkes_ctx *ctx)
         cudaFree(ctx->ws.ptr);
     if (ctx->bmds_ws.ptr)
         cudaFree(ctx->bmds_ws.ptr);
+    if (ctx->bmds_hmc.ptr)
+        cudaFree(ctx->bmds_hmc.ptr);
     if (ctx->ctl)
         cudaFree(ctx->ctl);
     delete ctx;
@@ -1004,6 +1007,27 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
     return enqueue_nan_on_invalid(ctx, out_prob, n, nullptr, 0, s);
 }
 
+// Grow-only device buffer; synchronizes the device before replacing it.
+static hawkes_status grow_buffer(hawkes_ctx *ctx, DeviceBuffer &b, size_t need, const char *what, size_t zero_head)
+{
+    if (need <= b.bytes)
+        return HAWKES_OK;
+    HK_TRY(cudaDeviceSynchronize(), "synchronize before growing a workspace");
+    if (b.ptr)
+        cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.ptr, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, HAWKES_ERR_OOM, std::string(what) + " of " + std::to_string(need) + " bytes");
+    }
+    b.bytes = need;
+    if (zero_head)
+        HK_TRY(cudaMemset(b.ptr, 0, zero_head), "clear workspace head");
+    ++ctx->ws_generation;
+    return HAWKES_OK;
+}
+
 size_t hawkes_bmds_workspace_bytes(int64_t n, int32_t d, hawkes_precision prec)
 {
     if (n < 1 || n > (int64_t)1 << 30 || d < 1 || d > kMaxD ||
@@ -1033,20 +1057,9 @@ hawkes_status hawkes_bmds_loglik_grad(hawkes_ctx *ctx, const void *Y, hawkes_dty
     HK_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = prec == HAWKES_PREC_FP64;
-    const size_t need = bmds_workspace_bytes(n, d, fp64);
-    if (need > ctx->bmds_ws.bytes) {
-        HK_TRY(cudaDeviceSynchronize(), "synchronize before growing the BMDS workspace");
-        if (ctx->bmds_ws.ptr)
-            cudaFree(ctx->bmds_ws.ptr);
-        ctx->bmds_ws.ptr = nullptr;
-        ctx->bmds_ws.bytes = 0;
-        if (cudaMalloc(&ctx->bmds_ws.ptr, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, HAWKES_ERR_OOM, "BMDS workspace of " + std::to_string(need) + " bytes");
-        }
-        ctx->bmds_ws.bytes = need;
-        HK_TRY(cudaMemset(ctx->bmds_ws.ptr, 0, 256), "clear the BMDS ticket");
-    }
+    hawkes_status gst = grow_buffer(ctx, ctx->bmds_ws, bmds_workspace_bytes(n, d, fp64), "BMDS workspace", 256);
+    if (gst != HAWKES_OK)
+        return gst;
     HK_TRY(launch_bmds(Y, y_type == HAWKES_F32, X, n, d, sigma2, fp64, ctx->bmds_ws.ptr, reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus),
                        out_loglik, out_grad_X, out_grad_sigma2, s, &ctx->launches_own),
            "BMDS kernels");
@@ -1140,11 +1153,20 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
 
 // One HMC proposal per set (Section 3), all sets advanced together; the
 // trajectory after the prologue is one CUDA graph cached per shape.
+// A BMDS term added to the HMC potential (single set): distances Y of
+// element type y_f32 ? float : double, variance sigma2.
+struct BmdsTerm {
+    const void *Y;
+    bool y_f32;
+    double sigma2;
+};
+
 static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *counts, const int32_t *dims,
                                 const double *t, double *X_inout, const double *p0, const double *box_lo,
                                 const double *box_hi, const hawkes_params *params, const double *eps,
                                 int32_t n_steps, const double *log_u, hawkes_precision prec, hawkes_stream stream,
-                                double *out_H0, double *out_H1, int32_t *out_accepted)
+                                double *out_H0, double *out_H1, int32_t *out_accepted,
+                                const BmdsTerm *bmds = nullptr)
 {
     hawkes_status st;
     if (!p0 || !log_u || !out_H0 || !out_H1 || !out_accepted)
@@ -1180,8 +1202,30 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
     HK_TRY(cudaMemcpyAsync(d_logu, log_u, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s), "log u");
     HK_TRY(cudaMemsetAsync(ctx->hint, 0, sizeof(int32_t) * 2 * ns, s), "flags");
 
+    // BMDS term: its workspace and the caller-order buffers exist before any capture
+    double *bx = nullptr, *bg = nullptr, *bl = nullptr;
+    if (bmds) {
+        const int64_t nd = counts[0] * dims[0];
+        if ((st = grow_buffer(ctx, ctx->bmds_ws, bmds_workspace_bytes(counts[0], dims[0], fp64), "BMDS workspace",
+                              256)) != HAWKES_OK)
+            return st;
+        if ((st = grow_buffer(ctx, ctx->bmds_hmc, sizeof(double) * (2 * nd + 32), "BMDS HMC buffers", 0)) !=
+            HAWKES_OK)
+            return st;
+        bx = static_cast<double *>(ctx->bmds_hmc.ptr);
+        bg = bx + nd;
+        bl = bg + nd;
+    }
+
     // the trajectory itself: captured once per shape, replayed as a graph
     std::vector<int64_t> key = {n_steps, (int64_t)prec, box ? 1 : 0, (int64_t)ctx->ws_generation, ns};
+    if (bmds) {
+        int64_t sbits;
+        std::memcpy(&sbits, &bmds->sigma2, sizeof(sbits));
+        key.push_back((int64_t)reinterpret_cast<intptr_t>(bmds->Y));
+        key.push_back(bmds->y_f32 ? 2 : 1);
+        key.push_back(sbits);
+    }
     for (int k = 0; k < ns; ++k) {
         key.push_back(counts[k]);
         key.push_back(dims[k]);
@@ -1198,11 +1242,27 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
         cudaStream_t es = capture ? cs : s;
         if (capture)
             HK_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        // the BMDS term of the potential, evaluated at the current locations
+        auto add_bmds = [&]() -> hawkes_status {
+            if (!bmds)
+                return HAWKES_OK;
+            HK_TRY(launch_to_caller(w, ctx->d_set_row0, w.x64, bx, pl.total_rows, es), "BMDS locations");
+            ++ctx->launches_own;
+            HK_TRY(launch_bmds(bmds->Y, bmds->y_f32, bx, counts[0], dims[0], bmds->sigma2, fp64, ctx->bmds_ws.ptr,
+                               reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, bg, nullptr, es,
+                               &ctx->launches_own),
+                   "BMDS kernels");
+            HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, bg, ctx->hg, pl.total_rows, bl, es), "BMDS gradient");
+            ++ctx->launches_own;
+            return HAWKES_OK;
+        };
         auto body = [&]() -> hawkes_status {
             hawkes_status r;
             if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                 return r;
             if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+                return r;
+            if ((r = add_bmds()) != HAWKES_OK)
                 return r;
             HK_TRY(launch_energy(w, ctx->hp, d_H0, es), "H0");
             for (int32_t k = 0; k < n_steps; ++k) {
@@ -1213,6 +1273,8 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                 if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                     return r;
                 if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+                    return r;
+                if ((r = add_bmds()) != HAWKES_OK)
                     return r;
             }
             if (n_steps > 0)
@@ -1271,6 +1333,26 @@ hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *
         return st;
     return hmc_common(ctx, 1, &n, &d, t, X_inout, p0, box_lo, box_hi, params, &eps, n_steps, log_u, prec, stream,
                       out_H0, out_H1, out_accepted);
+}
+
+hawkes_status hawkes_bmds_hmc_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
+                                         int64_t n, int32_t d, const hawkes_params *params, const void *Y,
+                                         hawkes_dtype y_type, double sigma2, double eps, int32_t n_steps,
+                                         const double *log_u, hawkes_precision prec, hawkes_stream stream,
+                                         double *out_H0, double *out_H1, int32_t *out_accepted)
+{
+    hawkes_status st = check_common(ctx, t, X_inout, n, d, params, prec);
+    if (st != HAWKES_OK)
+        return st;
+    if (!Y)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "Y must be a device pointer");
+    if (y_type != HAWKES_F64 && y_type != HAWKES_F32)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "y_type must be HAWKES_F64 or HAWKES_F32");
+    if (!(sigma2 > 0.0) || !std::isfinite(sigma2))
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "sigma2 must be finite and > 0");
+    const BmdsTerm bt{Y, y_type == HAWKES_F32, sigma2};
+    return hmc_common(ctx, 1, &n, &d, t, X_inout, p0, nullptr, nullptr, params, &eps, n_steps, log_u, prec, stream,
+                      out_H0, out_H1, out_accepted, &bt);
 }
 
 hawkes_status hawkes_batch_hmc_trajectory(hawkes_ctx *ctx, int32_t n_sets, const int64_t *offsets,

@@ -184,6 +184,39 @@ __global__ void scatter_kernel(Work w, const int64_t *set_row0, const double *__
     }
 }
 
+// Sorted rows (stride kMaxD) to the caller's order (row-major, width d),
+// for every row of every set.
+__global__ void to_caller_kernel(Work w, const int64_t *set_row0, const double *__restrict__ Xs,
+                                 double *__restrict__ X_out, int64_t total_rows)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const SetDesc &S = w.sets[set_of_row(w, set_row0, r)];
+        if (r - S.row0 >= S.n)
+            continue;
+        for (int k = 0; k < S.d; ++k)
+            X_out[S.x0 + (int64_t)w.perm[r] * S.d + k] = Xs[r * kMaxD + k];
+    }
+}
+
+// g_sorted += g (caller order) and, once, set_loglik[0] += *ell_add: folds a
+// second potential term (BMDS, evaluated in the caller's order) into the
+// Hawkes gradient and log-likelihood that the leapfrog and energy read.
+__global__ void add_caller_term_kernel(Work w, const int64_t *set_row0, const double *__restrict__ g,
+                                       double *__restrict__ g_sorted, int64_t total_rows, const double *ell_add)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        w.set_loglik[0] += *ell_add;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const SetDesc &S = w.sets[set_of_row(w, set_row0, r)];
+        if (r - S.row0 >= S.n)
+            continue;
+        for (int k = 0; k < S.d; ++k)
+            g_sorted[r * kMaxD + k] += g[S.x0 + (int64_t)w.perm[r] * S.d + k];
+    }
+}
+
 __global__ void set_scalar_kernel(double *dst, double v) { *dst = v; }
 
 int grid_for(int64_t n)
@@ -238,6 +271,20 @@ cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double 
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s)
 {
     scatter_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, Xs, X_out, accepted, total_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_caller(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
+                             int64_t total_rows, cudaStream_t s)
+{
+    to_caller_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, Xs, X_out, total_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const double *g, double *g_sorted,
+                                   int64_t total_rows, const double *ell_add, cudaStream_t s)
+{
+    add_caller_term_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, g, g_sorted, total_rows, ell_add);
     return cudaGetLastError();
 }
 

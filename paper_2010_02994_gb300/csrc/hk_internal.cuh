@@ -170,6 +170,10 @@ cudaError_t launch_accept(const double *H0, const double *H1, const double *log_
 cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s);
 cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s);
+cudaError_t launch_to_caller(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
+                             int64_t total_rows, cudaStream_t s);
+cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const double *g, double *g_sorted,
+                                   int64_t total_rows, const double *ell_add, cudaStream_t s);
 
 // hk_bmds.cu (BMDS likelihood of Eq. (4) and its gradients)
 size_t bmds_workspace_bytes(int64_t n, int d, bool fp64);
