@@ -328,6 +328,36 @@ def mwg_workload(dev, stream, l2) -> dict:
     return res
 
 
+def bmds_hawkes_hmc_workload(dev, stream, l2, steps: int = 20) -> dict:
+    """HMC over the latent locations of the BMDS-Hawkes model (the influenza
+    application): N = 4,733, D = 6, potential -ell - ell_B, `steps` leapfrog
+    steps per trajectory (one CUDA graph), mixed precision with FP32 Y.  The
+    paper reports 80 M states in about 10 days on a Titan V (about 93 per
+    second) without stating the number of leapfrog steps; that figure is
+    context, not a like-for-like comparison."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_bmds_hmc_trajectory
+
+    w, b = synth.make_bmds_hawkes()
+    ctx = HawkesContext(device=dev.index or 0, max_n=w.n, max_d=w.d)
+    t = torch.tensor(w.t, device=dev)
+    X = torch.tensor(w.X, device=dev)
+    Y = torch.tensor(b.Y, device=dev).float()
+    p0 = torch.tensor(np.random.default_rng(3).standard_normal(size=w.X.shape), device=dev)
+    log_u = torch.tensor(-1e30, dtype=torch.float64, device=dev)
+    eps = 5e-4
+    m = timed_calls(lambda: hawkes_bmds_hmc_trajectory(ctx, t, X, p0, w.params, Y, b.sigma2, eps, steps, log_u,
+                                                       "mixed", check=False), stream, l2, reps=10, warm=2)
+    ctx.sync_status()
+    ctx.close()
+    return {"workload": w.name, "n": w.n, "d": w.d, "leapfrog_steps": steps, "precision": "mixed, FP32 Y",
+            "ms_per_trajectory": m, "trajectories_per_s": 1e3 / m, "gradient_evals_per_s": (steps + 1) * 1e3 / m,
+            "paper_context": "80 M states / ~10 days = ~93 states/s on a Titan V, leapfrog steps not stated"}
+
+
 def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: float, sms: int) -> dict:
     """Batched 64-set latent-space workload (one call, mixed path), one
     20-step HMC trajectory at N=1e4 (mixed path, CUDA graph) and the BMDS
@@ -340,7 +370,8 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad, hmc_leapfrog_trajectory
 
     out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms),
-           "mwg_gunfire_like": mwg_workload(dev, stream, l2)}
+           "mwg_gunfire_like": mwg_workload(dev, stream, l2),
+           "bmds_hawkes_hmc_influenza_like": bmds_hawkes_hmc_workload(dev, stream, l2)}
     sets = synth.make_c4()
     sizes = [w.n for w in sets]
     dims = [w.d for w in sets]

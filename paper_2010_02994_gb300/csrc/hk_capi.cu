@@ -171,20 +171,24 @@ int choose_warps(const hawkes_ctx *ctx, int64_t n, int d, bool theta)
 {
     if (ctx->opt_warps > 0)
         return ctx->opt_warps;
+    const int R = rows_per_lane(d);
+    auto items_for = [&](int wv) {
+        const int64_t B = 32LL * R * wv;
+        const int64_t T = (n + B - 1) / B;
+        return T * (T + 1) / 2;
+    };
+    // a tuned shape (measured at one size of its octave) is kept only while
+    // it leaves at least three pair blocks per SM at this size
     const int tw = ctx->tune_warps[d][size_bucket(n)];
     if (tw > 0 && pass_smem_bytes(d, 2, tw) <= 200 * 1024 &&
-        (!theta || pass_smem_bytes(d, 3, tw) <= 200 * 1024))
+        (!theta || pass_smem_bytes(d, 3, tw) <= 200 * 1024) && items_for(tw) >= 3LL * ctx->sm_count)
         return tw;
-    const int R = rows_per_lane(d);
     const int candidates[4] = {8, 4, 2, 1};
     for (int wv : candidates) {
         // shared memory per CTA must leave room for two CTAs per SM
         if (pass_smem_bytes(d, 2, wv) > 110 * 1024 || (theta && pass_smem_bytes(d, 3, wv) > 110 * 1024))
             continue;
-        const int64_t B = 32LL * R * wv;
-        const int64_t T = (n + B - 1) / B;
-        const int64_t items = T * (T + 1) / 2;
-        if (items >= 6LL * ctx->sm_count)
+        if (items_for(wv) >= 3LL * ctx->sm_count)
             return wv;
     }
     return 1;
@@ -356,7 +360,7 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
     c.take<char>(sort_bytes);
     for (int k = 0; k < 4; ++k)
         c.take<double>(pl.total_rows * kMaxD);
-    c.take<double>(4 * ns + 8);
+    c.take<double>((4 + kEnergyParts) * ns + 8);
     c.take<int32_t>(2 * ns + 8);
     return c.off + 256;
 }
@@ -433,7 +437,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     ctx->hg = c.take<double>(pl.total_rows * kMaxD);
     ctx->hlo = c.take<double>(pl.total_rows * kMaxD);
     ctx->hhi = c.take<double>(pl.total_rows * kMaxD);
-    ctx->hscal = c.take<double>(4 * ns + 8);
+    ctx->hscal = c.take<double>((4 + kEnergyParts) * ns + 8);
     ctx->hint = c.take<int32_t>(2 * ns + 8);
     w.set_flags = ctx->ctl + kCtlSetFlags;
     w.set_cmmax = ctx->ctl + kCtlSetFlags + ctx->ctl_sets;
@@ -1264,7 +1268,7 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                 return r;
             if ((r = add_bmds()) != HAWKES_OK)
                 return r;
-            HK_TRY(launch_energy(w, ctx->hp, d_H0, es), "H0");
+            HK_TRY(launch_energy(w, ctx->hp, d_H0, ctx->hscal + 4 * ns, es), "H0");
             for (int32_t k = 0; k < n_steps; ++k) {
                 HK_TRY(launch_kick_drift(w, ctx->d_set_row0, ctx->hp, ctx->hg, box ? ctx->hlo : nullptr,
                                          box ? ctx->hhi : nullptr, d_eps, pl.total_rows, k == 0 ? 1 : 2, !fp64,
@@ -1279,7 +1283,7 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
             }
             if (n_steps > 0)
                 HK_TRY(launch_kick(w, ctx->d_set_row0, ctx->hp, ctx->hg, d_eps, pl.total_rows, es), "leapfrog kick");
-            HK_TRY(launch_energy(w, ctx->hp, d_H1, es), "H1");
+            HK_TRY(launch_energy(w, ctx->hp, d_H1, ctx->hscal + 4 * ns, es), "H1");
             HK_TRY(launch_accept(d_H0, d_H1, d_logu, d_bad, d_acc, ns, es), "accept");
             return HAWKES_OK;
         };

@@ -97,6 +97,43 @@ __device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ 
     return (double)s - (double)c;
 }
 
+// The same ordered compensated sums for nv <= kMaxD values at once (value q
+// at p[q * vstride + k * stride]): every value is added in the order
+// k = 0, 1, ..., exactly as ordered_strided_sum does, but the loads of four
+// slots of all values are issued together, so a row's gradient costs a
+// quarter of the memory round trips of nv separate sums.
+__device__ __forceinline__ void ordered_strided_sums(const float *__restrict__ p, int nv, int64_t vstride, int count,
+                                                     int64_t stride, double *out)
+{
+    float s[kMaxD], c[kMaxD];
+#pragma unroll
+    for (int q = 0; q < kMaxD; ++q)
+        s[q] = c[q] = 0.0f;
+    for (int k = 0; k < count; k += 4) {
+        float v[4][kMaxD];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < kMaxD; ++q)
+                v[u][q] = (q < nv && k + u < count) ? p[(int64_t)(k + u) * stride + (int64_t)q * vstride] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < kMaxD; ++q) {
+                if (q < nv && k + u < count) {
+                    const float y = v[u][q] - c[q];
+                    const float t = s[q] + y;
+                    c[q] = (t - s[q]) - y;
+                    s[q] = t;
+                }
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxD; ++q)
+        if (q < nv)
+            out[q] = (double)s[q] - (double)c[q];
+}
+
 struct PairFp64 {
     double a, b, c, Cmu, Cxi, omega, itx2, ih2;
     __device__ explicit PairFp64(const SetDesc &S)
@@ -150,10 +187,9 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
                 lam = acc.value();
             }
         } else if (theta) {
-            double v[kPass1ThetaVals];
-            for (int q = 0; q < kPass1ThetaVals; ++q)
-                v[q] = ordered_strided_sum(w.P1 + S.part0 + (int64_t)q * S.npad + i, S.nblk,
-                                           (int64_t)kPass1ThetaVals * S.npad);
+            double v[kMaxD];
+            ordered_strided_sums(w.P1 + S.part0 + i, kPass1ThetaVals, S.npad, S.nblk,
+                                 (int64_t)kPass1ThetaVals * S.npad, v);
             const double sum = v[0] + v[1];
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
@@ -368,9 +404,9 @@ __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, dou
             atomicOr(w.status, kStZeroRate);
         if (w.w32[r] == 0.0f)
             return;  // a flagged row: fixup_grad_kernel writes its gradient
+        ordered_strided_sums(w.P2 + S.part2_0 + i, d, S.npad, S.nblk, (int64_t)d * S.npad, gv);
         for (int q = 0; q < d; ++q)
-            gv[q] = S.Cg * ordered_strided_sum(w.P2 + S.part2_0 + (int64_t)q * S.npad + i, S.nblk,
-                                               (int64_t)d * S.npad);
+            gv[q] *= S.Cg;
         if (w.counters[2] > 0) {
             // contributions through the flagged rows' own rates:
             // w_n [mu_nm / tau_x^2 + xi_nm / h^2] (x_n - x_m), xi_nm when t_m < t_n

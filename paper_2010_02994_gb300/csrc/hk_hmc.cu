@@ -134,13 +134,20 @@ __global__ void kick_kernel(Work w, const int64_t *set_row0, double *__restrict_
     }
 }
 
-// H = -ell + sum p^2/2 of every set (one CTA per set, fixed-order reduction).
-__global__ void __launch_bounds__(1024) energy_kernel(Work w, const double *__restrict__ p, double *H_out)
+// H = -ell + sum p^2/2 of every set.  The FP64 sum of p^2/2 is split over
+// kEnergyParts CTAs per set (FP64 is 1/64 of the FP32 rate here, so one SM
+// per set would dominate a short trajectory step); each writes a
+// compensated partial, and a one-CTA-per-set kernel adds them in order.
+__global__ void __launch_bounds__(256) energy_parts_kernel(Work w, const double *__restrict__ p, double *parts)
 {
-    __shared__ double sh[1024];
-    const SetDesc &S = w.sets[blockIdx.x];
+    __shared__ double sh[256];
+    const int set = blockIdx.x, part = blockIdx.y;
+    const SetDesc &S = w.sets[set];
+    const int64_t total = (int64_t)S.n * S.d;
+    const int64_t per = (total + kEnergyParts - 1) / kEnergyParts;
+    const int64_t lo = min((int64_t)part * per, total), hi = min(lo + per, total);
     double s = 0.0, c = 0.0;
-    for (int64_t i = threadIdx.x; i < (int64_t)S.n * S.d; i += blockDim.x) {
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const int64_t r = S.row0 + i / S.d;
         const double v = p[r * kMaxD + i % S.d];
         const double x = __dmul_rn(0.5, __dmul_rn(v, v));
@@ -156,7 +163,18 @@ __global__ void __launch_bounds__(1024) energy_kernel(Work w, const double *__re
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        H_out[blockIdx.x] = -w.set_loglik[blockIdx.x] + sh[0];
+        parts[set * kEnergyParts + part] = sh[0];
+}
+
+__global__ void energy_finish_kernel(Work w, const double *__restrict__ parts, double *H_out)
+{
+    const int set = blockIdx.x * blockDim.x + threadIdx.x;
+    if (set >= w.nsets)
+        return;
+    double k = 0.0;
+    for (int q = 0; q < kEnergyParts; ++q)
+        k += parts[set * kEnergyParts + q];
+    H_out[set] = -w.set_loglik[set] + k;
 }
 
 __global__ void accept_kernel(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
@@ -219,13 +237,18 @@ __global__ void add_caller_term_kernel(Work w, const int64_t *set_row0, const do
 
 __global__ void set_scalar_kernel(double *dst, double v) { *dst = v; }
 
+// Element-wise HMC kernels run 64-thread CTAs: their FP64 updates are few
+// per row, and small CTAs spread them over every SM (FP64 is 1/64 of the
+// FP32 rate on this GPU).
+constexpr int kElemThreads = 64;
+
 int grid_for(int64_t n)
 {
-    int64_t g = (n + 255) / 256;
+    int64_t g = (n + kElemThreads - 1) / kElemThreads;
     if (g < 1)
         g = 1;
-    if (g > 2048)
-        g = 2048;
+    if (g > 8192)
+        g = 8192;
     return (int)g;
 }
 
@@ -234,7 +257,7 @@ int grid_for(int64_t n)
 cudaError_t launch_gather_sorted(const Work &w, const int64_t *set_row0, const double *src, double *dst,
                                  int64_t total_rows, double pad, cudaStream_t s)
 {
-    gather_sorted_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, src, dst, total_rows, pad);
+    gather_sorted_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, src, dst, total_rows, pad);
     return cudaGetLastError();
 }
 
@@ -242,7 +265,7 @@ cudaError_t launch_kick_drift(const Work &w, const int64_t *set_row0, double *p,
                               const double *hi, const double *eps_dev, int64_t total_rows, int kicks, bool repack,
                               int32_t *refl_bad, cudaStream_t s)
 {
-    kick_drift_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, p, g, lo, hi, eps_dev, total_rows, kicks,
+    kick_drift_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, p, g, lo, hi, eps_dev, total_rows, kicks,
                                                            repack ? 1 : 0, refl_bad);
     return cudaGetLastError();
 }
@@ -250,13 +273,14 @@ cudaError_t launch_kick_drift(const Work &w, const int64_t *set_row0, double *p,
 cudaError_t launch_kick(const Work &w, const int64_t *set_row0, double *p, const double *g, const double *eps_dev,
                         int64_t total_rows, cudaStream_t s)
 {
-    kick_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, p, g, eps_dev, total_rows);
+    kick_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, p, g, eps_dev, total_rows);
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const Work &w, const double *p, double *H_out, cudaStream_t s)
+cudaError_t launch_energy(const Work &w, const double *p, double *H_out, double *parts, cudaStream_t s)
 {
-    energy_kernel<<<w.nsets, 1024, 0, s>>>(w, p, H_out);
+    energy_parts_kernel<<<dim3(w.nsets, kEnergyParts), 256, 0, s>>>(w, p, parts);
+    energy_finish_kernel<<<(w.nsets + 127) / 128, 128, 0, s>>>(w, parts, H_out);
     return cudaGetLastError();
 }
 
@@ -270,21 +294,21 @@ cudaError_t launch_accept(const double *H0, const double *H1, const double *log_
 cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s)
 {
-    scatter_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, Xs, X_out, accepted, total_rows);
+    scatter_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, Xs, X_out, accepted, total_rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_to_caller(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                              int64_t total_rows, cudaStream_t s)
 {
-    to_caller_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, Xs, X_out, total_rows);
+    to_caller_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, Xs, X_out, total_rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const double *g, double *g_sorted,
                                    int64_t total_rows, const double *ell_add, cudaStream_t s)
 {
-    add_caller_term_kernel<<<grid_for(total_rows), 256, 0, s>>>(w, set_row0, g, g_sorted, total_rows, ell_add);
+    add_caller_term_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, g, g_sorted, total_rows, ell_add);
     return cudaGetLastError();
 }
 

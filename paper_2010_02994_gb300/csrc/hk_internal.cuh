@@ -32,7 +32,7 @@ constexpr int kMaxD = 8;
 constexpr float kPadTime = 1.0e18f;  // its square stays finite in FP32
 constexpr int kPass1Vals = 1;       // S
 constexpr int kPass1ThetaVals = 6;  // M, Xi, sum mu' q, sum mu' dt^2, sum xi'' dt, sum xi'' q
-constexpr int kFinalizeThreads = 256;
+constexpr int kFinalizeThreads = 128;  // rows per finalize segment (one CTA each)
 constexpr int kMaxThetaSets = 1;
 
 // Bits of the sticky device status word.
@@ -164,7 +164,8 @@ cudaError_t launch_kick_drift(const Work &w, const int64_t *set_row0, double *p,
                               int32_t *refl_bad, cudaStream_t s);
 cudaError_t launch_kick(const Work &w, const int64_t *set_row0, double *p, const double *g, const double *eps_dev,
                         int64_t total_rows, cudaStream_t s);
-cudaError_t launch_energy(const Work &w, const double *p, double *H_out, cudaStream_t s);
+constexpr int kEnergyParts = 32;  // CTAs per set in the HMC energy reduction
+cudaError_t launch_energy(const Work &w, const double *p, double *H_out, double *parts, cudaStream_t s);
 cudaError_t launch_accept(const double *H0, const double *H1, const double *log_u, const int32_t *refl_bad,
                           int32_t *accepted, int nsets, cudaStream_t s);
 cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,

@@ -264,3 +264,23 @@ def bmds_random(seed: int, n: int, d: int, noise: float = 0.2, sigma2: float = 0
     Y = np.tril(Y, -1) + np.tril(Y, -1).T
     X = Xt + 0.1 * rng.normal(size=Xt.shape)
     return BmdsWorkload(f"bmds_random_n{n}_d{d}", np.ascontiguousarray(Y), X, float(sigma2))
+
+
+def make_bmds_hawkes(seed: int = 5, n: int = 4733, d: int = 6) -> tuple:
+    """BMDS-Hawkes inputs shaped like the influenza application (Section 4.3:
+    4,733 cases over 2000-2012, D = 6): the latent locations and distance
+    matrix of make_bmds, and case times spread over 12 years (4,383 days),
+    each country's cases clustered around a few seasonal outbreaks.
+    Parameters: tau_x = 1 and h = 0.1 in latent units (country scale and
+    within-country jitter), tau_t = 30 d, theta = 0.5, omega = 1/7 d^-1,
+    mu0 = 0.5.  Returns (Workload, BmdsWorkload)."""
+    b = make_bmds(seed, n, d)
+    rng = np.random.default_rng(seed + 100)
+    n_c = int(b.country.max()) + 1
+    waves = rng.uniform(0.0, 4383.0, size=(n_c, 4))
+    pick = rng.integers(0, 4, size=n)
+    t = np.clip(waves[b.country, pick] + rng.exponential(20.0, size=n), 0.0, 4383.0)
+    params = {"mu0": 0.5, "tau_x": 1.0, "tau_t": 30.0, "theta": 0.5, "omega": 1.0 / 7.0, "h": 0.1}
+    w = Workload(name=f"influenza_like_n{n}_d{d}", t=t, X=b.X.copy(), X_obs=b.X.copy(),
+                 box_lo=None, box_hi=None, params=params)
+    return w, b
