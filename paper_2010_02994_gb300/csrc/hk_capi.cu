@@ -525,9 +525,11 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
         HK_TRY(launch_identity_order(t, ctx->keys_b, ctx->vals_b, pl.n_total, ctx->d_set_ev0, ns, w.status, s),
                "order check");
     } else {
-        HK_TRY(launch_sort(ctx->sort_temp, ctx->sort_bytes, ctx->keys_a, ctx->keys_b, ctx->vals_a, ctx->vals_b,
-                           pl.n_total, ns, ctx->d_set_ev0, s),
+        HK_TRY(launch_sort(ctx->sort_temp, ctx->sort_bytes, t, ctx->keys_a, ctx->keys_b, ctx->vals_a, ctx->vals_b,
+                           pl.n_total, ns, ctx->d_set_ev0, s, &ctx->launches_own),
                "time sort");
+        if (ns > 1)
+            ctx->launches_lib += 1;  // the second library sort of a batch
     }
     HK_TRY(launch_pack_rows(w, X, ctx->keys_b, ctx->vals_b, pl.total_rows, ctx->d_set_row0, s), "pack");
     if (ctx->opt_profile)

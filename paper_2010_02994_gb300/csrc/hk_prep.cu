@@ -198,30 +198,88 @@ cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *va
     return cudaGetLastError();
 }
 
-size_t sort_temp_bytes(int64_t n_total, int32_t nsets)
+// Batches are sorted by two stable radix sorts instead of a segmented one:
+// every event by its full FP64 time (value: its global index), then that
+// order by set index (a few key bits).  The result is exact -- grouped by
+// set, in time order within a set, ties in the caller's order -- and costs
+// a handful of full-width passes instead of one small sort per set.
+namespace {
+
+int set_bits(int32_t nsets)
 {
-    size_t bytes = 0;
-    if (nsets <= 1) {
-        cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const double *)nullptr, (double *)nullptr,
-                                        (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total);
-    } else {
-        cub::DeviceSegmentedRadixSort::SortPairs(nullptr, bytes, (const double *)nullptr, (double *)nullptr,
-                                                 (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total, nsets,
-                                                 (const int64_t *)nullptr, (const int64_t *)nullptr);
-    }
-    return bytes;
+    int b = 1;
+    while ((1 << b) < nsets)
+        ++b;
+    return b;
 }
 
-cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *keys_in, double *keys_out,
-                        const int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
-                        const int64_t *d_seg_offsets, cudaStream_t s)
+__global__ void iota_kernel(int32_t *v, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (int32_t)i;
+}
+
+__global__ void set_key_kernel(const int32_t *__restrict__ gidx, int32_t *__restrict__ key, int64_t n,
+                               const int64_t *__restrict__ set_ev0, int32_t nsets)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = find_set_by(set_ev0, nsets, gidx[i]);
+}
+
+// final order: times and set-relative indices, as the segmented sort gave
+__global__ void batch_order_kernel(const double *__restrict__ t, const int32_t *__restrict__ gidx,
+                                   double *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
+                                   const int64_t *__restrict__ set_ev0, int32_t nsets)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = gidx[i];
+        keys_out[i] = t[g];
+        vals_out[i] = (int32_t)(g - set_ev0[find_set_by(set_ev0, nsets, g)]);
+    }
+}
+
+}  // namespace
+
+size_t sort_temp_bytes(int64_t n_total, int32_t nsets)
+{
+    size_t bytes = 0, b2 = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const double *)nullptr, (double *)nullptr,
+                                    (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total);
+    if (nsets > 1)
+        cub::DeviceRadixSort::SortPairs(nullptr, b2, (const int32_t *)nullptr, (int32_t *)nullptr,
+                                        (const int32_t *)nullptr, (int32_t *)nullptr, (int)n_total, 0,
+                                        set_bits(nsets));
+    return bytes > b2 ? bytes : b2;
+}
+
+cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *t, double *keys_in, double *keys_out,
+                        int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
+                        const int64_t *d_set_ev0, cudaStream_t s, int64_t *launches)
 {
     // Radix sort is stable: events with equal times keep the caller's order.
-    if (nsets <= 1)
+    if (nsets <= 1) {
+        if (launches)
+            *launches += 0;
         return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out, (int)n_total,
                                                0, 64, s);
-    return cub::DeviceSegmentedRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out,
-                                                    (int)n_total, nsets, d_seg_offsets, d_seg_offsets + 1, 0, 64, s);
+    }
+    const int g = grid_for(n_total, 256);
+    iota_kernel<<<g, 256, 0, s>>>(vals_in, n_total);
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out,
+                                                    (int)n_total, 0, 64, s);
+    if (e != cudaSuccess)
+        return e;
+    // keys_in is free now: its 8-byte slots hold two int32 key arrays
+    int32_t *sk_in = reinterpret_cast<int32_t *>(keys_in), *sk_out = sk_in + n_total;
+    set_key_kernel<<<g, 256, 0, s>>>(vals_out, sk_in, n_total, d_set_ev0, nsets);
+    e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, sk_in, sk_out, vals_out, vals_in, (int)n_total, 0,
+                                        set_bits(nsets), s);
+    if (e != cudaSuccess)
+        return e;
+    batch_order_kernel<<<g, 256, 0, s>>>(t, vals_in, keys_out, vals_out, n_total, d_set_ev0, nsets);
+    if (launches)
+        *launches += 3;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
