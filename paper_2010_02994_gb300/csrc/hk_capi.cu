@@ -352,6 +352,7 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
     c.take<int32_t>(pl.total_segs);
     c.take<int32_t>((size_t)pl.total_segs * kFinalizeThreads);
     c.take<double>(pl.total_segs);
+    c.take<double>((size_t)kThetaParts * kPass1ThetaVals);
     c.take<double>(ns);
     c.take<double>(pl.n_total);
     c.take<double>(pl.n_total);
@@ -426,6 +427,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     w.seg_count = c.take<int32_t>(pl.total_segs);
     w.seg_rows = c.take<int32_t>((size_t)pl.total_segs * kFinalizeThreads);
     w.seg_sum = c.take<double>(pl.total_segs);
+    w.theta_parts = c.take<double>((size_t)kThetaParts * kPass1ThetaVals);
     w.set_loglik = c.take<double>(ns);
     ctx->keys_a = c.take<double>(pl.n_total);
     ctx->keys_b = c.take<double>(pl.n_total);
@@ -622,7 +624,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         }
         if (theta) {
             ++ctx->launches_own;
-            HK_TRY(launch_theta_grad(w, out_grad_params, s), "parameter gradient");
+            HK_TRY(launch_theta_grad(w, pl.n_total, out_grad_params, s), "parameter gradient");
         }
         return HAWKES_OK;
     }
@@ -645,7 +647,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         prof_end(ctx, s, pf);
     if (theta) {
         ++ctx->launches_own;
-        HK_TRY(launch_theta_grad(w, out_grad_params, s), "parameter gradient");
+        HK_TRY(launch_theta_grad(w, pl.n_total, out_grad_params, s), "parameter gradient");
     }
     if (!want_grad)
         return HAWKES_OK;

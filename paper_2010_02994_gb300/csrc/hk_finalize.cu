@@ -10,6 +10,7 @@
 // gradient from FP64 loops over all events; in the FP32 gradient pass their
 // weight w_n is zero.  Flagged rows are listed per finalize CTA (segment) in
 // row order, so every sum over them is also taken in a fixed order.
+#include <algorithm>
 #include <cmath>
 
 #include "hk_internal.cuh"
@@ -510,7 +511,11 @@ __global__ void __launch_bounds__(kT) fixup_grad_kernel(Work w, int total_segs, 
 // d ell / d Theta of set 0 (Theta order mu0, tau_x, tau_t, theta, omega, h):
 // per row, the rate-term sums divided by lambda_n plus the derivative of
 // -Lambda_n; summed over rows in a fixed order.
-__global__ void __launch_bounds__(kT) theta_grad_kernel(Work w, double *out6)
+// The six Theta-gradient sums over the rows (each row's terms need FP64
+// normcdf, exp and divisions), split over kThetaParts CTAs so that the FP64
+// work spreads over the SMs; each CTA writes its six compensated partials
+// and theta_finish_kernel adds them in CTA order.
+__global__ void __launch_bounds__(kT) theta_grad_kernel(Work w)
 {
     __shared__ double sh[kT];
     const SetDesc &S = w.sets[0];
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(kT) theta_grad_kernel(Work w, double *out6)
     const double T = w.t64[S.row0 + S.n - 1];
     const double inv_sqrt_2pi = 0.39894228040143267793994605993438;
     Nsum acc[6];
-    for (int i = threadIdx.x; i < S.n; i += kT) {
+    for (int i = blockIdx.x * kT + threadIdx.x; i < S.n; i += gridDim.x * kT) {
         const int64_t r = S.row0 + i;
         const double *A = w.theta_rows + r * kPass1ThetaVals;
         const double lam = w.lam64[r];
@@ -535,12 +540,23 @@ __global__ void __launch_bounds__(kT) theta_grad_kernel(Work w, double *out6)
         acc[4].add((A[1] / om - A[4]) / lam - th * a * ea);
         acc[5].add((A[5] / (h * h * h) - D * A[1] / h) / lam);
     }
-    const bool zero_rate = (w.set_flags[0] & 1) != 0;
     for (int q = 0; q < 6; ++q) {
         const double v = block_sum(acc[q].value(), sh);
         if (threadIdx.x == 0)
-            out6[q] = zero_rate ? nan("") : v;
+            w.theta_parts[blockIdx.x * kPass1ThetaVals + q] = v;
     }
+}
+
+__global__ void theta_finish_kernel(Work w, int parts, double *out6)
+{
+    const int q = threadIdx.x;
+    if (q >= 6)
+        return;
+    Nsum acc;
+    for (int b = 0; b < parts; ++b)
+        acc.add(w.theta_parts[b * kPass1ThetaVals + q]);
+    const bool zero_rate = (w.set_flags[0] & 1) != 0;
+    out6[q] = zero_rate ? nan("") : acc.value();
 }
 
 // xi_n / lambda_n per event in the caller's order (the self-excitation
@@ -593,9 +609,11 @@ cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_theta_grad(const Work &w, double *out6, cudaStream_t s)
+cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream_t s)
 {
-    theta_grad_kernel<<<1, kT, 0, s>>>(w, out6);
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(kThetaParts, (n + kT - 1) / kT));
+    theta_grad_kernel<<<parts, kT, 0, s>>>(w);
+    theta_finish_kernel<<<1, 32, 0, s>>>(w, parts, out6);
     return cudaGetLastError();
 }
 

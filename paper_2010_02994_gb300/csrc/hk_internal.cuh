@@ -34,6 +34,7 @@ constexpr int kPass1Vals = 1;       // S
 constexpr int kPass1ThetaVals = 6;  // M, Xi, sum mu' q, sum mu' dt^2, sum xi'' dt, sum xi'' q
 constexpr int kFinalizeThreads = 128;  // rows per finalize segment (one CTA each)
 constexpr int kMaxThetaSets = 1;
+constexpr int kThetaParts = 256;  // CTAs of the Theta-gradient reduction
 
 // Bits of the sticky device status word.
 enum : unsigned {
@@ -101,6 +102,7 @@ struct Work {
     int32_t *seg_rows;   // their set-relative rows (kFinalizeThreads slots per CTA)
     double *seg_sum;     // each finalize CTA's sum of lnl over its unflagged rows
     double *set_loglik;  // ell per set
+    double *theta_parts; // kThetaParts x 6 partial sums of the Theta gradient
     int32_t *set_flags;  // bit 0: some rate of the set is zero
     int32_t *set_cmmax;  // per set: max(0, max_n cm32[n]) as float bits (gradient-pass skip bound)
     int32_t skip_far;    // skip pair blocks whose kernel values all underflow
@@ -148,7 +150,7 @@ cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s);
 cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
                               cudaStream_t s);
-cudaError_t launch_theta_grad(const Work &w, double *out6, cudaStream_t s);
+cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream_t s);
 cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
                                  cudaStream_t s);
 cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,

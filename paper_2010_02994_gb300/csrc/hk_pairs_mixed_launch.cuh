@@ -3,6 +3,8 @@
 // pass: 1 rates, 2 gradient, 3 rates with Theta sums.
 #pragma once
 
+#include <algorithm>
+
 #include "hk_pairs_mixed.cuh"
 
 namespace hk {
@@ -43,7 +45,17 @@ int occupancy_kind(int warps)
 {
     constexpr int R = rows_per_lane(D);
     const size_t smem = pair_smem_bytes<KIND, D, R>(warps);
-    const size_t smem_max = pair_smem_bytes<KIND, D, R>(8);
+    // the largest any warp count needs, capped at the per-CTA maximum (some
+    // 8-warp shapes exceed it; the shape choice never selects those)
+    // (static shared memory counts against the same per-CTA maximum)
+    int dev = 0, cap = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, pair_kernel<KIND, D, R>);
+    const size_t smem_max = std::min<size_t>(pair_smem_bytes<KIND, D, R>(8), (size_t)cap - fa.sharedSizeBytes);
+    if (smem > smem_max)
+        return 0;
     cudaFuncSetAttribute(pair_kernel<KIND, D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<KIND, D, R>, warps * 32, smem);

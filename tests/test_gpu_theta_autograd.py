@@ -123,3 +123,23 @@ def test_self_excitation_probability(ctx, prec):
         tol = 1e-12 if prec == "fp64" else 1e-5
         assert np.max(np.abs(got - ref)) <= tol
         assert np.all((got >= 0) & (got <= 1))
+
+
+def test_parameter_gradient_large_n_mixed_vs_fp64(ctx):
+    """At N = 70,000 the Theta pass takes its 4-warp shape (the 8-warp one
+    needs more shared memory than a CTA may have): the mixed parameter
+    gradient agrees with the FP64 GPU path, which the tests above pin to the
+    oracle, within the mixed tolerance."""
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesContext, hawkes_loglik_grad_locations
+
+    w = synth.scaled_down(synth.make_c5(), 70_000)
+    big = HawkesContext(device=0, max_n=w.n, max_d=w.d)
+    t = torch.tensor(w.t, device="cuda")
+    X = torch.tensor(w.X, device="cuda")
+    _, _, gm = hawkes_loglik_grad_locations(big, t, X, w.params, precision="mixed", grad_params=True)
+    _, _, gf = hawkes_loglik_grad_locations(big, t, X, w.params, precision="fp64", grad_params=True)
+    big.close()
+    err = np.max(np.abs(gm.cpu().numpy() - gf.cpu().numpy()) * w.theta_vector()) / w.n
+    assert err <= 1e-6, err
