@@ -163,6 +163,7 @@ def hawkes_loglik_grad_locations(ctx: HawkesContext, t, X, params, precision="mi
         gp = torch.empty(6, dtype=torch.float64, device=t.device) if grad_params else None
     else:
         ell, g, gp = out
+        gp = gp if grad_params else None
     p = params_struct(params)
     ctx.check(ctx.lib.hawkes_loglik_grad_locations(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p),
                                                    _precision(precision), ctx.stream(), _ptr(ell), _ptr(g),
