@@ -71,18 +71,18 @@ __device__ double block_sum(double v, double *sh)
 // sum_{k < count} p[k * stride] of FP32 partials, added in the order
 // k = 0, 1, ... with Kahan compensation in FP32 (FP64 adds run at 1/64 of
 // the FP32 rate here), returned in FP64.  The error is about two FP32 units
-// of sum |p_k|; the loads of eight consecutive terms are issued together.
+// of sum |p_k|; the loads of sixteen consecutive terms are issued together.
 __device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ p, int count, int64_t stride)
 {
     float s = 0.0f, c = 0.0f;
     int k = 0;
-    for (; k + 8 <= count; k += 8) {
-        float v[8];
+    for (; k + 16 <= count; k += 16) {
+        float v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 16; ++u)
             v[u] = p[(int64_t)(k + u) * stride];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const float y = v[u] - c;
             const float t = s + y;
             c = (t - s) - y;
@@ -98,30 +98,31 @@ __device__ __forceinline__ double ordered_strided_sum(const float *__restrict__ 
     return (double)s - (double)c;
 }
 
-// The same ordered compensated sums for nv <= kMaxD values at once (value q
-// at p[q * vstride + k * stride]): every value is added in the order
-// k = 0, 1, ..., exactly as ordered_strided_sum does, but the loads of four
-// slots of all values are issued together, so a row's gradient costs a
-// quarter of the memory round trips of nv separate sums.
-__device__ __forceinline__ void ordered_strided_sums(const float *__restrict__ p, int nv, int64_t vstride, int count,
+// The same ordered compensated sums for NV values at once (value q at
+// p[q * vstride + k * stride]): every value is added in the order
+// k = 0, 1, ..., exactly as ordered_strided_sum does, but the loads of eight
+// slots of all NV values are issued together, so a row's NV sums cost the
+// memory round trips of one.
+template <int NV>
+__device__ __forceinline__ void ordered_strided_sums(const float *__restrict__ p, int64_t vstride, int count,
                                                      int64_t stride, double *out)
 {
-    float s[kMaxD], c[kMaxD];
+    float s[NV], c[NV];
 #pragma unroll
-    for (int q = 0; q < kMaxD; ++q)
+    for (int q = 0; q < NV; ++q)
         s[q] = c[q] = 0.0f;
-    for (int k = 0; k < count; k += 4) {
-        float v[4][kMaxD];
+    for (int k = 0; k < count; k += 8) {
+        float v[8][NV];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int q = 0; q < kMaxD; ++q)
-                v[u][q] = (q < nv && k + u < count) ? p[(int64_t)(k + u) * stride + (int64_t)q * vstride] : 0.0f;
+            for (int q = 0; q < NV; ++q)
+                v[u][q] = (k + u < count) ? p[(int64_t)(k + u) * stride + (int64_t)q * vstride] : 0.0f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int q = 0; q < kMaxD; ++q) {
-                if (q < nv && k + u < count) {
+            for (int q = 0; q < NV; ++q) {
+                if (k + u < count) {
                     const float y = v[u][q] - c[q];
                     const float t = s[q] + y;
                     c[q] = (t - s[q]) - y;
@@ -130,9 +131,24 @@ __device__ __forceinline__ void ordered_strided_sums(const float *__restrict__ p
             }
     }
 #pragma unroll
-    for (int q = 0; q < kMaxD; ++q)
-        if (q < nv)
-            out[q] = (double)s[q] - (double)c[q];
+    for (int q = 0; q < NV; ++q)
+        out[q] = (double)s[q] - (double)c[q];
+}
+
+// Runtime value count 1..kMaxD dispatched to the compile-time version.
+__device__ __forceinline__ void ordered_strided_sums_d(int nv, const float *__restrict__ p, int64_t vstride,
+                                                       int count, int64_t stride, double *out)
+{
+    switch (nv) {
+    case 1: ordered_strided_sums<1>(p, vstride, count, stride, out); break;
+    case 2: ordered_strided_sums<2>(p, vstride, count, stride, out); break;
+    case 3: ordered_strided_sums<3>(p, vstride, count, stride, out); break;
+    case 4: ordered_strided_sums<4>(p, vstride, count, stride, out); break;
+    case 5: ordered_strided_sums<5>(p, vstride, count, stride, out); break;
+    case 6: ordered_strided_sums<6>(p, vstride, count, stride, out); break;
+    case 7: ordered_strided_sums<7>(p, vstride, count, stride, out); break;
+    default: ordered_strided_sums<8>(p, vstride, count, stride, out); break;
+    }
 }
 
 struct PairFp64 {
@@ -189,8 +205,8 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             }
         } else if (theta) {
             double v[kMaxD];
-            ordered_strided_sums(w.P1 + S.part0 + i, kPass1ThetaVals, S.npad, S.nblk,
-                                 (int64_t)kPass1ThetaVals * S.npad, v);
+            ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                                                  (int64_t)kPass1ThetaVals * S.npad, v);
             const double sum = v[0] + v[1];
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
@@ -394,20 +410,25 @@ __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, dou
     const bool zero_rate = (w.set_flags[s] & 1) != 0;
     double gv[kMaxD];
     if (fp64) {
-        for (int q = 0; q < d; ++q) {
-            Nsum acc;
-            for (int sp = 0; sp < S.fsplit; ++sp)
-                acc.add(w.F2[S.fpart2_0 + ((int64_t)sp * d + q) * S.npad + i]);
-            gv[q] = acc.value();
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q) {
+            if (q < d) {
+                Nsum acc;
+                for (int sp = 0; sp < S.fsplit; ++sp)
+                    acc.add(w.F2[S.fpart2_0 + ((int64_t)sp * d + q) * S.npad + i]);
+                gv[q] = acc.value();
+            }
         }
     } else {
         if (zero_rate && i == 0)
             atomicOr(w.status, kStZeroRate);
         if (w.w32[r] == 0.0f)
             return;  // a flagged row: fixup_grad_kernel writes its gradient
-        ordered_strided_sums(w.P2 + S.part2_0 + i, d, S.npad, S.nblk, (int64_t)d * S.npad, gv);
-        for (int q = 0; q < d; ++q)
-            gv[q] *= S.Cg;
+        ordered_strided_sums_d(d, w.P2 + S.part2_0 + i, S.npad, S.nblk, (int64_t)d * S.npad, gv);
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q)
+            if (q < d)
+                gv[q] *= S.Cg;
         if (w.counters[2] > 0) {
             // contributions through the flagged rows' own rates:
             // w_n [mu_nm / tau_x^2 + xi_nm / h^2] (x_n - x_m), xi_nm when t_m < t_n
@@ -433,25 +454,35 @@ __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, dou
                     if (tm < tn)
                         coef += k.Cxi * exp(-(k.omega * dt + r2 * k.c)) * k.ih2;
                     coef *= w.w64[rn];
-                    for (int q = 0; q < d; ++q)
-                        gv[q] += coef * (w.x64[rn * kMaxD + q] - w.x64[r * kMaxD + q]);
+#pragma unroll
+                    for (int q = 0; q < kMaxD; ++q)
+                        if (q < d)
+                            gv[q] += coef * (w.x64[rn * kMaxD + q] - w.x64[r * kMaxD + q]);
                 }
             }
         }
     }
     if (zero_rate) {
-        for (int q = 0; q < d; ++q)
-            gv[q] = nan("");
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q)
+            if (q < d)
+                gv[q] = nan("");
         if (fp64 && i == 0)
             atomicOr(w.status, kStZeroRate);
     }
     const int src = w.perm[r];
-    if (out_grad)
-        for (int q = 0; q < d; ++q)
-            out_grad[S.x0 + (int64_t)src * d + q] = gv[q];
-    if (g_sorted)
-        for (int q = 0; q < d; ++q)
-            g_sorted[r * kMaxD + q] = gv[q];
+    if (out_grad) {
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q)
+            if (q < d)
+                out_grad[S.x0 + (int64_t)src * d + q] = gv[q];
+    }
+    if (g_sorted) {
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q)
+            if (q < d)
+                g_sorted[r * kMaxD + q] = gv[q];
+    }
 }
 
 // Own gradient of every flagged row, in FP64 over all events (the paper's
