@@ -428,6 +428,75 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     return out
 
 
+def run_workload_calls(name: str, calls: int) -> int:
+    """`calls` untimed calls of one of the other workloads (same inputs as their
+    bench lines), for profiler captures of their kernels."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2010_02994_gb300 import (HawkesContext, HawkesMwG, hawkes_batch_loglik_grad,
+                                        hawkes_bmds_hmc_trajectory, hawkes_bmds_loglik_grad,
+                                        hmc_leapfrog_trajectory)
+
+    dev = torch.device("cuda", 0)
+    if name in ("bmds", "bmds_f64y"):
+        b = synth.make_bmds()
+        ctx = HawkesContext(device=0, max_n=b.X.shape[0], max_d=b.X.shape[1])
+        Y = torch.tensor(b.Y, device=dev)
+        Y = Y if name == "bmds_f64y" else Y.float()
+        X = torch.tensor(b.X, device=dev)
+        for _ in range(calls):
+            hawkes_bmds_loglik_grad(ctx, Y, X, b.sigma2, "mixed", check=False)
+        ctx.sync_status()
+        ctx.close()
+    elif name in ("mwg1", "mwg32"):
+        nb = 1 if name == "mwg1" else 32
+        w = synth.make_c2()
+        s = HawkesMwG(torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev), w.params, max_block=nb)
+        lo, hi = torch.tensor(w.box_lo, device=dev), torch.tensor(w.box_hi, device=dev)
+        gen = torch.Generator(device=dev).manual_seed(12)
+        for _ in range(calls):
+            idx = torch.randperm(w.n, generator=gen, device=dev)[:nb]
+            u = torch.rand((nb, w.d), generator=gen, device=dev, dtype=torch.float64)
+            Xn, lq = s.propose_box(idx, lo, hi, 0.02, u, check=False)
+            s.step(idx, Xn, float(np.log(0.5)), lq, check=False)
+        s.sync_status()
+        s.close()
+    elif name == "bmds_hmc":
+        w, b = synth.make_bmds_hawkes()
+        ctx = HawkesContext(device=0, max_n=w.n, max_d=w.d)
+        t, X = torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev)
+        Y = torch.tensor(b.Y, device=dev).float()
+        p0 = torch.tensor(np.random.default_rng(3).standard_normal(size=w.X.shape), device=dev)
+        for _ in range(calls):
+            hawkes_bmds_hmc_trajectory(ctx, t, X, p0, w.params, Y, b.sigma2, 5e-4, 4, -1e30, "mixed", check=False)
+        ctx.sync_status()
+        ctx.close()
+    elif name == "hmc_c2":
+        w = synth.make_c2()
+        ctx = HawkesContext(device=0, max_n=w.n, max_d=w.d)
+        t, X = torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev)
+        lo, hi = torch.tensor(w.box_lo, device=dev), torch.tensor(w.box_hi, device=dev)
+        p0 = torch.tensor(np.random.default_rng(11).standard_normal(size=w.X.shape), device=dev)
+        for _ in range(calls):
+            hmc_leapfrog_trajectory(ctx, t, X, p0, w.params, 2e-3, 4, 0.0, lo, hi, check=False)
+        ctx.sync_status()
+        ctx.close()
+    else:
+        sets = synth.make_c4()
+        sizes, dims = [w.n for w in sets], [w.d for w in sets]
+        ctx = HawkesContext(device=0, max_n=sum(sizes), max_d=8)
+        t = torch.tensor(np.concatenate([w.t for w in sets]), device=dev)
+        X = torch.tensor(np.concatenate([w.X.reshape(-1) for w in sets]), device=dev)
+        for _ in range(calls):
+            hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, [w.params for w in sets], check=False)
+        ctx.sync_status()
+        ctx.close()
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,11 +511,17 @@ def main():
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--kernels-only", action="store_true",
                     help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
+    ap.add_argument("--workload", default=None,
+                    choices=["bmds", "bmds_f64y", "mwg1", "mwg32", "bmds_hmc", "hmc_c2", "batched_c4"],
+                    help="with --kernels-only: run warmup + steps calls of that other workload instead "
+                         "(for profiler captures); prints no JSON")
     args = ap.parse_args()
     args.steps_ref = max(1, min(args.steps, 10))
     args.warmup_ref = min(args.warmup, 1)
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernels_only and args.workload:
+        return run_workload_calls(args.workload, args.warmup + args.steps)
 
     import numpy as np
     import torch
