@@ -11,14 +11,15 @@
 //   Delta ell = sum_m [log lambda*_m - log lambda_m],
 // an O(|B| N) computation instead of the O(N^2) of a full evaluation.
 //
-// Three launches per proposal: a column kernel (every m: block membership,
-// the |B| column updates, log1p(Delta_m / lambda_m) summed per CTA), a row
-// kernel (one CTA per moved event: its new rate over all events), and a
-// one-CTA finish kernel (Delta ell in a fixed order; in step mode the accept
-// decision log u < Delta ell + log q-ratio and, on accept, the commit).  The
-// rates live in two buffers; the device-side index of the current one flips
-// on accept, so no call reads anything back to the host and a sequence of
-// steps can be captured in a CUDA graph.  Everything is FP64.
+// One launch per proposal: its first CTAs take the unmoved events (block
+// membership, the |B| column updates, log1p(Delta_m / lambda_m) summed per
+// CTA), the others the moved events (each moved event's new rate over all
+// events, split over several CTAs), and the CTA that finishes last adds
+// everything in a fixed order and, in step mode, takes the accept decision
+// log u < Delta ell + log q-ratio and, on accept, the commit.  The rates live
+// in two buffers; the device-side index of the current one flips on accept,
+// so no call reads anything back to the host and a sequence of steps can be
+// captured in a CUDA graph.  Everything is FP64.
 #include <cuda_runtime.h>
 
 #include <math_constants.h>
@@ -67,19 +68,49 @@ __device__ __forceinline__ double contrib(const double *xm, double tm, const dou
     return v;
 }
 
-template <int NT = kThreads>
-__device__ double block_sum(double v, double *sh)
+// Sum over a CTA of NT threads (a multiple of 32), valid in thread 0: a
+// shuffle tree per warp, then one over the warp sums; the order is fixed, so
+// the result is reproducible.  sh holds NT / 32 doubles.
+template <int NT>
+__device__ double cta_sum(double v, double *sh)
 {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = NT / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            sh[threadIdx.x] += sh[threadIdx.x + o];
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    if constexpr (NT > 32) {
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0)
+            sh[w] = v;
+        __syncthreads();
+        v = 0.0;
+        if (w == 0) {
+            v = l < NT / 32 ? sh[l] : 0.0;
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_down_sync(0xffffffffu, v, o);
+        }
         __syncthreads();
     }
-    const double r = sh[0];
+    return v;
+}
+
+// Whether this CTA is the last of `count` CTAs to get here: every CTA
+// publishes its writes, then takes a ticket; the last one resets the counter
+// for the next launch and may then read what all the others wrote.
+__device__ bool last_cta_of(unsigned *ticket, unsigned count, int *flag)
+{
+    __threadfence();
     __syncthreads();
-    return r;
+    if (threadIdx.x == 0) {
+        const unsigned k = atomicAdd(ticket, 1u);
+        *flag = k == count - 1;
+        if (*flag)
+            *ticket = 0u;
+    }
+    __syncthreads();
+    const bool last = *flag;
+    __syncthreads();  // flag is reused by the next call
+    if (last)
+        __threadfence();
+    return last;
 }
 
 // log(lam_new / lam) with the extended-real convention for zero rates.
@@ -143,40 +174,63 @@ __global__ void __launch_bounds__(kRateTile) rates_kernel(const double *__restri
         part[(int64_t)sp * n + row] = s;
 }
 
-// lambda_m from the splits (fixed order) into the current buffer, and
-// ell = sum log lambda - sum Lambda in one CTA.
-__global__ void __launch_bounds__(kThreads) rates_finish_kernel(const double *__restrict__ t, int64_t n, Consts k,
-                                                                int fsplit, const double *__restrict__ part,
-                                                                double *lam0, double *lam1, const int *active,
-                                                                double *loglik)
+// T = max t_n (the end of the observation window), once per state.
+__global__ void __launch_bounds__(kThreads) tmax_kernel(const double *__restrict__ t, int64_t n, double *T)
 {
     __shared__ double sh[kThreads];
-    double *lam = *active ? lam1 : lam0;
-    double tmax = -INFINITY;
+    double m = -INFINITY;
     for (int64_t i = threadIdx.x; i < n; i += kThreads)
-        tmax = fmax(tmax, t[i]);
-    sh[threadIdx.x] = tmax;
+        m = fmax(m, t[i]);
+    sh[threadIdx.x] = m;
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
             sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
         __syncthreads();
     }
-    const double T = sh[0];
-    __syncthreads();
+    if (threadIdx.x == 0)
+        *T = sh[0];
+}
+
+// lambda_m from the splits (fixed order) into the current buffer and
+// log lambda_m - Lambda_m summed per CTA; the last CTA adds the CTA sums in
+// order into ell.  Small CTAs spread the FP64 logs and normal CDFs over every
+// SM.
+constexpr int kFinThreads = 64;
+
+__global__ void __launch_bounds__(kFinThreads) rates_finish_kernel(const double *__restrict__ t, int64_t n,
+                                                                   Consts k, int fsplit,
+                                                                   const double *__restrict__ part,
+                                                                   const double *__restrict__ Tmax, double *lam0,
+                                                                   double *lam1, int *ctl, double *cpart,
+                                                                   double *loglik)
+{
+    __shared__ double sh[kFinThreads / 32];
+    __shared__ int flag;
+    double *lam = ctl[0] ? lam1 : lam0;
+    const double T = *Tmax;
     double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+    const int64_t i = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;
+    if (i < n) {
         double l = 0.0;
         for (int sp = 0; sp < fsplit; ++sp)
             l += part[(int64_t)sp * n + i];
         lam[i] = l;
         const double a = T - t[i];
         const double Lam = k.mu0 * (normcdf(a / k.tau_t) - normcdf(-t[i] / k.tau_t)) - k.theta * expm1(-k.omega * a);
-        acc += log(l) - Lam;
+        acc = log(l) - Lam;
     }
-    const double ell = block_sum(acc, sh);
+    acc = cta_sum<kFinThreads>(acc, sh);
     if (threadIdx.x == 0)
-        *loglik = ell;
+        cpart[blockIdx.x] = acc;
+    if (!last_cta_of(reinterpret_cast<unsigned *>(ctl + 2), gridDim.x, &flag))
+        return;
+    double v = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += kFinThreads)
+        v += __ldcg(cpart + c);
+    v = cta_sum<kFinThreads>(v, sh);
+    if (threadIdx.x == 0)
+        *loglik = v;
 }
 
 // ------------------------------------------------------------- proposal --
@@ -187,135 +241,165 @@ struct Block {
     const double *xnew;   // caller's device proposals, nb x d
 };
 
-// Every m: its position in the block (or -1), and for m outside the block
-// the change of its rate and log1p(Delta_m / lambda_m), summed per CTA.
-// Small CTAs, so that the FP64 work spreads over every SM.
-constexpr int kColThreads = 64;
+// The launch of one proposal.  CTAs [0, ncol) take 64 / lanes consecutive
+// events each, `lanes` threads per event splitting its loop over the block
+// (the column part); CTA ncol + b * splits + sp takes moved event b against
+// events [sp * per, (sp + 1) * per) (the row part).
+constexpr int kEvalThreads = 64;
+constexpr int kRangeMax = 8192;  // events per row CTA at most (membership bitmap in shared memory)
 
-__global__ void __launch_bounds__(kColThreads) columns_kernel(const double *__restrict__ t,
-                                                              const double *__restrict__ X, int64_t n, int d,
-                                                              Consts k, Block B, double *lam0, double *lam1,
-                                                              const int *active, int *pos, double *part, int *status)
+struct Launch {
+    int ncol, splits, lanes;
+    int64_t per;
+};
+
+// For m in [lo, lo + cnt): set the bit of every moved event in the range; a
+// bit found already set means a repeated index when `dup` is given.
+__device__ void mark_block(const Block &B, int64_t n, int64_t lo, int64_t cnt, unsigned *bits, int *dup)
 {
-    __shared__ double sh[kColThreads];
-    __shared__ double sxo[kMaxBlock * kMaxDim], sxn[kMaxBlock * kMaxDim], stb[kMaxBlock];
-    __shared__ int64_t sid[kMaxBlock];
-    const double *lam = *active ? lam1 : lam0;
-    double *lam_new = *active ? lam0 : lam1;
-    for (int b = threadIdx.x; b < B.nb; b += kColThreads) {
+    for (int w = threadIdx.x; w < (int)((cnt + 31) / 32); w += kEvalThreads)
+        bits[w] = 0u;
+    __syncthreads();
+    for (int b = threadIdx.x; b < B.nb; b += kEvalThreads) {
         const int64_t m = B.idx[b];
-        const bool ok = m >= 0 && m < n;
-        sid[b] = ok ? m : -1;
-        stb[b] = ok ? t[m] : 0.0;
-        bool bad = false;
-        for (int q = 0; q < d; ++q) {
-            sxo[b * kMaxDim + q] = ok ? X[m * d + q] : 0.0;
-            const double v = B.xnew[(int64_t)b * d + q];
-            bad |= !isfinite(v);
-            sxn[b * kMaxDim + q] = v;
-        }
-        if (blockIdx.x == 0) {
-            if (!ok)
-                atomicOr(status, kBadBlock);
-            if (bad)
-                atomicOr(status, kBadProposal);
+        if (m >= lo && m < lo + cnt && m < n) {
+            const unsigned bit = 1u << ((m - lo) & 31);
+            const unsigned old = atomicOr(bits + ((m - lo) >> 5), bit);
+            if (dup && (old & bit))
+                atomicOr(dup, kBadBlock);
         }
     }
     __syncthreads();
-    double term = 0.0;
-    const int64_t m = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
-    if (m < n) {
-        int p = -1;
-        for (int b = 0; b < B.nb; ++b)
-            if (sid[b] == m) {
-                if (p >= 0)
-                    atomicOr(status, kBadBlock);  // repeated index
-                p = b;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kEvalThreads) eval_kernel(const double *__restrict__ t, double *X, int64_t n,
+                                                            Consts k, Block B, Launch L, double *lam0,
+                                                            double *lam1, int *ctl, double *cpart, double *rowpart,
+                                                            unsigned *bticket, double *bterm, double *out_delta,
+                                                            bool step,
+                                                            const double *log_q_ratio, const double *log_u,
+                                                            int *accepted_out, double *loglik)
+{
+    constexpr int d = D;
+    extern __shared__ double blk[];  // column part: old places, new places, times of the block
+    double *sxo = blk, *sxn = blk + B.nb * d, *stb = blk + 2 * B.nb * d;
+    __shared__ unsigned bits[kRangeMax / 32];
+    __shared__ double sh[kEvalThreads / 32];
+    __shared__ int flag, acc;
+    int *status = ctl + 1;
+    const int act = ctl[0];
+    const double *lam = act ? lam1 : lam0;
+    double *lam_new = act ? lam0 : lam1;
+    if ((int)blockIdx.x < L.ncol) {
+        // column part: every unmoved m of this CTA's range gets the change of
+        // its rate, sum over b of k(m <- x*_b) - k(m <- x_b)
+        const int ev = kEvalThreads / L.lanes;
+        const int64_t lo = (int64_t)blockIdx.x * ev;
+        for (int b = threadIdx.x; b < B.nb; b += kEvalThreads) {
+            const int64_t m = B.idx[b];
+            const bool ok = m >= 0 && m < n;
+            stb[b] = ok ? t[m] : 0.0;
+            bool bad = false;
+            for (int q = 0; q < d; ++q) {
+                sxo[b * d + q] = ok ? X[m * d + q] : 0.0;
+                const double v = B.xnew[(int64_t)b * d + q];
+                bad |= !isfinite(v);
+                sxn[b * d + q] = v;
             }
-        pos[m] = p;
-        if (p < 0) {
-            double xm[kMaxDim];
+            if (blockIdx.x == 0) {
+                if (!ok)
+                    atomicOr(status, kBadBlock);
+                if (bad)
+                    atomicOr(status, kBadProposal);
+            }
+        }
+        mark_block(B, n, lo, ev, bits, status);
+        const int e = threadIdx.x / L.lanes, j = threadIdx.x % L.lanes;
+        const int64_t m = lo + e;
+        const bool mine = m < n && !((bits[e >> 5] >> (e & 31)) & 1u);
+        double delta = 0.0;
+        if (mine) {
+            double xm[D];
             for (int q = 0; q < d; ++q)
                 xm[q] = X[m * d + q];
             const double tm = t[m];
-            double delta = 0.0;
-            for (int b = 0; b < B.nb; ++b)
-                delta += contrib(xm, tm, sxn + b * kMaxDim, stb[b], d, k) -
-                         contrib(xm, tm, sxo + b * kMaxDim, stb[b], d, k);
+            for (int b = j; b < B.nb; b += L.lanes)
+                delta += contrib(xm, tm, sxn + b * d, stb[b], d, k) - contrib(xm, tm, sxo + b * d, stb[b], d, k);
+        }
+        for (int o = L.lanes / 2; o > 0; o >>= 1)  // the event's lanes, in a fixed order
+            delta += __shfl_down_sync(0xffffffffu, delta, o, L.lanes);
+        double term = 0.0;
+        if (mine && j == 0) {
             const double l = lam[m];
             const double ln = l + delta;
             lam_new[m] = ln;
             term = log_ratio(l, ln, delta);
         }
-    }
-    term = block_sum<kColThreads>(term, sh);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = term;
-}
-
-// Moved event b's new rate over all events (moved ones at their proposed
-// places), split over `splits` CTAs per event (grid b x split), each adding
-// one contiguous range of events; the finish kernel adds the splits in order.
-constexpr int kRowThreads = 64;
-
-__global__ void __launch_bounds__(kRowThreads) rows_kernel(const double *__restrict__ t,
-                                                           const double *__restrict__ X, int64_t n, int d, Consts k,
-                                                           Block B, const int *pos, int splits, double *rowpart)
-{
-    __shared__ double sh[kRowThreads];
-    const int b = blockIdx.x, sp = blockIdx.y;
-    const int64_t mb = B.idx[b];
-    const int64_t per = (n + splits - 1) / splits;
-    const int64_t lo = min((int64_t)sp * per, n), hi = min(lo + per, n);
-    double s = 0.0;
-    if (mb >= 0 && mb < n) {  // a bad index is reported by the column kernel
-        double xb[kMaxDim];
-        for (int q = 0; q < d; ++q)
-            xb[q] = B.xnew[(int64_t)b * d + q];
-        const double tb = t[mb];
-        for (int64_t m = lo + threadIdx.x; m < hi; m += kRowThreads) {
-            if (m == mb)
-                continue;
-            const int p = pos[m];
-            const double *xm = p >= 0 ? B.xnew + (int64_t)p * d : X + m * d;
-            s += contrib(xb, tb, xm, t[m], d, k);
+        term = cta_sum<kEvalThreads>(term, sh);
+        if (threadIdx.x == 0)
+            cpart[blockIdx.x] = term;
+    } else {
+        // row part: moved event b's new rate over one range of events, the
+        // moved ones at their proposed places
+        const int r = (int)blockIdx.x - L.ncol;
+        const int b = r / L.splits, sp = r % L.splits;
+        const int64_t lo = min((int64_t)sp * L.per, n), cnt = min(L.per, n - lo);
+        mark_block(B, n, lo, cnt, bits, nullptr);
+        const int64_t mb = B.idx[b];
+        double s = 0.0;
+        if (mb >= 0 && mb < n) {  // a bad index is reported by the column part
+            double xb[D];
+            for (int q = 0; q < d; ++q)
+                xb[q] = B.xnew[(int64_t)b * d + q];
+            const double tb = t[mb];
+            for (int64_t j = threadIdx.x; j < cnt; j += kEvalThreads) {
+                const int64_t m = lo + j;
+                if (m == mb)
+                    continue;
+                const double *xm = X + m * d;
+                if ((bits[j >> 5] >> (j & 31)) & 1u)
+                    for (int p = 0; p < B.nb; ++p)
+                        if (B.idx[p] == m) {
+                            xm = B.xnew + (int64_t)p * d;
+                            break;
+                        }
+                s += contrib(xb, tb, xm, t[m], d, k);
+            }
+        }
+        s = cta_sum<kEvalThreads>(s, sh);
+        if (threadIdx.x == 0)
+            rowpart[r] = s;
+        // the last of event b's CTAs adds its splits in order (lane-strided,
+        // then a shuffle tree) and takes the log ratio of its rate
+        if (last_cta_of(bticket + b, L.splits, &flag) && threadIdx.x < 32) {
+            double lnew = 0.0;
+            for (int q = threadIdx.x; q < L.splits; q += 32)
+                lnew += __ldcg(rowpart + (int64_t)b * L.splits + q);
+            for (int o = 16; o > 0; o >>= 1)
+                lnew += __shfl_down_sync(0xffffffffu, lnew, o);
+            if (threadIdx.x == 0) {
+                double v = 0.0;
+                if (mb >= 0 && mb < n) {
+                    const double l = lam[mb];
+                    lam_new[mb] = lnew;
+                    v = (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
+                }
+                bterm[b] = v;
+            }
         }
     }
-    s = block_sum<kRowThreads>(s, sh);
-    if (threadIdx.x == 0)
-        rowpart[(int64_t)b * splits + sp] = s;
-}
+    if (!last_cta_of(reinterpret_cast<unsigned *>(ctl + 2), gridDim.x, &flag))
+        return;
 
-// Delta ell in a fixed order: the moved events' new rates (their splits
-// added in order) and log ratios, then the column partials; in step mode
-// the accept decision and, on accept, the commit (moved locations, running
-// ell, current-buffer flip).
-__global__ void __launch_bounds__(kThreads) finish_kernel(int ncta, const double *__restrict__ part, Block B,
-                                                          int64_t n, int splits, const double *__restrict__ rowpart,
-                                                          double *lam0, double *lam1, const int *status,
-                                                          double *out_delta, bool step, const double *log_q_ratio,
-                                                          const double *log_u, int *accepted_out, double *X, int d,
-                                                          int *active, double *loglik)
-{
-    __shared__ double sh[kThreads];
-    __shared__ int acc;
-    const double *lam = *active ? lam1 : lam0;
-    double *lam_new = *active ? lam0 : lam1;
+    // Delta ell in a fixed order: the moved events' log ratios, then the
+    // column partials; in step mode the decision and, on accept, the commit.
     double v = 0.0;
-    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
-        const int64_t mb = B.idx[b];
-        if (mb < 0 || mb >= n)
-            continue;
-        double lnew = 0.0;
-        for (int sp = 0; sp < splits; ++sp)
-            lnew += rowpart[(int64_t)b * splits + sp];
-        const double l = lam[mb];
-        lam_new[mb] = lnew;
-        v += (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
-    }
-    for (int i = threadIdx.x; i < ncta; i += kThreads)
-        v += part[i];
-    const double delta = block_sum(v, sh);
+    for (int b = threadIdx.x; b < B.nb; b += kEvalThreads)
+        v += __ldcg(bterm + b);
+    for (int c = threadIdx.x; c < L.ncol; c += kEvalThreads)
+        v += __ldcg(cpart + c);
+    const double delta = cta_sum<kEvalThreads>(v, sh);
     if (threadIdx.x == 0) {
         const bool bad = *(volatile const int *)status != 0;
         const double dl = bad ? nan("") : delta;
@@ -331,12 +415,12 @@ __global__ void __launch_bounds__(kThreads) finish_kernel(int ncta, const double
             *accepted_out = a;
         if (a) {
             *loglik += dl;
-            *active ^= 1;
+            ctl[0] = act ^ 1;
         }
     }
     __syncthreads();
     if (acc)
-        for (int e = threadIdx.x; e < B.nb * d; e += kThreads) {
+        for (int e = threadIdx.x; e < B.nb * d; e += kEvalThreads) {
             const int b = e / d, q = e % d;
             X[B.idx[b] * d + q] = B.xnew[e];
         }
@@ -394,15 +478,16 @@ __device__ double log_success(double A, double rho, int tries)
 
 // Lens proposals of Eq. (6) for a D = 2 block, one thread per moved event;
 // the block's log q-ratio is summed in a fixed order.
-__global__ void __launch_bounds__(kThreads) propose_circle_kernel(const double *__restrict__ X, int64_t n, Block B,
-                                                                  const double *__restrict__ centers,
-                                                                  const double *__restrict__ radii, double eps,
-                                                                  int tries, const double *__restrict__ u,
-                                                                  double *X_new, double *log_q_ratio, int *status)
+template <int NT>
+__global__ void __launch_bounds__(NT) propose_circle_kernel(const double *__restrict__ X, int64_t n, Block B,
+                                                            const double *__restrict__ centers,
+                                                            const double *__restrict__ radii, double eps, int tries,
+                                                            const double *__restrict__ u, double *X_new,
+                                                            double *log_q_ratio, int *status)
 {
-    __shared__ double sh[kThreads];
+    __shared__ double sh[NT / 32];
     double lq = 0.0;
-    for (int b = threadIdx.x; b < B.nb; b += kThreads) {
+    for (int b = threadIdx.x; b < B.nb; b += NT) {
         const int64_t m = B.idx[b];
         if (m < 0 || m >= n) {
             atomicOr(status, kBadBlock);
@@ -433,7 +518,7 @@ __global__ void __launch_bounds__(kThreads) propose_circle_kernel(const double *
         X_new[(int64_t)b * 2] = y0;
         X_new[(int64_t)b * 2 + 1] = y1;
     }
-    lq = block_sum(lq, sh);
+    lq = cta_sum<NT>(lq, sh);
     if (threadIdx.x == 0)
         *log_q_ratio = lq;
 }
@@ -441,15 +526,15 @@ __global__ void __launch_bounds__(kThreads) propose_circle_kernel(const double *
 // Truncated-normal proposals inside the boxes of Eq. (2), one thread per
 // coordinate: x* = x + s Phi^{-1}(Phi(a) + u (Phi(b) - Phi(a))), and the
 // log q-ratio sum log Z(x) - log Z(x*), Z(y) = Phi((hi - y)/s) - Phi((lo - y)/s).
-__global__ void __launch_bounds__(kThreads) propose_box_kernel(const double *__restrict__ X, int64_t n, int d,
-                                                               Block B, const double *__restrict__ lo,
-                                                               const double *__restrict__ hi, double sd,
-                                                               const double *__restrict__ u, double *X_new,
-                                                               double *log_q_ratio, int *status)
+template <int NT>
+__global__ void __launch_bounds__(NT) propose_box_kernel(const double *__restrict__ X, int64_t n, int d, Block B,
+                                                         const double *__restrict__ lo, const double *__restrict__ hi,
+                                                         double sd, const double *__restrict__ u, double *X_new,
+                                                         double *log_q_ratio, int *status)
 {
-    __shared__ double sh[kThreads];
+    __shared__ double sh[NT / 32];
     double lq = 0.0;
-    for (int e = threadIdx.x; e < B.nb * d; e += kThreads) {
+    for (int e = threadIdx.x; e < B.nb * d; e += NT) {
         const int b = e / d, q = e % d;
         const int64_t m = B.idx[b];
         if (m < 0 || m >= n) {
@@ -466,7 +551,7 @@ __global__ void __launch_bounds__(kThreads) propose_box_kernel(const double *__r
         X_new[e] = y;
         lq += log(Pb - Pa) - log(normcdf((h - y) / sd) - normcdf((l - y) / sd));
     }
-    lq = block_sum(lq, sh);
+    lq = cta_sum<NT>(lq, sh);
     if (threadIdx.x == 0)
         *log_q_ratio = lq;
 }
@@ -512,11 +597,14 @@ struct hawkes_mwg {
     std::string err;
     // device buffers
     double *t = nullptr, *X = nullptr, *lam0 = nullptr, *lam1 = nullptr;
-    double *part = nullptr;     // max(kRateSplit * n, column-kernel CTAs)
-    double *rowterm = nullptr;  // row-kernel partials: max_block x (2 SMs + 1)
+    double *part = nullptr;     // rate splits: kRateSplit x n
+    double *cpart = nullptr;    // per-CTA sums: ceil(n / 8)
+    double *rowterm = nullptr;  // row partials: max_block x most splits
     double *loglik = nullptr;   // running ell
-    int *ctl = nullptr;         // [0] current rate buffer, [1] status
-    int *pos = nullptr;         // n
+    double *Tmax = nullptr;     // max t
+    double *bterm = nullptr;    // per moved event: log of its rate ratio (max_block)
+    unsigned *bticket = nullptr;  // per moved event: last-CTA ticket of its row CTAs (max_block)
+    int *ctl = nullptr;         // [0] current rate buffer, [1] status, [2] last-CTA ticket
 };
 
 namespace {
@@ -550,20 +638,41 @@ hawkes_status enqueue_rates(hawkes_mwg *s, cudaStream_t st)
     rates_kernel<<<dim3((unsigned)tiles, fsplit), kRateTile, 0, st>>>(s->t, s->X, s->n, s->d, s->k, fsplit, s->part,
                                                                       s->ctl + 1);
     MWG_TRY(cudaGetLastError(), "rate kernel");
-    rates_finish_kernel<<<1, kThreads, 0, st>>>(s->t, s->n, s->k, fsplit, s->part, s->lam0, s->lam1, s->ctl,
-                                                s->loglik);
+    const int64_t ncta = (s->n + kFinThreads - 1) / kFinThreads;
+    rates_finish_kernel<<<(unsigned)ncta, kFinThreads, 0, st>>>(s->t, s->n, s->k, fsplit, s->part, s->Tmax, s->lam0,
+                                                                  s->lam1, s->ctl, s->cpart, s->loglik);
     MWG_TRY(cudaGetLastError(), "rate finish kernel");
     return HAWKES_OK;
 }
 
-// CTAs per moved event in the row kernel: about two per SM in total, each
-// with at least one event per thread.  (FP64 runs at 1/64 of the FP32 rate
-// on this GPU, so one event's O(N) row must spread over many SMs.)
-int row_splits(const hawkes_mwg *s, int nb)
+// CTAs per moved event in the row part: about two per SM in total, each with
+// at least one event per thread and at most kRangeMax events.  (FP64 runs at
+// 1/64 of the FP32 rate on this GPU, so one event's O(N) row must spread
+// over many SMs.)
+int64_t most_splits(int64_t n, int sms)
 {
+    return std::max<int64_t>(2 * (int64_t)sms + 1, (n + kRangeMax - 1) / kRangeMax);
+}
+
+// Threads per event in the column part: a power of two up to 8 and up to
+// |B|, chosen so that a column CTA (64 / lanes events, 2|B| pair terms each)
+// does about the work of a row CTA (`per` pair terms); the CTAs then finish
+// together instead of the few SMs holding two column CTAs setting the time.
+Launch plan_launch(const hawkes_mwg *s, int nb)
+{
+    Launch L;
     const int64_t want = (2 * (int64_t)s->sms + std::max(nb, 1) - 1) / std::max(nb, 1);
-    const int64_t most = std::max<int64_t>(1, s->n / kRowThreads);
-    return (int)std::max<int64_t>(1, std::min(want, most));
+    const int64_t most = std::max<int64_t>(1, s->n / kEvalThreads);
+    const int64_t need = (s->n + kRangeMax - 1) / kRangeMax;
+    const int64_t splits = std::max(std::min(want, most), need);
+    L.per = (s->n + splits - 1) / splits;
+    L.splits = (int)((s->n + L.per - 1) / L.per);  // no empty range
+    L.lanes = 1;
+    while (L.lanes < 8 && 2 * L.lanes <= nb && 2 * kEvalThreads * (int64_t)nb >= 2 * L.lanes * L.per)
+        L.lanes *= 2;
+    const int ev = kEvalThreads / L.lanes;
+    L.ncol = (int)((s->n + ev - 1) / ev);
+    return L;
 }
 
 hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, const double *X_new, bool step,
@@ -578,20 +687,30 @@ hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, co
         return fail(s, HAWKES_ERR_INVALID_ARG, "log_u must be a device pointer");
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
     const Block B{nb, idx, X_new};
-    const int ncta = (int)((s->n + kColThreads - 1) / kColThreads);
-    columns_kernel<<<ncta, kColThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->lam0, s->lam1, s->ctl, s->pos,
-                                                 s->part, s->ctl + 1);
-    MWG_TRY(cudaGetLastError(), "column kernel");
-    const int splits = row_splits(s, nb);
-    if (nb > 0) {
-        rows_kernel<<<dim3(nb, splits), kRowThreads, 0, st>>>(s->t, s->X, s->n, s->d, s->k, B, s->pos, splits,
-                                                           s->rowterm);
-        MWG_TRY(cudaGetLastError(), "row kernel");
+    const Launch L = plan_launch(s, nb);
+    const int64_t grid = (int64_t)L.ncol + (int64_t)nb * L.splits;
+    const size_t smem = sizeof(double) * (size_t)nb * (2 * s->d + 1);
+    switch (s->d) {
+#define HK_MWG_EVAL(DD)                                                                                         \
+    case DD:                                                                                                    \
+        eval_kernel<DD><<<(unsigned)grid, kEvalThreads, smem, st>>>(s->t, s->X, s->n, s->k, B, L, s->lam0,      \
+                                                                    s->lam1, s->ctl, s->cpart, s->rowterm,      \
+                                                                    s->bticket, s->bterm, out_delta, step,      \
+                                                                    log_q_ratio, log_u, out_accepted, s->loglik); \
+        break;
+        HK_MWG_EVAL(1)
+        HK_MWG_EVAL(2)
+        HK_MWG_EVAL(3)
+        HK_MWG_EVAL(4)
+        HK_MWG_EVAL(5)
+        HK_MWG_EVAL(6)
+        HK_MWG_EVAL(7)
+        HK_MWG_EVAL(8)
+#undef HK_MWG_EVAL
+    default:
+        return fail(s, HAWKES_ERR_INVALID_ARG, "dimension out of range");
     }
-    finish_kernel<<<1, kThreads, 0, st>>>(ncta, s->part, B, s->n, splits, s->rowterm, s->lam0, s->lam1, s->ctl + 1,
-                                          out_delta, step, log_q_ratio, log_u, out_accepted, s->X, s->d, s->ctl,
-                                          s->loglik);
-    MWG_TRY(cudaGetLastError(), "finish kernel");
+    MWG_TRY(cudaGetLastError(), "proposal kernel");
     return HAWKES_OK;
 }
 
@@ -625,24 +744,31 @@ hawkes_status hawkes_mwg_create(int32_t device, const double *t, const double *X
         cudaGetLastError();
         return bail(HAWKES_ERR_CUDA);
     }
-    const size_t part_n = std::max<size_t>((size_t)kRateSplit * n, (size_t)((n + kColThreads - 1) / kColThreads));
+    const size_t ncta = (size_t)((n + 7) / 8);  // column CTAs of 8 events at the least
     if (cudaMalloc(&s->t, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&s->X, sizeof(double) * n * d) != cudaSuccess ||
         cudaMalloc(&s->lam0, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&s->lam1, sizeof(double) * n) != cudaSuccess ||
-        cudaMalloc(&s->part, sizeof(double) * part_n) != cudaSuccess ||
-        cudaMalloc(&s->rowterm, sizeof(double) * (size_t)max_block * (2 * s->sms + 1)) != cudaSuccess ||
-        cudaMalloc(&s->loglik, sizeof(double)) != cudaSuccess || cudaMalloc(&s->ctl, sizeof(int) * 2) != cudaSuccess ||
-        cudaMalloc(&s->pos, sizeof(int) * n) != cudaSuccess) {
+        cudaMalloc(&s->part, sizeof(double) * (size_t)kRateSplit * n) != cudaSuccess ||
+        cudaMalloc(&s->cpart, sizeof(double) * ncta) != cudaSuccess ||
+        cudaMalloc(&s->rowterm, sizeof(double) * (size_t)max_block * most_splits(n, s->sms)) != cudaSuccess ||
+        cudaMalloc(&s->loglik, sizeof(double)) != cudaSuccess || cudaMalloc(&s->Tmax, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->bterm, sizeof(double) * max_block) != cudaSuccess ||
+        cudaMalloc(&s->bticket, sizeof(unsigned) * max_block) != cudaSuccess ||
+        cudaMalloc(&s->ctl, sizeof(int) * 3) != cudaSuccess) {
         cudaGetLastError();
         return bail(HAWKES_ERR_OOM);
     }
     if (cudaMemcpyAsync(s->t, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(s->X, X, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(s->ctl, 0, sizeof(int) * 2, st) != cudaSuccess) {
+        cudaMemsetAsync(s->ctl, 0, sizeof(int) * 3, st) != cudaSuccess ||
+        cudaMemsetAsync(s->bticket, 0, sizeof(unsigned) * max_block, st) != cudaSuccess) {
         cudaGetLastError();
         return bail(HAWKES_ERR_CUDA);
     }
+    tmax_kernel<<<1, kThreads, 0, st>>>(s->t, n, s->Tmax);
+    if (cudaGetLastError() != cudaSuccess)
+        return bail(HAWKES_ERR_CUDA);
     if (enqueue_rates(s, st) != HAWKES_OK)
         return bail(HAWKES_ERR_CUDA);
     *out = s;
@@ -659,10 +785,13 @@ void hawkes_mwg_destroy(hawkes_mwg *s)
     cudaFree(s->lam0);
     cudaFree(s->lam1);
     cudaFree(s->part);
+    cudaFree(s->cpart);
     cudaFree(s->rowterm);
     cudaFree(s->loglik);
+    cudaFree(s->Tmax);
+    cudaFree(s->bterm);
+    cudaFree(s->bticket);
     cudaFree(s->ctl);
-    cudaFree(s->pos);
     delete s;
 }
 
@@ -701,8 +830,14 @@ hawkes_status hawkes_mwg_propose_circle(hawkes_mwg *s, int32_t nb, const int64_t
         (nb > 0 && (!idx || !centers || !radii || !u || !X_new)))
         return fail(s, HAWKES_ERR_INVALID_ARG, "bad circle-proposal arguments");
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
-    propose_circle_kernel<<<1, kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        s->X, s->n, Block{nb, idx, nullptr}, centers, radii, eps, tries, u, X_new, log_q_ratio, s->ctl + 1);
+    const Block B{nb, idx, nullptr};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (nb <= 32)  // one warp: no cross-warp step in the q-ratio sum
+        propose_circle_kernel<32><<<1, 32, 0, st>>>(s->X, s->n, B, centers, radii, eps, tries, u, X_new, log_q_ratio,
+                                                    s->ctl + 1);
+    else
+        propose_circle_kernel<kThreads><<<1, kThreads, 0, st>>>(s->X, s->n, B, centers, radii, eps, tries, u, X_new,
+                                                                log_q_ratio, s->ctl + 1);
     MWG_TRY(cudaGetLastError(), "circle proposals");
     return HAWKES_OK;
 }
@@ -717,8 +852,13 @@ hawkes_status hawkes_mwg_propose_box(hawkes_mwg *s, int32_t nb, const int64_t *i
         (nb > 0 && (!idx || !lo || !hi || !u || !X_new)))
         return fail(s, HAWKES_ERR_INVALID_ARG, "bad box-proposal arguments");
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
-    propose_box_kernel<<<1, kThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        s->X, s->n, s->d, Block{nb, idx, nullptr}, lo, hi, sd, u, X_new, log_q_ratio, s->ctl + 1);
+    const Block B{nb, idx, nullptr};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if ((int64_t)nb * s->d <= 32)
+        propose_box_kernel<32><<<1, 32, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, u, X_new, log_q_ratio, s->ctl + 1);
+    else
+        propose_box_kernel<kThreads><<<1, kThreads, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, u, X_new, log_q_ratio,
+                                                             s->ctl + 1);
     MWG_TRY(cudaGetLastError(), "box proposals");
     return HAWKES_OK;
 }
