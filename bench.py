@@ -287,8 +287,8 @@ def mwg_workload(dev, stream, l2) -> dict:
     iters = 30
     gen = torch.Generator(device=dev).manual_seed(12)
     res = {"workload": "c2_gunfire_like_n10000_d2", "n": w.n, "d": w.d, "iterations_per_graph": iters}
-    for nb in (1, 32):
-        s = HawkesMwG(t, X, w.params, max_block=nb)
+    for nb, prec in ((1, "fp64"), (32, "fp64"), (1, "mixed"), (32, "mixed")):
+        s = HawkesMwG(t, X, w.params, max_block=nb, precision=prec)
         idx = torch.stack([torch.randperm(w.n, generator=gen, device=dev)[:nb] for _ in range(iters)])
         u = torch.rand((iters, nb, w.d), generator=gen, device=dev, dtype=torch.float64)
         log_u = torch.log(torch.rand(iters, generator=gen, device=dev, dtype=torch.float64))
@@ -316,9 +316,11 @@ def mwg_workload(dev, stream, l2) -> dict:
         s.sync_status()
         acc = int(sum(o[1].item() for o in outs))
         per = m / iters
-        res[f"block_{nb}"] = {"ms_per_iteration": per, "iterations_per_s": 1e3 / per,
+        res[f"block_{nb}" + ("" if prec == "fp64" else "_mixed")] = {
+                              "ms_per_iteration": per, "iterations_per_s": 1e3 / per,
                               "location_updates_per_s": nb * 1e3 / per,
-                              "fp64_pair_evals_per_iteration": 3 * nb * w.n, "accepted_last_replay": acc}
+                              "pair_terms_per_iteration": 3 * nb * w.n, "pair_term_precision": prec,
+                              "accepted_last_replay": acc}
         s.close()
     # the same proposal evaluated by a full log-likelihood instead (what the increments avoid)
     ctx = HawkesContext(device=dev.index or 0, max_n=w.n, max_d=w.d)
@@ -450,10 +452,11 @@ def run_workload_calls(name: str, calls: int) -> int:
             hawkes_bmds_loglik_grad(ctx, Y, X, b.sigma2, "mixed", check=False)
         ctx.sync_status()
         ctx.close()
-    elif name in ("mwg1", "mwg32"):
+    elif name in ("mwg1", "mwg32", "mwg32_mixed"):
         nb = 1 if name == "mwg1" else 32
         w = synth.make_c2()
-        s = HawkesMwG(torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev), w.params, max_block=nb)
+        s = HawkesMwG(torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev), w.params, max_block=nb,
+                      precision="mixed" if name.endswith("_mixed") else "fp64")
         lo, hi = torch.tensor(w.box_lo, device=dev), torch.tensor(w.box_hi, device=dev)
         gen = torch.Generator(device=dev).manual_seed(12)
         for _ in range(calls):
@@ -512,7 +515,8 @@ def main():
     ap.add_argument("--kernels-only", action="store_true",
                     help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
     ap.add_argument("--workload", default=None,
-                    choices=["bmds", "bmds_f64y", "mwg1", "mwg32", "bmds_hmc", "hmc_c2", "batched_c4"],
+                    choices=["bmds", "bmds_f64y", "mwg1", "mwg32", "mwg32_mixed", "bmds_hmc", "hmc_c2",
+                             "batched_c4"],
                     help="with --kernels-only: run warmup + steps calls of that other workload instead "
                          "(for profiler captures); prints no JSON")
     args = ap.parse_args()

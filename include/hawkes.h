@@ -246,8 +246,9 @@ size_t hawkes_bmds_workspace_bytes(int64_t n, int32_t d, hawkes_precision prec);
  *   Delta ell = ell(X with x_b -> x*_b, b in B) - ell(X)
  *             = sum_n [log lambda*_n - log lambda_n]
  * costs O(|B| N) pair evaluations instead of the O(N^2) of a full evaluation
- * (the integrated rate does not depend on X).  Everything is FP64; calls
- * enqueue on `stream`, allocate nothing after hawkes_mwg_create and read
+ * (the integrated rate does not depend on X).  Rates, logs and decisions
+ * are FP64, and so are the pair terms unless hawkes_mwg_set_precision
+ * selects FP32 for them; calls enqueue on `stream`, allocate nothing after hawkes_mwg_create and read
  * nothing back to the host (the accept decision and the commit happen on the
  * device), so a sequence of steps may be captured in a CUDA graph.  Use one
  * stream per state.  Device-side data errors (an index out of range or
@@ -316,6 +317,24 @@ hawkes_status hawkes_mwg_propose_box(hawkes_mwg *s, int32_t nb, const int64_t *i
 /* Recompute every rate and ell from the current locations (O(n^2)); the
  * incremental updates accumulate rounding over many accepted steps. */
 hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream);
+
+/* Precision of the pair terms in later delta and step calls (a state starts
+ * in HAWKES_PREC_FP64).  HAWKES_PREC_MIXED evaluates them in FP32: FP32
+ * (hi, lo) copies of X and t (made on `stream` by this call and kept up to
+ * date by accepted steps), differences (hi - hi) + (lo - lo), the MUFU
+ * exponential with the prefactor as an FP32 factor, compensated FP32 sums,
+ * exact time comparisons; the rates, logs, Delta ell and the decision stay
+ * FP64.  An unmoved event takes the FP64 path where its rate is below
+ * max(prefactors) 2^-60 (FP32 terms could underflow) or where the move takes
+ * away all but 1/1024 of it (the FP32 error would be magnified); a moved
+ * event whose new rate is below that bound is recomputed in FP64.  The
+ * relative error of each new rate is then a few 2^-24 times (1 + the
+ * exponent of its dominant terms); refresh more often than in FP64.  When
+ * some |x| or t is 2^100 or more the state keeps evaluating in FP64, and a
+ * proposal coordinate of that size counts as a bad proposal.  Returns
+ * HAWKES_ERR_INVALID_ARG when a kernel prefactor or scale (times log2 e)
+ * lies outside [2^-100, 2^100]. */
+hawkes_status hawkes_mwg_set_precision(hawkes_mwg *s, hawkes_precision prec, hawkes_stream stream);
 
 /* Copy the current locations (device [n*d]), rates (device [n]) and running
  * ell (device [1]) out; any pointer may be NULL. */

@@ -36,6 +36,7 @@ EXPORTED = (
     "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
     "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
     "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box", "hawkes_bmds_hmc_trajectory",
+    "hawkes_mwg_set_precision",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -95,6 +96,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_mwg_step.restype = st
     lib.hawkes_mwg_refresh.argtypes = [vp, vp]
     lib.hawkes_mwg_refresh.restype = st
+    lib.hawkes_mwg_set_precision.argtypes = [vp, ctypes.c_int, vp]
+    lib.hawkes_mwg_set_precision.restype = st
     lib.hawkes_mwg_read.argtypes = [vp, vp, dp, dp, dp]
     lib.hawkes_mwg_read.restype = st
     lib.hawkes_mwg_propose_circle.argtypes = [vp, i32, dp, dp, dp, ctypes.c_double, i32, dp, vp, dp, dp]

@@ -356,9 +356,11 @@ def version() -> str:
 class HawkesMwG:
     """Incremental Metropolis-within-Gibbs state over the event locations
     (hawkes_mwg_* in the C ABI): FP64 rates cached on the device, block moves
-    evaluated in O(|B| N), accept and commit on the device."""
+    evaluated in O(|B| N), accept and commit on the device.  precision
+    "fp64" (default) evaluates the pair terms in FP64, "mixed" in FP32 with
+    FP64 logs, rates and decisions."""
 
-    def __init__(self, t, X, params, max_block: int = 64, device: int | None = None):
+    def __init__(self, t, X, params, max_block: int = 64, device: int | None = None, precision: str = "fp64"):
         self.lib = _lib.load()
         t = _dev_f64(t, "t")
         X = _dev_f64(X, "X")
@@ -374,6 +376,8 @@ class HawkesMwG:
             raise HawkesError(st, "hawkes_mwg_create failed")
         self.handle = h
         self._dev = t.device
+        if precision != "fp64":
+            self.set_precision(precision)
 
     def stream(self):
         return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
@@ -381,6 +385,10 @@ class HawkesMwG:
     def check(self, status: int):
         if status != 0:
             raise HawkesError(status, self.lib.hawkes_mwg_last_error(self.handle).decode())
+
+    def set_precision(self, precision: str):
+        """Precision of the pair terms of later calls ("mixed" or "fp64")."""
+        self.check(self.lib.hawkes_mwg_set_precision(self.handle, _precision(precision), self.stream()))
 
     def close(self):
         if getattr(self, "handle", None):

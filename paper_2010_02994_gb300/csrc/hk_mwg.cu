@@ -19,7 +19,8 @@
 // log u < Delta ell + log q-ratio and, on accept, the commit.  The rates live
 // in two buffers; the device-side index of the current one flips on accept,
 // so no call reads anything back to the host and a sequence of steps can be
-// captured in a CUDA graph.  Everything is FP64.
+// captured in a CUDA graph.  Rates, logs and decisions are FP64; the pair
+// terms are FP64 or, in the mixed precision, FP32 (see State32 below).
 #include <cuda_runtime.h>
 
 #include <math_constants.h>
@@ -66,6 +67,94 @@ __device__ __forceinline__ double contrib(const double *xm, double tm, const dou
     if (ts < tm)
         v += k.Cxi * exp(-(k.omega * dt + r2 * k.c));
     return v;
+}
+
+// ---------------------------------------------------- mixed precision --
+//
+// The pair terms in FP32: coordinates and times held as FP32 (hi, lo) pairs
+// (hi the nearest float, lo the nearest float to the rest), differences
+// taken as (hi - hi) + (lo - lo) (relative error a few 2^-24: when the hi
+// parts cancel they are within an ulp and subtract exactly), exponentials
+// on the MUFU (ex2.approx) with the prefactor as an FP32 factor, and
+// compensated FP32 sums.  The tie indicators compare the FP64 times exactly,
+// through their bit patterns.  Logs, rates and the decision stay FP64.
+struct State32 {
+    float *xh, *xl;         // n x d
+    float *th, *tl;         // n
+    float Cmu, Cxi;         // prefactors of the two kernels
+    float a2, b2, c2, w2;   // a, b, c, omega times log2(e)
+    double tau;             // rates below tau take the FP64 path (FP32 terms underflow)
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void split32(double v, float &h, float &l)
+{
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+// For t >= 0 the bit pattern with the sign cleared (so -0 equals +0) orders
+// like the value: the time indicators compare these keys.
+__device__ __forceinline__ long long tkey(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffLL; }
+
+struct Sum32 {  // compensated (Kahan) FP32 sum
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float u = s + y;
+        c = (u - s) - y;
+        s = u;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// contrib() in FP32: event s's contribution to the rate at event m.
+template <int D>
+__device__ __forceinline__ float contrib32(const float *xmh, const float *xml, float tmh, float tml, long long km,
+                                           const float *xsh, const float *xsl, float tsh, float tsl, long long ks,
+                                           const State32 &c)
+{
+    float r2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const float dx = (xmh[q] - xsh[q]) + (xml[q] - xsl[q]);
+        r2 = fmaf(dx, dx, r2);
+    }
+    const float dt = (tmh - tsh) + (tml - tsl);
+    float v = 0.f;
+    if (ks != km)
+        v = c.Cmu * ex2_approx(-fmaf(r2, c.a2, dt * dt * c.b2));
+    if (ks < km)
+        v = fmaf(c.Cxi, ex2_approx(-fmaf(c.w2, dt, r2 * c.c2)), v);
+    return v;
+}
+
+// FP32 copies of X and t; flag[0] is set when some |value| >= 2^100, where
+// the FP32 differences could overflow (the state then stays on FP64).
+__global__ void split_kernel(const double *__restrict__ X, const double *__restrict__ t, int64_t n, int d, float *xh,
+                             float *xl, float *th, float *tl, int *flag)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * d; i += stride) {
+        const double v = X[i];
+        bad |= !(fabs(v) < 0x1p100);
+        split32(v, xh[i], xl[i]);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v = t[i];
+        bad |= !(fabs(v) < 0x1p100);
+        split32(v, th[i], tl[i]);
+    }
+    if (bad)
+        atomicOr(flag, 1);
 }
 
 // Sum over a CTA of NT threads (a multiple of 32), valid in thread 0: a
@@ -272,40 +361,100 @@ __device__ void mark_block(const Block &B, int64_t n, int64_t lo, int64_t cnt, u
     __syncthreads();
 }
 
+// Everything one proposal's launch needs.
+struct EvalArgs {
+    const double *t;
+    double *X;
+    int64_t n;
+    Consts k;
+    State32 m32;
+    Block B;
+    Launch L;
+    double *lam0, *lam1;
+    int *ctl;  // [0] current rate buffer, [1] status, [2] ticket, [3] FP32 range flag
+    double *cpart, *rowpart, *bterm;
+    unsigned *bticket;
+    double *out_delta;
+    bool step;
+    const double *log_q_ratio, *log_u;
+    int *accepted_out;
+    double *loglik;
+};
+
+// Delta_m of an unmoved event m in FP64 over the whole block, reading the
+// block from global memory (the FP64 path of the mixed precision).
 template <int D>
-__global__ void __launch_bounds__(kEvalThreads) eval_kernel(const double *__restrict__ t, double *X, int64_t n,
-                                                            Consts k, Block B, Launch L, double *lam0,
-                                                            double *lam1, int *ctl, double *cpart, double *rowpart,
-                                                            unsigned *bticket, double *bterm, double *out_delta,
-                                                            bool step,
-                                                            const double *log_q_ratio, const double *log_u,
-                                                            int *accepted_out, double *loglik)
+__device__ double delta64(const double *xm, double tm, const EvalArgs &a)
+{
+    double dl = 0.0;
+    for (int b = 0; b < a.B.nb; ++b) {
+        const int64_t mb = a.B.idx[b];
+        if (mb < 0 || mb >= a.n)
+            continue;
+        const double tb = a.t[mb];
+        dl += contrib(xm, tm, a.B.xnew + (int64_t)b * D, tb, D, a.k) - contrib(xm, tm, a.X + mb * D, tb, D, a.k);
+    }
+    return dl;
+}
+
+// Position of event m in the block, or -1.
+__device__ __forceinline__ int block_pos(const Block &B, int64_t m)
+{
+    for (int p = 0; p < B.nb; ++p)
+        if (B.idx[p] == m)
+            return p;
+    return -1;
+}
+
+template <int D, bool MIXED>
+__global__ void __launch_bounds__(kEvalThreads) eval_kernel(const EvalArgs a)
 {
     constexpr int d = D;
-    extern __shared__ double blk[];  // column part: old places, new places, times of the block
-    double *sxo = blk, *sxn = blk + B.nb * d, *stb = blk + 2 * B.nb * d;
+    extern __shared__ __align__(16) unsigned char blk_raw[];  // the block, staged by the column part
     __shared__ unsigned bits[kRangeMax / 32];
     __shared__ double sh[kEvalThreads / 32];
+    __shared__ double sl;
     __shared__ int flag, acc;
-    int *status = ctl + 1;
+    const Block &B = a.B;
+    const int64_t n = a.n;
+    int *ctl = a.ctl, *status = ctl + 1;
     const int act = ctl[0];
-    const double *lam = act ? lam1 : lam0;
-    double *lam_new = act ? lam0 : lam1;
-    if ((int)blockIdx.x < L.ncol) {
+    const bool use32 = MIXED && ctl[3] == 0;
+    const double *lam = act ? a.lam1 : a.lam0;
+    double *lam_new = act ? a.lam0 : a.lam1;
+    const State32 &c32 = a.m32;
+    if ((int)blockIdx.x < a.L.ncol) {
         // column part: every unmoved m of this CTA's range gets the change of
         // its rate, sum over b of k(m <- x*_b) - k(m <- x_b)
-        const int ev = kEvalThreads / L.lanes;
+        const int ev = kEvalThreads / a.L.lanes;
         const int64_t lo = (int64_t)blockIdx.x * ev;
+        double *sxo = reinterpret_cast<double *>(blk_raw), *sxn = sxo + B.nb * d, *stb = sxn + B.nb * d;
+        float *soh = reinterpret_cast<float *>(blk_raw), *sol = soh + B.nb * d, *snh = sol + B.nb * d,
+              *snl = snh + B.nb * d, *sth = snl + B.nb * d, *stl = sth + B.nb;
+        long long *skey = reinterpret_cast<long long *>(stl + B.nb);  // 8-byte aligned: 4 nb (4 d + 2) bytes in
         for (int b = threadIdx.x; b < B.nb; b += kEvalThreads) {
             const int64_t m = B.idx[b];
             const bool ok = m >= 0 && m < n;
-            stb[b] = ok ? t[m] : 0.0;
             bool bad = false;
-            for (int q = 0; q < d; ++q) {
-                sxo[b * d + q] = ok ? X[m * d + q] : 0.0;
-                const double v = B.xnew[(int64_t)b * d + q];
-                bad |= !isfinite(v);
-                sxn[b * d + q] = v;
+            if (use32) {
+                sth[b] = ok ? c32.th[m] : 0.f;
+                stl[b] = ok ? c32.tl[m] : 0.f;
+                skey[b] = ok ? tkey(a.t[m]) : 0;
+                for (int q = 0; q < d; ++q) {
+                    soh[b * d + q] = ok ? c32.xh[m * d + q] : 0.f;
+                    sol[b * d + q] = ok ? c32.xl[m * d + q] : 0.f;
+                    const double v = B.xnew[(int64_t)b * d + q];
+                    bad |= !(fabs(v) < 0x1p100);
+                    split32(v, snh[b * d + q], snl[b * d + q]);
+                }
+            } else {
+                stb[b] = ok ? a.t[m] : 0.0;
+                for (int q = 0; q < d; ++q) {
+                    sxo[b * d + q] = ok ? a.X[m * d + q] : 0.0;
+                    const double v = B.xnew[(int64_t)b * d + q];
+                    bad |= !isfinite(v);
+                    sxn[b * d + q] = v;
+                }
             }
             if (blockIdx.x == 0) {
                 if (!ok)
@@ -315,77 +464,146 @@ __global__ void __launch_bounds__(kEvalThreads) eval_kernel(const double *__rest
             }
         }
         mark_block(B, n, lo, ev, bits, status);
-        const int e = threadIdx.x / L.lanes, j = threadIdx.x % L.lanes;
+        const int e = threadIdx.x / a.L.lanes, j = threadIdx.x % a.L.lanes;
         const int64_t m = lo + e;
         const bool mine = m < n && !((bits[e >> 5] >> (e & 31)) & 1u);
         double delta = 0.0;
         if (mine) {
-            double xm[D];
-            for (int q = 0; q < d; ++q)
-                xm[q] = X[m * d + q];
-            const double tm = t[m];
-            for (int b = j; b < B.nb; b += L.lanes)
-                delta += contrib(xm, tm, sxn + b * d, stb[b], d, k) - contrib(xm, tm, sxo + b * d, stb[b], d, k);
+            if (use32) {
+                float xmh[D], xml[D];
+                for (int q = 0; q < d; ++q) {
+                    xmh[q] = c32.xh[m * d + q];
+                    xml[q] = c32.xl[m * d + q];
+                }
+                const float tmh = c32.th[m], tml = c32.tl[m];
+                const long long km = tkey(a.t[m]);
+                Sum32 s;
+                for (int b = j; b < B.nb; b += a.L.lanes)
+                    s.add(contrib32<D>(xmh, xml, tmh, tml, km, snh + b * d, snl + b * d, sth[b], stl[b], skey[b], c32) -
+                          contrib32<D>(xmh, xml, tmh, tml, km, soh + b * d, sol + b * d, sth[b], stl[b], skey[b], c32));
+                delta = s.value();
+            } else {
+                double xm[D];
+                for (int q = 0; q < d; ++q)
+                    xm[q] = a.X[m * d + q];
+                const double tm = a.t[m];
+                for (int b = j; b < B.nb; b += a.L.lanes)
+                    delta += contrib(xm, tm, sxn + b * d, stb[b], d, a.k) - contrib(xm, tm, sxo + b * d, stb[b], d, a.k);
+            }
         }
-        for (int o = L.lanes / 2; o > 0; o >>= 1)  // the event's lanes, in a fixed order
-            delta += __shfl_down_sync(0xffffffffu, delta, o, L.lanes);
+        for (int o = a.L.lanes / 2; o > 0; o >>= 1)  // the event's lanes, in a fixed order
+            delta += __shfl_down_sync(0xffffffffu, delta, o, a.L.lanes);
         double term = 0.0;
         if (mine && j == 0) {
             const double l = lam[m];
+            // FP64 again where FP32 terms may underflow or where the move takes
+            // away nearly all of the rate (the FP32 error would be magnified)
+            if (use32 && (!(l >= c32.tau) || l + delta < l * 0x1p-10)) {
+                double xm[D];
+                for (int q = 0; q < d; ++q)
+                    xm[q] = a.X[m * d + q];
+                delta = delta64<D>(xm, a.t[m], a);
+            }
             const double ln = l + delta;
             lam_new[m] = ln;
             term = log_ratio(l, ln, delta);
         }
         term = cta_sum<kEvalThreads>(term, sh);
         if (threadIdx.x == 0)
-            cpart[blockIdx.x] = term;
+            a.cpart[blockIdx.x] = term;
     } else {
         // row part: moved event b's new rate over one range of events, the
         // moved ones at their proposed places
-        const int r = (int)blockIdx.x - L.ncol;
-        const int b = r / L.splits, sp = r % L.splits;
-        const int64_t lo = min((int64_t)sp * L.per, n), cnt = min(L.per, n - lo);
+        const int r = (int)blockIdx.x - a.L.ncol;
+        const int b = r / a.L.splits;
+        const int64_t lo = min((int64_t)(r % a.L.splits) * a.L.per, n), cnt = min(a.L.per, n - lo);
         mark_block(B, n, lo, cnt, bits, nullptr);
         const int64_t mb = B.idx[b];
+        const bool okb = mb >= 0 && mb < n;  // a bad index is reported by the column part
         double s = 0.0;
-        if (mb >= 0 && mb < n) {  // a bad index is reported by the column part
+        if (okb && use32) {
+            float xbh[D], xbl[D];
+            for (int q = 0; q < d; ++q)
+                split32(B.xnew[(int64_t)b * d + q], xbh[q], xbl[q]);
+            const float tbh = c32.th[mb], tbl = c32.tl[mb];
+            const long long kb = tkey(a.t[mb]);
+            Sum32 acc32;
+            for (int64_t jj = threadIdx.x; jj < cnt; jj += kEvalThreads) {
+                const int64_t m = lo + jj;
+                if (m == mb)
+                    continue;
+                float xh[D], xl[D];
+                if ((bits[jj >> 5] >> (jj & 31)) & 1u) {
+                    const int p = block_pos(B, m);
+                    for (int q = 0; q < d; ++q)
+                        split32(B.xnew[(int64_t)p * d + q], xh[q], xl[q]);
+                } else {
+                    for (int q = 0; q < d; ++q) {
+                        xh[q] = c32.xh[m * d + q];
+                        xl[q] = c32.xl[m * d + q];
+                    }
+                }
+                acc32.add(contrib32<D>(xbh, xbl, tbh, tbl, kb, xh, xl, c32.th[m], c32.tl[m], tkey(a.t[m]), c32));
+            }
+            s = acc32.value();
+        } else if (okb) {
             double xb[D];
             for (int q = 0; q < d; ++q)
                 xb[q] = B.xnew[(int64_t)b * d + q];
-            const double tb = t[mb];
-            for (int64_t j = threadIdx.x; j < cnt; j += kEvalThreads) {
-                const int64_t m = lo + j;
+            const double tb = a.t[mb];
+            for (int64_t jj = threadIdx.x; jj < cnt; jj += kEvalThreads) {
+                const int64_t m = lo + jj;
                 if (m == mb)
                     continue;
-                const double *xm = X + m * d;
-                if ((bits[j >> 5] >> (j & 31)) & 1u)
-                    for (int p = 0; p < B.nb; ++p)
-                        if (B.idx[p] == m) {
-                            xm = B.xnew + (int64_t)p * d;
-                            break;
-                        }
-                s += contrib(xb, tb, xm, t[m], d, k);
+                const double *xm = a.X + m * d;
+                if ((bits[jj >> 5] >> (jj & 31)) & 1u)
+                    xm = B.xnew + (int64_t)block_pos(B, m) * d;
+                s += contrib(xb, tb, xm, a.t[m], d, a.k);
             }
         }
         s = cta_sum<kEvalThreads>(s, sh);
         if (threadIdx.x == 0)
-            rowpart[r] = s;
+            a.rowpart[r] = s;
         // the last of event b's CTAs adds its splits in order (lane-strided,
         // then a shuffle tree) and takes the log ratio of its rate
-        if (last_cta_of(bticket + b, L.splits, &flag) && threadIdx.x < 32) {
-            double lnew = 0.0;
-            for (int q = threadIdx.x; q < L.splits; q += 32)
-                lnew += __ldcg(rowpart + (int64_t)b * L.splits + q);
-            for (int o = 16; o > 0; o >>= 1)
-                lnew += __shfl_down_sync(0xffffffffu, lnew, o);
-            if (threadIdx.x == 0) {
+        if (last_cta_of(a.bticket + b, a.L.splits, &flag)) {
+            if (threadIdx.x < 32) {
+                double lnew = 0.0;
+                for (int q = threadIdx.x; q < a.L.splits; q += 32)
+                    lnew += __ldcg(a.rowpart + (int64_t)b * a.L.splits + q);
+                for (int o = 16; o > 0; o >>= 1)
+                    lnew += __shfl_down_sync(0xffffffffu, lnew, o);
+                if (threadIdx.x == 0)
+                    sl = lnew;
+            }
+            __syncthreads();
+            if (use32 && okb && !(sl >= c32.tau)) {
+                // FP32 terms may have underflowed: the whole rate again in FP64
+                double xb[D];
+                for (int q = 0; q < d; ++q)
+                    xb[q] = B.xnew[(int64_t)b * d + q];
+                const double tb = a.t[mb];
                 double v = 0.0;
-                if (mb >= 0 && mb < n) {
+                for (int64_t m = threadIdx.x; m < n; m += kEvalThreads) {
+                    if (m == mb)
+                        continue;
+                    const int p = block_pos(B, m);
+                    v += contrib(xb, tb, p >= 0 ? B.xnew + (int64_t)p * d : a.X + m * d, a.t[m], d, a.k);
+                }
+                v = cta_sum<kEvalThreads>(v, sh);
+                if (threadIdx.x == 0)
+                    sl = v;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const double lnew = sl;
+                double v = 0.0;
+                if (okb) {
                     const double l = lam[mb];
                     lam_new[mb] = lnew;
                     v = (l > 0.0 && lnew > 0.0) ? log(lnew) - log(l) : log_ratio(l, lnew, lnew - l);
                 }
-                bterm[b] = v;
+                a.bterm[b] = v;
             }
         }
     }
@@ -396,33 +614,36 @@ __global__ void __launch_bounds__(kEvalThreads) eval_kernel(const double *__rest
     // column partials; in step mode the decision and, on accept, the commit.
     double v = 0.0;
     for (int b = threadIdx.x; b < B.nb; b += kEvalThreads)
-        v += __ldcg(bterm + b);
-    for (int c = threadIdx.x; c < L.ncol; c += kEvalThreads)
-        v += __ldcg(cpart + c);
+        v += __ldcg(a.bterm + b);
+    for (int cc = threadIdx.x; cc < a.L.ncol; cc += kEvalThreads)
+        v += __ldcg(a.cpart + cc);
     const double delta = cta_sum<kEvalThreads>(v, sh);
     if (threadIdx.x == 0) {
         const bool bad = *(volatile const int *)status != 0;
         const double dl = bad ? nan("") : delta;
-        if (out_delta)
-            *out_delta = dl;
-        int a = 0;
-        if (step && !bad) {
-            const double lhs = *log_u, rhs = dl + (log_q_ratio ? *log_q_ratio : 0.0);
-            a = (lhs < rhs) ? 1 : 0;  // NaN on either side rejects
+        if (a.out_delta)
+            *a.out_delta = dl;
+        int ac = 0;
+        if (a.step && !bad) {
+            const double lhs = *a.log_u, rhs = dl + (a.log_q_ratio ? *a.log_q_ratio : 0.0);
+            ac = (lhs < rhs) ? 1 : 0;  // NaN on either side rejects
         }
-        acc = a;
-        if (accepted_out)
-            *accepted_out = a;
-        if (a) {
-            *loglik += dl;
+        acc = ac;
+        if (a.accepted_out)
+            *a.accepted_out = ac;
+        if (ac) {
+            *a.loglik += dl;
             ctl[0] = act ^ 1;
         }
     }
     __syncthreads();
     if (acc)
         for (int e = threadIdx.x; e < B.nb * d; e += kEvalThreads) {
-            const int b = e / d, q = e % d;
-            X[B.idx[b] * d + q] = B.xnew[e];
+            const int64_t i = B.idx[e / d] * d + e % d;
+            const double x = B.xnew[e];
+            a.X[i] = x;
+            if (MIXED)
+                split32(x, c32.xh[i], c32.xl[i]);
         }
 }
 
@@ -523,33 +744,63 @@ __global__ void __launch_bounds__(NT) propose_circle_kernel(const double *__rest
         *log_q_ratio = lq;
 }
 
-// Truncated-normal proposals inside the boxes of Eq. (2), one thread per
-// coordinate: x* = x + s Phi^{-1}(Phi(a) + u (Phi(b) - Phi(a))), and the
-// log q-ratio sum log Z(x) - log Z(x*), Z(y) = Phi((hi - y)/s) - Phi((lo - y)/s).
+// Truncated-normal proposals inside the boxes of Eq. (2):
+// x* = x + s Phi^{-1}(Phi(a) + u (Phi(b) - Phi(a))), and the log q-ratio
+// sum log Z(x) - log Z(x*), Z(y) = Phi((hi - y)/s) - Phi((lo - y)/s).  Two
+// adjacent lanes per coordinate, the even one for the lower wall and the odd
+// one for the upper, so that the two normal CDFs of each stage and the two
+// logs run side by side; FP64 on this GPU is a long-latency path, and this
+// chain is most of a small block's step.
 template <int NT>
 __global__ void __launch_bounds__(NT) propose_box_kernel(const double *__restrict__ X, int64_t n, int d, Block B,
                                                          const double *__restrict__ lo, const double *__restrict__ hi,
-                                                         double sd, const double *__restrict__ u, double *X_new,
-                                                         double *log_q_ratio, int *status)
+                                                         double sd, double inv_sd, const double *__restrict__ u,
+                                                         double *X_new, double *log_q_ratio, int *status)
 {
     __shared__ double sh[NT / 32];
     double lq = 0.0;
-    for (int e = threadIdx.x; e < B.nb * d; e += NT) {
-        const int b = e / d, q = e % d;
-        const int64_t m = B.idx[b];
-        if (m < 0 || m >= n) {
-            atomicOr(status, kBadBlock);
-            continue;
+    const int total = 2 * B.nb * d;
+    for (int base = 0; base < total; base += NT) {  // uniform trip count: every lane takes part in the shuffles
+        const int e2 = base + threadIdx.x;
+        const bool active = e2 < total;
+        const int e = e2 >> 1, upper = e2 & 1;
+        bool ok = false;
+        double x = 0.0, l = 0.0, h = 0.0;
+        if (active) {
+            const int b = e / d, q = e % d;
+            const int64_t m = B.idx[b];
+            if (m < 0 || m >= n) {
+                if (!upper)
+                    atomicOr(status, kBadBlock);
+            } else {
+                x = X[m * d + q];
+                l = lo[m * d + q];
+                h = hi[m * d + q];
+                ok = l <= x && x <= h && sd > 0.0;
+                if (!ok && !upper)
+                    atomicOr(status, kBadProposal);
+            }
         }
-        const double x = X[m * d + q], l = lo[m * d + q], h = hi[m * d + q];
-        if (!(l <= x && x <= h) || !(sd > 0.0)) {
-            atomicOr(status, kBadProposal);
-            continue;
+        const double wall = upper ? h : l;
+        const double P = ok ? normcdf((wall - x) * inv_sd) : 0.0;
+        const double Q = __shfl_xor_sync(0xffffffffu, P, 1);
+        const double Pa = upper ? Q : P, Pb = upper ? P : Q;
+        double y = x, L1 = 0.0;
+        if (ok) {
+            if (!upper)
+                y = fmin(fmax(x + sd * normcdfinv(Pa + u[e] * (Pb - Pa)), l), h);
+            else
+                L1 = log(Pb - Pa);
         }
-        const double Pa = normcdf((l - x) / sd), Pb = normcdf((h - x) / sd);
-        const double y = fmin(fmax(x + sd * normcdfinv(Pa + u[e] * (Pb - Pa)), l), h);
-        X_new[e] = y;
-        lq += log(Pb - Pa) - log(normcdf((h - y) / sd) - normcdf((l - y) / sd));
+        y = __shfl_sync(0xffffffffu, y, threadIdx.x & ~1);
+        const double Z = ok ? normcdf((wall - y) * inv_sd) : 0.0;
+        const double Zo = __shfl_xor_sync(0xffffffffu, Z, 1);
+        if (ok) {
+            if (!upper)
+                X_new[e] = y;
+            else
+                lq += L1 - log(Z - Zo);
+        }
     }
     lq = cta_sum<NT>(lq, sh);
     if (threadIdx.x == 0)
@@ -604,7 +855,9 @@ struct hawkes_mwg {
     double *Tmax = nullptr;     // max t
     double *bterm = nullptr;    // per moved event: log of its rate ratio (max_block)
     unsigned *bticket = nullptr;  // per moved event: last-CTA ticket of its row CTAs (max_block)
-    int *ctl = nullptr;         // [0] current rate buffer, [1] status, [2] last-CTA ticket
+    int *ctl = nullptr;         // [0] current rate buffer, [1] status, [2] last-CTA ticket, [3] FP32 range flag
+    hawkes_precision prec = HAWKES_PREC_FP64;
+    State32 m32{};              // FP32 copies of X and t (mixed precision)
 };
 
 namespace {
@@ -628,6 +881,38 @@ hawkes_status cuda_fail(hawkes_mwg *s, cudaError_t e, const char *where)
         if (e_ != cudaSuccess)                  \
             return cuda_fail(s, e_, where);     \
     } while (0)
+
+// FP32 copies of the current X and t and their range flag.
+hawkes_status enqueue_split(hawkes_mwg *s, cudaStream_t st)
+{
+    MWG_TRY(cudaMemsetAsync(s->ctl + 3, 0, sizeof(int), st), "clear range flag");
+    const int grid = (int)std::min<int64_t>(4 * (int64_t)s->sms, (s->n * s->d + kThreads - 1) / kThreads);
+    split_kernel<<<std::max(grid, 1), kThreads, 0, st>>>(s->X, s->t, s->n, s->d, s->m32.xh, s->m32.xl, s->m32.th,
+                                                         s->m32.tl, s->ctl + 3);
+    MWG_TRY(cudaGetLastError(), "split kernel");
+    return HAWKES_OK;
+}
+
+// The FP32 constants of the mixed precision, or false where they leave the
+// range in which FP32 products and the underflow bound below hold.
+bool make_state32(const Consts &k, State32 &c)
+{
+    const double log2e = 1.4426950408889634074;
+    const double v[6] = {k.Cmu, k.Cxi, k.a * log2e, k.b * log2e, k.c * log2e, k.omega * log2e};
+    for (double x : v)
+        if (!(x >= 0x1p-100 && x <= 0x1p100))
+            return false;
+    c.Cmu = (float)v[0];
+    c.Cxi = (float)v[1];
+    c.a2 = (float)v[2];
+    c.b2 = (float)v[3];
+    c.c2 = (float)v[4];
+    c.w2 = (float)v[5];
+    // below tau, FP32 terms that flushed to zero (each < C 2^-126, at most
+    // 2^30 of them) could reach 2^-36 of the rate
+    c.tau = std::max(k.Cmu, k.Cxi) * 0x1p-60;
+    return true;
+}
 
 hawkes_status enqueue_rates(hawkes_mwg *s, cudaStream_t st)
 {
@@ -686,17 +971,39 @@ hawkes_status enqueue_proposal(hawkes_mwg *s, int32_t nb, const int64_t *idx, co
     if (step && !log_u)
         return fail(s, HAWKES_ERR_INVALID_ARG, "log_u must be a device pointer");
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
-    const Block B{nb, idx, X_new};
-    const Launch L = plan_launch(s, nb);
-    const int64_t grid = (int64_t)L.ncol + (int64_t)nb * L.splits;
-    const size_t smem = sizeof(double) * (size_t)nb * (2 * s->d + 1);
-    switch (s->d) {
-#define HK_MWG_EVAL(DD)                                                                                         \
-    case DD:                                                                                                    \
-        eval_kernel<DD><<<(unsigned)grid, kEvalThreads, smem, st>>>(s->t, s->X, s->n, s->k, B, L, s->lam0,      \
-                                                                    s->lam1, s->ctl, s->cpart, s->rowterm,      \
-                                                                    s->bticket, s->bterm, out_delta, step,      \
-                                                                    log_q_ratio, log_u, out_accepted, s->loglik); \
+    EvalArgs a;
+    a.t = s->t;
+    a.X = s->X;
+    a.n = s->n;
+    a.k = s->k;
+    a.m32 = s->m32;
+    a.B = Block{nb, idx, X_new};
+    a.L = plan_launch(s, nb);
+    a.lam0 = s->lam0;
+    a.lam1 = s->lam1;
+    a.ctl = s->ctl;
+    a.cpart = s->cpart;
+    a.rowpart = s->rowterm;
+    a.bterm = s->bterm;
+    a.bticket = s->bticket;
+    a.out_delta = out_delta;
+    a.step = step;
+    a.log_q_ratio = log_q_ratio;
+    a.log_u = log_u;
+    a.accepted_out = out_accepted;
+    a.loglik = s->loglik;
+    const bool mixed = s->prec == HAWKES_PREC_MIXED;
+    const int64_t grid = (int64_t)a.L.ncol + (int64_t)nb * a.L.splits;
+    // the staged block: FP64 old and new places and times, or their FP32
+    // (hi, lo) pairs and the time keys
+    const size_t smem = mixed ? (size_t)nb * (16 * s->d + 16) : sizeof(double) * (size_t)nb * (2 * s->d + 1);
+    switch (s->d * 2 + (mixed ? 1 : 0)) {
+#define HK_MWG_EVAL(DD)                                                                   \
+    case 2 * DD:                                                                          \
+        eval_kernel<DD, false><<<(unsigned)grid, kEvalThreads, smem, st>>>(a);            \
+        break;                                                                            \
+    case 2 * DD + 1:                                                                      \
+        eval_kernel<DD, true><<<(unsigned)grid, kEvalThreads, smem, st>>>(a);             \
         break;
         HK_MWG_EVAL(1)
         HK_MWG_EVAL(2)
@@ -755,13 +1062,17 @@ hawkes_status hawkes_mwg_create(int32_t device, const double *t, const double *X
         cudaMalloc(&s->loglik, sizeof(double)) != cudaSuccess || cudaMalloc(&s->Tmax, sizeof(double)) != cudaSuccess ||
         cudaMalloc(&s->bterm, sizeof(double) * max_block) != cudaSuccess ||
         cudaMalloc(&s->bticket, sizeof(unsigned) * max_block) != cudaSuccess ||
-        cudaMalloc(&s->ctl, sizeof(int) * 3) != cudaSuccess) {
+        cudaMalloc(&s->m32.xh, sizeof(float) * n * d) != cudaSuccess ||
+        cudaMalloc(&s->m32.xl, sizeof(float) * n * d) != cudaSuccess ||
+        cudaMalloc(&s->m32.th, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&s->m32.tl, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&s->ctl, sizeof(int) * 4) != cudaSuccess) {
         cudaGetLastError();
         return bail(HAWKES_ERR_OOM);
     }
     if (cudaMemcpyAsync(s->t, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(s->X, X, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(s->ctl, 0, sizeof(int) * 3, st) != cudaSuccess ||
+        cudaMemsetAsync(s->ctl, 0, sizeof(int) * 4, st) != cudaSuccess ||
         cudaMemsetAsync(s->bticket, 0, sizeof(unsigned) * max_block, st) != cudaSuccess) {
         cudaGetLastError();
         return bail(HAWKES_ERR_CUDA);
@@ -791,6 +1102,10 @@ void hawkes_mwg_destroy(hawkes_mwg *s)
     cudaFree(s->Tmax);
     cudaFree(s->bterm);
     cudaFree(s->bticket);
+    cudaFree(s->m32.xh);
+    cudaFree(s->m32.xl);
+    cudaFree(s->m32.th);
+    cudaFree(s->m32.tl);
     cudaFree(s->ctl);
     delete s;
 }
@@ -854,11 +1169,12 @@ hawkes_status hawkes_mwg_propose_box(hawkes_mwg *s, int32_t nb, const int64_t *i
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
     const Block B{nb, idx, nullptr};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if ((int64_t)nb * s->d <= 32)
-        propose_box_kernel<32><<<1, 32, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, u, X_new, log_q_ratio, s->ctl + 1);
+    if (2 * (int64_t)nb * s->d <= 32)
+        propose_box_kernel<32><<<1, 32, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, 1.0 / sd, u, X_new, log_q_ratio,
+                                                 s->ctl + 1);
     else
-        propose_box_kernel<kThreads><<<1, kThreads, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, u, X_new, log_q_ratio,
-                                                             s->ctl + 1);
+        propose_box_kernel<kThreads><<<1, kThreads, 0, st>>>(s->X, s->n, s->d, B, lo, hi, sd, 1.0 / sd, u, X_new,
+                                                             log_q_ratio, s->ctl + 1);
     MWG_TRY(cudaGetLastError(), "box proposals");
     return HAWKES_OK;
 }
@@ -868,7 +1184,34 @@ hawkes_status hawkes_mwg_refresh(hawkes_mwg *s, hawkes_stream stream)
     if (!s)
         return HAWKES_ERR_INVALID_ARG;
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
-    return enqueue_rates(s, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (s->prec == HAWKES_PREC_MIXED) {
+        const hawkes_status r = enqueue_split(s, st);
+        if (r != HAWKES_OK)
+            return r;
+    }
+    return enqueue_rates(s, st);
+}
+
+hawkes_status hawkes_mwg_set_precision(hawkes_mwg *s, hawkes_precision prec, hawkes_stream stream)
+{
+    if (!s)
+        return HAWKES_ERR_INVALID_ARG;
+    if (prec != HAWKES_PREC_MIXED && prec != HAWKES_PREC_FP64)
+        return fail(s, HAWKES_ERR_INVALID_ARG, "unknown precision");
+    if (prec == HAWKES_PREC_MIXED) {
+        State32 c = s->m32;
+        if (!make_state32(s->k, c))
+            return fail(s, HAWKES_ERR_INVALID_ARG,
+                        "mixed precision needs the kernel prefactors and scales within [2^-100, 2^100]");
+        MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
+        const hawkes_status r = enqueue_split(s, reinterpret_cast<cudaStream_t>(stream));
+        if (r != HAWKES_OK)
+            return r;
+        s->m32 = c;
+    }
+    s->prec = prec;
+    return HAWKES_OK;
 }
 
 hawkes_status hawkes_mwg_read(hawkes_mwg *s, hawkes_stream stream, double *X_out, double *lam_out,
@@ -904,7 +1247,8 @@ hawkes_status hawkes_mwg_sync_status(hawkes_mwg *s, hawkes_stream stream)
     if (st & kBadBlock)
         return fail(s, HAWKES_ERR_INVALID_DATA, "a block index is out of range or repeated");
     if (st & kBadProposal)
-        return fail(s, HAWKES_ERR_INVALID_DATA, "a proposed location is not finite");
+        return fail(s, HAWKES_ERR_INVALID_DATA,
+                    "a proposed location is not finite (or, in mixed precision, has a coordinate of 2^100 or more)");
     s->err.clear();
     return HAWKES_OK;
 }
