@@ -369,7 +369,8 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     import torch
 
     import synth
-    from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad, hmc_leapfrog_trajectory
+    from paper_2010_02994_gb300 import (HawkesContext, hawkes_batch_hmc_trajectory, hawkes_batch_loglik_grad,
+                                        hmc_leapfrog_trajectory)
 
     out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms),
            "mwg_gunfire_like": mwg_workload(dev, stream, l2),
@@ -426,6 +427,30 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     m = statistics.median(ms)
     out["hmc_c2"] = {"n": w.n, "d": w.d, "leapfrog_steps": steps, "ms_per_trajectory": m,
                      "trajectories_per_s": 1e3 / m, "grad_evals_per_s": (steps + 1) * 1e3 / m}
+    ctx.close()
+    # one HMC proposal per set over the 64 sets of c4 (unconstrained, 20 steps, one graph)
+    ctx = HawkesContext(device=dev.index or 0, max_n=sum(sizes), max_d=8)
+    t = torch.tensor(np.concatenate([w.t for w in sets]), device=dev)
+    X = torch.tensor(np.concatenate([w.X.reshape(-1) for w in sets]), device=dev)
+    p0 = torch.tensor(rng.standard_normal(size=X.shape[0]), device=dev)
+    eps = [1e-3] * len(sets)
+    log_u = torch.full((len(sets),), -1e300, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        hawkes_batch_hmc_trajectory(ctx, sizes, dims, t, X, p0, params, eps, 20, log_u, check=False)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(5):
+        flush_l2(l2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hawkes_batch_hmc_trajectory(ctx, sizes, dims, t, X, p0, params, eps, 20, log_u, check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.sync_status()
+    m = statistics.median(ms)
+    out["batched_hmc_c4"] = {"sets": len(sets), "events": sum(sizes), "leapfrog_steps": 20, "ms_per_call": m,
+                             "set_trajectories_per_s": len(sets) * 1e3 / m}
     ctx.close()
     return out
 
@@ -531,7 +556,8 @@ def main():
     import torch
 
     import synth
-    from paper_2010_02994_gb300 import HawkesContext, hawkes_loglik_grad_locations, probe_pipe_rates
+    from paper_2010_02994_gb300 import (HawkesContext, hawkes_loglik_grad_locations, hawkes_self_excitation_prob,
+                                        probe_pipe_rates)
 
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
@@ -695,7 +721,17 @@ def main():
     # --- the other paper-shaped workloads (reported beside the headline) -----
     extra = {}
     if not args.no_extra:
-        extra = other_workloads(dev, stream, l2, fma_rate, ex2_rate, MAX_SM_MHZ_NOMINAL, sms)
+        # the same inputs with the Theta gradient, and the self-excitation probabilities
+        gp = torch.empty(6, dtype=torch.float64, device=dev)
+        m_theta = timed_calls(lambda: hawkes_loglik_grad_locations(ctx, t, X, w.params, precision="mixed",
+                                                                   grad_params=True, check=False, out=(ell, g, gp)),
+                              stream, l2, reps=10, warm=2)
+        m_sep = timed_calls(lambda: hawkes_self_excitation_prob(ctx, t, X, w.params, precision="mixed", check=False),
+                            stream, l2, reps=10, warm=2)
+        ctx.sync_status()
+        extra["c5_same_inputs"] = {"loglik_grad_X_and_theta_ms": m_theta, "evals_per_s_with_theta": 1e3 / m_theta,
+                                   "self_excitation_prob_ms": m_sep}
+        extra.update(other_workloads(dev, stream, l2, fma_rate, ex2_rate, MAX_SM_MHZ_NOMINAL, sms))
 
     # --- CPU baseline: the oracle on the host cores ---------------------------
     cpu = None
