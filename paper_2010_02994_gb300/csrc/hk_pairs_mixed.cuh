@@ -154,7 +154,9 @@ __device__ __forceinline__ void chunk_steps(const float4 *__restrict__ pv, int s
                                             float (&acc)[KindTraits<KIND, D>::VC])
 {
     using T = KindTraits<KIND, D>;
-#pragma unroll(MASKED ? 1 : 8)
+    // unrolled by 16: 1% shorter than 8 for the gradient pass at N = 1e5 on
+    // GB300 (4 and 32 are slower; the arithmetic and its order are unchanged)
+#pragma unroll(MASKED ? 1 : 16)
     for (int j = 0; j < 32; ++j) {
         float cf[4 * T::NPP];
 #pragma unroll
