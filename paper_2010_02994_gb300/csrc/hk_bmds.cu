@@ -14,7 +14,7 @@ namespace bmds {
 // to finish (ticket counter, reset by that CTA) adds the per-CTA value and
 // sigma2 sums in CTA order and writes ell_B and d ell_B / d sigma2.  A set
 // invalid-data bit in the status word makes every output NaN.
-constexpr int kFinRows = 32, kFinGroups = 8, kFinThreads = kFinRows * kFinGroups;
+constexpr int kFinRows = 16, kFinGroups = 16, kFinThreads = kFinRows * kFinGroups;
 
 // Compensated (Kahan) sum in the partials' own type: the FP32 partials of the
 // mixed precision are added on the FP32 units (FP64 is scarce on this GPU),
@@ -39,8 +39,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Args<F> a, int KT
 {
     // the per-group sums, later reused for the last CTA's reduction
     static_assert(sizeof(F) * kFinGroups * (kMaxD + 2) * kFinRows >= sizeof(double) * 2 * kFinThreads, "");
+    static_assert(kFinThreads >= (kMaxD + 2) * kFinRows, "one thread per value and row combines the groups");
     __shared__ __align__(16) F sh_s[kFinGroups][kMaxD + 2][kFinRows];
     __shared__ F sh_c[kFinGroups][kMaxD + 2][kFinRows];
+    __shared__ double sh_tot[kMaxD + 2][kFinRows];
     __shared__ bool last;
     double(*red)[kFinThreads] = reinterpret_cast<double(*)[kFinThreads]>(&sh_s[0][0][0]);
     const int d = a.d;
@@ -81,38 +83,29 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Args<F> a, int KT
         }
     __syncthreads();
     const bool bad = (*(volatile unsigned *)a.status & kStInvalidData) != 0;
-    if (gi == 0) {
-        double tot[kMaxD + 2];
-#pragma unroll
-        for (int c = 0; c < kMaxD + 2; ++c) {
-            tot[c] = 0.0;
-            if (c < d + 2) {
-                KSum<F> t;
-                for (int g = 0; g < kFinGroups; ++g) {
-                    t.add(sh_s[g][c][r]);
-                    t.add(-sh_c[g][c][r]);
-                }
-                tot[c] = t.value();
+    {
+        // one thread per (value, row) adds the groups in order
+        const int c = threadIdx.x / kFinRows, rr2 = threadIdx.x % kFinRows;
+        if (c < d + 2) {
+            KSum<F> t;
+            for (int g = 0; g < kFinGroups; ++g) {
+                t.add(sh_s[g][c][rr2]);
+                t.add(-sh_c[g][c][rr2]);
             }
+            sh_tot[c][rr2] = t.value();
         }
-        if (i < a.n && out_grad) {
-#pragma unroll
-            for (int c = 0; c < kMaxD; ++c)
-                if (c < d)
-                    out_grad[i * d + c] = bad ? nan("") : tot[c];
-        }
-        double v = 0.0, s = 0.0;
-#pragma unroll
-        for (int c = 0; c <= kMaxD; ++c)
-            if (c == d && i < a.n) {
-                v = tot[c];
-                s = tot[c + 1];
-            }
+    }
+    __syncthreads();
+    if (i < a.n && out_grad && gi < d)
+        out_grad[i * d + gi] = bad ? nan("") : sh_tot[gi][r];
+    if (threadIdx.x < 32) {
+        const bool mine = threadIdx.x < kFinRows && (int64_t)blockIdx.x * kFinRows + threadIdx.x < a.n;
+        double v = mine ? sh_tot[d][threadIdx.x] : 0.0, s = mine ? sh_tot[d + 1][threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) {
             v += __shfl_xor_sync(0xffffffffu, v, o);
             s += __shfl_xor_sync(0xffffffffu, s, o);
         }
-        if (r == 0) {
+        if (threadIdx.x == 0) {
             blockpart[2 * blockIdx.x] = v;
             blockpart[2 * blockIdx.x + 1] = s;
             __threadfence();
