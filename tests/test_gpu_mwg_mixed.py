@@ -269,3 +269,30 @@ def test_mixed_invalid_and_out_of_range():
     assert abs(s2.delta(idx, Xn).item() - ref) <= 1e-11 * float(np.sum(np.abs(np.log(lam2[live]))))
     s.close()
     s2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_largest_block_in_eight_dimensions(prec):
+    """The largest block (256 events, D = 8: the most staged shared memory)
+    in both precisions, against the oracle."""
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesMwG
+
+    w = synth.random_case(51, 900, 8, ties=2, shuffle=True)
+    s = HawkesMwG(torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"), w.params, max_block=256,
+                  precision=prec)
+    rng = np.random.default_rng(51)
+    idx = rng.choice(w.n, size=256, replace=False)
+    Xn = w.X[idx] + 0.2 * rng.standard_normal(size=(256, w.d))
+    X1 = w.X.copy()
+    X1[idx] = Xn
+    ref = oracle.loglik(w.t, X1, w.params) - oracle.loglik(w.t, w.X, w.params)
+    got = s.delta(idx, Xn).item()
+    if prec == "fp64":
+        lam = oracle.rates(w.t, w.X, w.params)
+        sc = float(np.sum(np.abs(np.log(lam))) + oracle.Lambda(w.t, w.params))
+        assert abs(got - ref) <= 1e-11 * sc
+    else:
+        assert abs(got - ref) <= bound(w, w.X, idx, Xn)
+    s.close()
