@@ -521,17 +521,14 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
                                 w.status, s),
            "validate");
     ctx->launches_own += 2;  // validate, pack
-    ctx->launches_lib += ctx->opt_sorted ? 0 : 1;
     ctx->launches_own += ctx->opt_sorted ? 1 : 0;
     if (ctx->opt_sorted) {
         HK_TRY(launch_identity_order(t, ctx->keys_b, ctx->vals_b, pl.n_total, ctx->d_set_ev0, ns, w.status, s),
                "order check");
     } else {
         HK_TRY(launch_sort(ctx->sort_temp, ctx->sort_bytes, t, ctx->keys_a, ctx->keys_b, ctx->vals_a, ctx->vals_b,
-                           pl.n_total, ns, ctx->d_set_ev0, s, &ctx->launches_own),
+                           pl.n_total, ns, ctx->d_set_ev0, s, &ctx->launches_own, &ctx->launches_lib),
                "time sort");
-        if (ns > 1)
-            ctx->launches_lib += 1;  // the second library sort of a batch
     }
     HK_TRY(launch_pack_rows(w, X, ctx->keys_b, ctx->vals_b, pl.total_rows, ctx->d_set_row0, s), "pack");
     if (ctx->opt_profile)

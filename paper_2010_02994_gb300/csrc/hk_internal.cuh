@@ -121,7 +121,7 @@ cudaError_t launch_validate_keys(const double *t, const double *X, int64_t n_tot
 size_t sort_temp_bytes(int64_t n_total, int32_t nsets);
 cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *t, double *keys_in, double *keys_out,
                         int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
-                        const int64_t *d_set_ev0, cudaStream_t s, int64_t *launches);
+                        const int64_t *d_set_ev0, cudaStream_t s, int64_t *launches, int64_t *lib_launches);
 cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *vals_out, int64_t n_total,
                                   const int64_t *set_ev0, int32_t nsets, unsigned *status, cudaStream_t s);
 cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,

@@ -9,6 +9,7 @@
 // full relative accuracy in FP32.
 #include <cub/cub.cuh>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hk_internal.cuh"
@@ -205,6 +206,73 @@ cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *va
 // a handful of full-width passes instead of one small sort per set.
 namespace {
 
+// Sort of one set of at most kCountSortMax events by rank counting (about
+// ten instructions per comparison, N^2 comparisons spread over every SM).  The key
+// of an event is the bit pattern of its time with the sign cleared: times are
+// validated non-negative, non-negative doubles order like their bit patterns,
+// and -0 then equals +0.  Event i's rank is the number of events j with
+// key_j < key_i, or key_j == key_i and j < i (the caller's order among equal
+// times, as a stable sort keeps it).  Each thread counts for kCountPer events
+// over one slice of the keys, staged in shared memory; the slices' counts
+// are added with integer atomics, exact in any order.
+constexpr int kCountSortMax = 8192;  // N^2 comparisons: beyond this the radix sort is faster on GB300
+constexpr int kCountThreads = 256, kCountPer = 4, kCountPerCta = kCountThreads * kCountPer;
+constexpr int kCountTile = 1024, kCountSplitsMax = 64, kCountCtas = 608;  // 4 CTAs per SM
+
+__device__ __forceinline__ unsigned long long time_key(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+__global__ void __launch_bounds__(kCountThreads) count_rank_kernel(const double *__restrict__ keys, int n, int splits,
+                                                                   int32_t *rank)
+{
+    __shared__ unsigned long long sk[kCountTile];
+    int idx[kCountPer];
+    unsigned long long key[kCountPer];
+    int cnt[kCountPer];
+#pragma unroll
+    for (int k = 0; k < kCountPer; ++k) {
+        idx[k] = blockIdx.x * kCountPerCta + k * kCountThreads + threadIdx.x;
+        key[k] = idx[k] < n ? time_key(keys[idx[k]]) : 0ull;
+        cnt[k] = 0;
+    }
+    const int per = (n + splits - 1) / splits;
+    const int lo = min((int)blockIdx.y * per, n), hi = min(lo + per, n);
+    for (int j0 = lo; j0 < hi; j0 += kCountTile) {
+        const int m = min(kCountTile, hi - j0);
+        __syncthreads();
+        for (int u = threadIdx.x; u < m; u += kCountThreads)
+            sk[u] = time_key(keys[j0 + u]);
+        __syncthreads();
+        for (int u = 0; u < m; ++u) {
+            const unsigned long long kj = sk[u];
+            const int j = j0 + u;
+#pragma unroll
+            for (int k = 0; k < kCountPer; ++k)
+                cnt[k] += (kj < key[k] || (kj == key[k] && j < idx[k])) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCountPer; ++k)
+        if (idx[k] < n && cnt[k])
+            atomicAdd(rank + idx[k], cnt[k]);
+}
+
+__global__ void scatter_rank_kernel(const double *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
+                                    const int32_t *__restrict__ rank, int n, double *keys_out, int32_t *vals_out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = rank[i];
+        keys_out[r] = __longlong_as_double((long long)time_key(keys_in[i]));
+        vals_out[r] = vals_in[i];
+    }
+}
+
+}  // namespace
+
+namespace {
+
 int set_bits(int32_t nsets)
 {
     int b = 1;
@@ -254,15 +322,31 @@ size_t sort_temp_bytes(int64_t n_total, int32_t nsets)
 
 cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *t, double *keys_in, double *keys_out,
                         int32_t *vals_in, int32_t *vals_out, int64_t n_total, int32_t nsets,
-                        const int64_t *d_set_ev0, cudaStream_t s, int64_t *launches)
+                        const int64_t *d_set_ev0, cudaStream_t s, int64_t *launches, int64_t *lib_launches)
 {
-    // Radix sort is stable: events with equal times keep the caller's order.
-    if (nsets <= 1) {
+    // Both sorts are stable: events with equal times keep the caller's order.
+    if (nsets <= 1 && n_total <= kCountSortMax && temp_bytes >= sizeof(int32_t) * (size_t)n_total) {
+        // one set of at most 8192 events: ranks by counting, which takes a
+        // few microseconds where the eight radix passes take tens
+        int32_t *rank = static_cast<int32_t *>(temp);
+        cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int32_t) * n_total, s);
+        if (e != cudaSuccess)
+            return e;
+        const int n = (int)n_total;
+        const int gx = (n + kCountPerCta - 1) / kCountPerCta;
+        const int splits = std::max(1, std::min({kCountSplitsMax, kCountCtas / gx, n / 64}));
+        const dim3 grid((unsigned)gx, (unsigned)splits);
+        count_rank_kernel<<<grid, kCountThreads, 0, s>>>(keys_in, n, splits, rank);
+        scatter_rank_kernel<<<grid_for(n_total, 256), 256, 0, s>>>(keys_in, vals_in, rank, n, keys_out, vals_out);
         if (launches)
-            *launches += 0;
+            *launches += 2;
+        return cudaGetLastError();
+    }
+    if (lib_launches)
+        *lib_launches += nsets <= 1 ? 1 : 2;
+    if (nsets <= 1)
         return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out, (int)n_total,
                                                0, 64, s);
-    }
     const int g = grid_for(n_total, 256);
     iota_kernel<<<g, 256, 0, s>>>(vals_in, n_total);
     cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys_in, keys_out, vals_in, vals_out,
