@@ -209,6 +209,8 @@ void describe_set(SetDesc &S, int64_t n, int d, const hawkes_params &p, double f
     S.kx = k0 / p.tau_x;
     S.kt = k0 / p.tau_t;
     S.Pmu = p.mu0 / (std::pow(p.tau_x, d) * p.tau_t * std::pow(kTwoPi, 0.5 * (d + 1)));
+    S.iPmu = 1.0 / S.Pmu;
+    S.lPmu = std::log(S.Pmu);
     S.Cg = 1.0 / (p.tau_x * p.tau_x * S.kx);
     const double rho = (p.tau_x * p.tau_x) / (p.h * p.h);
     const double cxi1 = std::log2(p.theta * p.omega * std::pow(p.tau_x, d) * p.tau_t * std::sqrt(kTwoPi) /

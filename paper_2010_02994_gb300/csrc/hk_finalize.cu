@@ -169,6 +169,8 @@ struct PairFp64 {
 
 // ------------------------------------------------------ finalize rows --
 
+constexpr double kLog2e = 1.4426950408889634074;
+
 __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int theta)
 {
     __shared__ double sh[kT];
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
     double lnl_v = 0.0;
     if (active) {
         const int64_t r = S.row0 + i;
-        double lam;
+        double lam, inv_sum = 0.0, log_sum = 0.0;
         if (fp64) {
             const int V = theta ? kPass1ThetaVals : 1;
             Nsum acc;
@@ -210,8 +212,12 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             const double sum = v[0] + v[1];
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
-            w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
-            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log2(sum));
+            if (!flagged) {
+                inv_sum = 1.0 / sum;
+                log_sum = log(sum);
+            }
+            w.w32[r] = flagged ? 0.0f : (float)inv_sum;
+            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log_sum * kLog2e);
             // natural units: sum mu, sum xi, sum mu r^2, sum mu dt^2, sum xi dt, sum xi r^2
             const double ikx2 = 1.0 / (S.kx * S.kx), ikt = 1.0 / S.kt;
             double *T = w.theta_rows + r * kPass1ThetaVals;
@@ -225,13 +231,19 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             const double sum = ordered_strided_sum(w.P1 + S.part0 + i, S.nblk, S.npad);
             flagged = !(sum >= S.s_min);
             lam = S.Pmu * sum;
-            w.w32[r] = flagged ? 0.0f : (float)(1.0 / sum);
-            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log2(sum));
+            if (!flagged) {
+                inv_sum = 1.0 / sum;
+                log_sum = log(sum);
+            }
+            w.w32[r] = flagged ? 0.0f : (float)inv_sum;
+            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log_sum * kLog2e);
         }
         if (!flagged) {
+            // one FP64 division and one log per row (FP64 is a long-latency
+            // path on this GPU): 1/lambda = (1/S) (1/Pmu), log lambda = log Pmu + log S
             w.lam64[r] = lam;
-            w.w64[r] = 1.0 / lam;
-            lnl_v = log(lam) - w.Lam64[r];
+            w.w64[r] = fp64 ? 1.0 / lam : inv_sum * S.iPmu;
+            lnl_v = (fp64 ? log(lam) : S.lPmu + log_sum) - w.Lam64[r];
             w.lnl[r] = lnl_v;
             if (!(lam > 0.0))
                 atomicOr(&w.set_flags[s], 1);

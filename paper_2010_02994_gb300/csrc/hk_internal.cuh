@@ -69,6 +69,7 @@ struct SetDesc {
     // FP64 constants
     double kx, kt;    // coordinate scalings sqrt(log2(e)/2)/tau_x and /tau_t
     double Pmu;       // mu0 / (tau_x^D tau_t (2 pi)^((D+1)/2))
+    double iPmu, lPmu;  // 1 / Pmu and log(Pmu), so a row needs one division and one log
     double Cg;        // 1 / (tau_x^2 kx): scaled pass-2 sums -> d ell / d x
     double s_min;     // rows with S_n < s_min are recomputed in FP64
     double mu0, tau_x, tau_t, theta, omega, h;

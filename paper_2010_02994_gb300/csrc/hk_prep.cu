@@ -369,7 +369,9 @@ cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *t, double *
 cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
                              int64_t total_rows, const int64_t *set_row0, cudaStream_t s)
 {
-    pack_kernel<<<grid_for(total_rows, 256), 256, 0, s>>>(w, X, keys_sorted, vals_sorted, total_rows, set_row0);
+    // 64-thread CTAs: the FP64 work per row (Lambda, the hi/lo splits) spreads
+    // over four times as many SMs at the sizes of the paper's data sets
+    pack_kernel<<<grid_for(total_rows, 64), 64, 0, s>>>(w, X, keys_sorted, vals_sorted, total_rows, set_row0);
     return cudaGetLastError();
 }
 
