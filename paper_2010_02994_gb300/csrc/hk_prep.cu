@@ -215,7 +215,7 @@ namespace {
 // times, as a stable sort keeps it).  Each thread counts for kCountPer events
 // over one slice of the keys, staged in shared memory; the slices' counts
 // are added with integer atomics, exact in any order.
-constexpr int kCountSortMax = 8192;  // N^2 comparisons: beyond this the radix sort is faster on GB300
+constexpr int kCountSortMax = 12288;  // N^2 comparisons: beyond this the radix sort is faster on GB300
 constexpr int kCountThreads = 256, kCountPer = 4, kCountPerCta = kCountThreads * kCountPer;
 constexpr int kCountTile = 1024, kCountSplitsMax = 64, kCountCtas = 608;  // 4 CTAs per SM
 
@@ -326,7 +326,7 @@ cudaError_t launch_sort(void *temp, size_t temp_bytes, const double *t, double *
 {
     // Both sorts are stable: events with equal times keep the caller's order.
     if (nsets <= 1 && n_total <= kCountSortMax && temp_bytes >= sizeof(int32_t) * (size_t)n_total) {
-        // one set of at most 8192 events: ranks by counting, which takes a
+        // one set of at most 12288 events: ranks by counting, which takes a
         // few microseconds where the eight radix passes take tens
         int32_t *rank = static_cast<int32_t *>(temp);
         cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int32_t) * n_total, s);
