@@ -322,6 +322,44 @@ def mwg_workload(dev, stream, l2) -> dict:
                               "pair_terms_per_iteration": 3 * nb * w.n, "pair_term_precision": prec,
                               "accepted_last_replay": acc}
         s.close()
+    # wildfire-like (c3: N = 5,000, circle priors of Eq. (3)): lens proposals of Eq. (6), 4 tries
+    wc = synth.make_c3()
+    centers_np, radii_np = synth.circle_priors(wc)
+    tc, Xc = torch.tensor(wc.t, device=dev), torch.tensor(wc.X, device=dev)
+    centers, radii = torch.tensor(centers_np, device=dev), torch.tensor(radii_np, device=dev)
+    for nb, prec in ((1, "fp64"), (32, "fp64"), (1, "mixed"), (32, "mixed")):
+        s = HawkesMwG(tc, Xc, wc.params, max_block=nb, precision=prec)
+        idx = torch.stack([torch.randperm(wc.n, generator=gen, device=dev)[:nb] for _ in range(iters)])
+        u = torch.rand((iters, nb, 4, 2), generator=gen, device=dev, dtype=torch.float64)
+        log_u = torch.log(torch.rand(iters, generator=gen, device=dev, dtype=torch.float64))
+        props = [(torch.empty((nb, 2), dtype=torch.float64, device=dev),
+                  torch.empty((), dtype=torch.float64, device=dev)) for _ in range(iters)]
+        outs = [(torch.empty((), dtype=torch.float64, device=dev), torch.empty((), dtype=torch.int32, device=dev))
+                for _ in range(iters)]
+
+        def run_c():
+            for k in range(iters):
+                s.propose_circle(idx[k], centers, radii, 0.5, 4, u[k], out=props[k], check=False)
+                s.step(idx[k], props[k][0], log_u[k], props[k][1], out=outs[k], check=False)
+
+        run_c()
+        torch.cuda.synchronize()
+        s.sync_status()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                run_c()
+        torch.cuda.synchronize()
+        m = timed_calls(g.replay, stream, l2, reps=10, warm=2)
+        s.sync_status()
+        per = m / iters
+        res[f"circle_block_{nb}" + ("" if prec == "fp64" else "_mixed")] = {
+            "workload": "c3_wildfire_like_n5000_d2_circles", "ms_per_iteration": per,
+            "iterations_per_s": 1e3 / per, "location_updates_per_s": nb * 1e3 / per, "pair_term_precision": prec,
+            "accepted_last_replay": int(sum(o[1].item() for o in outs))}
+        s.close()
     # the same proposal evaluated by a full log-likelihood instead (what the increments avoid)
     ctx = HawkesContext(device=dev.index or 0, max_n=w.n, max_d=w.d)
     full = timed_calls(lambda: hawkes_loglik(ctx, t, X, w.params, "fp64", check=False), stream, l2, reps=5, warm=1)

@@ -671,24 +671,6 @@ __device__ double x_minus_sin(double x)
     return sum;
 }
 
-// Area of the intersection of discs of radii R and rho, centres c apart:
-// the two circular segments cut off by the common chord, each
-// r^2 (2 theta - sin 2 theta) / 2 with theta = atan2(half-chord, signed
-// distance of the chord from the centre).
-__device__ double lens_area(double R, double rho, double c)
-{
-    if (c >= R + rho)
-        return 0.0;
-    if (c <= fabs(R - rho)) {
-        const double m = fmin(R, rho);
-        return CUDART_PI * m * m;
-    }
-    const double d1 = (c * c + R * R - rho * rho) / (2.0 * c);
-    const double d2 = c - d1;
-    const double h = sqrt(fmax((R - d1) * (R + d1), 0.0));
-    return 0.5 * R * R * x_minus_sin(2.0 * atan2(h, d1)) + 0.5 * rho * rho * x_minus_sin(2.0 * atan2(h, d2));
-}
-
 // log P(at least one of `tries` uniform draws from a disc of radius rho
 // lands in a region of area A inside it)
 __device__ double log_success(double A, double rho, int tries)
@@ -697,8 +679,34 @@ __device__ double log_success(double A, double rho, int tries)
     return p >= 1.0 ? 0.0 : log(-expm1((double)tries * log1p(-p)));
 }
 
-// Lens proposals of Eq. (6) for a D = 2 block, one thread per moved event;
-// the block's log q-ratio is summed in a fixed order.
+// The area of the intersection of discs of radii R and rho, centres c apart,
+// is the sum of the two circular segments cut off by the common chord, each
+// r^2 (2 theta - sin 2 theta) / 2 with theta = atan2(half-chord, signed
+// distance of the chord from the centre).  lens_part returns one of them
+// (which = 0: the prior circle's, 1: the disc's), so that two lanes evaluate
+// a lens together; in the cases without a chord (no overlap, one disc inside
+// the other) lane 0 carries the whole area.
+__device__ double lens_part(double R, double rho, double c, int which)
+{
+    if (c >= R + rho)
+        return 0.0;
+    if (c <= fabs(R - rho)) {
+        const double m = fmin(R, rho);
+        return which == 0 ? CUDART_PI * m * m : 0.0;
+    }
+    const double d1 = (c * c + R * R - rho * rho) / (2.0 * c);
+    const double d2 = c - d1;
+    const double h = sqrt(fmax((R - d1) * (R + d1), 0.0));
+    return which == 0 ? 0.5 * R * R * x_minus_sin(2.0 * atan2(h, d1))
+                      : 0.5 * rho * rho * x_minus_sin(2.0 * atan2(h, d2));
+}
+
+// Lens proposals of Eq. (6) for a D = 2 block, four lanes per moved event:
+// the two segments of each lens area on alternate lanes, the rejection tries
+// four at a time (the first try inside the circle wins, as in a serial loop),
+// and the four logs of the ratio side by side.  FP64 is a long-latency path
+// on this GPU and these chains are most of a small block's step.  The
+// block's log q-ratio is summed in a fixed order.
 template <int NT>
 __global__ void __launch_bounds__(NT) propose_circle_kernel(const double *__restrict__ X, int64_t n, Block B,
                                                             const double *__restrict__ centers,
@@ -706,38 +714,77 @@ __global__ void __launch_bounds__(NT) propose_circle_kernel(const double *__rest
                                                             const double *__restrict__ u, double *X_new,
                                                             double *log_q_ratio, int *status)
 {
+    constexpr int G = 4;  // lanes per event
     __shared__ double sh[NT / 32];
+    const int g = threadIdx.x & (G - 1), lane = threadIdx.x & 31;
+    const unsigned gmask = 0xfu << (lane & ~(G - 1));
     double lq = 0.0;
-    for (int b = threadIdx.x; b < B.nb; b += NT) {
-        const int64_t m = B.idx[b];
-        if (m < 0 || m >= n) {
-            atomicOr(status, kBadBlock);
-            continue;
-        }
-        const double x0 = X[m * 2], x1 = X[m * 2 + 1], c0 = centers[m * 2], c1 = centers[m * 2 + 1];
-        const double R = radii[m], rho = R * eps;
-        const double A_x = lens_area(R, rho, hypot(x0 - c0, x1 - c1));
-        if (!(R > 0.0) || !isfinite(R) || !(A_x > 0.0)) {
-            atomicOr(status, kBadProposal);
-            continue;
-        }
-        double y0 = x0, y1 = x1;
-        for (int k = 0; k < tries; ++k) {
-            const double r = rho * sqrt(u[((int64_t)b * tries + k) * 2]);
-            double sn, cs;
-            sincospi(2.0 * u[((int64_t)b * tries + k) * 2 + 1], &sn, &cs);
-            const double z0 = x0 + r * cs, z1 = x1 + r * sn;
-            const double dx = z0 - c0, dy = z1 - c1;
-            if (dx * dx + dy * dy < R * R) {
-                y0 = z0;
-                y1 = z1;
-                const double A_y = lens_area(R, rho, hypot(dx, dy));
-                lq += (log_success(A_y, rho, tries) - log(A_y)) - (log_success(A_x, rho, tries) - log(A_x));
-                break;
+    const int total = B.nb * G;
+    for (int base = 0; base < total; base += NT) {  // uniform trip counts: every lane takes part in the shuffles
+        const int e = (base + (int)threadIdx.x) / G;
+        bool ok = false;
+        double x0 = 0.0, x1 = 0.0, c0 = 0.0, c1 = 0.0, R = 0.0, rho = 0.0;
+        if (e < B.nb) {
+            const int64_t m = B.idx[e];
+            if (m < 0 || m >= n) {
+                if (g == 0)
+                    atomicOr(status, kBadBlock);
+            } else {
+                x0 = X[m * 2];
+                x1 = X[m * 2 + 1];
+                c0 = centers[m * 2];
+                c1 = centers[m * 2 + 1];
+                R = radii[m];
+                rho = R * eps;
+                ok = true;
             }
         }
-        X_new[(int64_t)b * 2] = y0;
-        X_new[(int64_t)b * 2 + 1] = y1;
+        double part = ok ? lens_part(R, rho, hypot(x0 - c0, x1 - c1), g & 1) : 0.0;
+        const double A_x = part + __shfl_xor_sync(0xffffffffu, part, 1);
+        if (ok && (!(R > 0.0) || !isfinite(R) || !(A_x > 0.0))) {
+            if (g == 0)
+                atomicOr(status, kBadProposal);
+            ok = false;
+        }
+        double y0 = x0, y1 = x1;
+        bool moved = false;
+        for (int k0 = 0; k0 < tries; k0 += G) {
+            const int k = k0 + g;
+            bool inside = false;
+            double z0 = 0.0, z1 = 0.0;
+            if (ok && !moved && k < tries) {
+                const double r = rho * sqrt(u[((int64_t)e * tries + k) * 2]);
+                double sn, cs;
+                sincospi(2.0 * u[((int64_t)e * tries + k) * 2 + 1], &sn, &cs);
+                z0 = x0 + r * cs;
+                z1 = x1 + r * sn;
+                const double dx = z0 - c0, dy = z1 - c1;
+                inside = dx * dx + dy * dy < R * R;
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, inside) & gmask;
+            const int src = hit ? __ffs(hit) - 1 : lane;
+            const double w0 = __shfl_sync(0xffffffffu, z0, src), w1 = __shfl_sync(0xffffffffu, z1, src);
+            if (hit && !moved) {
+                y0 = w0;
+                y1 = w1;
+                moved = true;
+            }
+        }
+        part = moved ? lens_part(R, rho, hypot(y0 - c0, y1 - c1), g & 1) : 0.0;
+        const double A_y = part + __shfl_xor_sync(0xffffffffu, part, 1);
+        // lanes 0..3: log P(x*), log A(x*), log P(x), log A(x)
+        double L = 0.0;
+        if (moved)
+            L = g == 0 ? log_success(A_y, rho, tries) : g == 1 ? log(A_y) : g == 2 ? log_success(A_x, rho, tries)
+                                                                                  : log(A_x);
+        const double L1 = __shfl_down_sync(0xffffffffu, L, 1), L2 = __shfl_down_sync(0xffffffffu, L, 2),
+                     L3 = __shfl_down_sync(0xffffffffu, L, 3);
+        if (ok && g == 0) {
+            if (moved)
+                lq += (L - L1) - (L2 - L3);
+            X_new[(int64_t)e * 2] = y0;
+            X_new[(int64_t)e * 2 + 1] = y1;
+        }
     }
     lq = cta_sum<NT>(lq, sh);
     if (threadIdx.x == 0)
@@ -1147,7 +1194,7 @@ hawkes_status hawkes_mwg_propose_circle(hawkes_mwg *s, int32_t nb, const int64_t
     MWG_TRY(cudaSetDevice(s->device), "cudaSetDevice");
     const Block B{nb, idx, nullptr};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (nb <= 32)  // one warp: no cross-warp step in the q-ratio sum
+    if (4 * nb <= 32)  // one warp: no cross-warp step in the q-ratio sum
         propose_circle_kernel<32><<<1, 32, 0, st>>>(s->X, s->n, B, centers, radii, eps, tries, u, X_new, log_q_ratio,
                                                     s->ctl + 1);
     else

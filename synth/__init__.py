@@ -157,6 +157,21 @@ def make_c3(seed: int = 2, n: int = 5000) -> Workload:
                     {"square_km": 200.0, "days": 3650.0, "seed": seed})
 
 
+def circle_priors(w: Workload, seed: int = 7) -> tuple[np.ndarray, np.ndarray]:
+    """Circle priors of Eq. (3) for the events of w, drawn as the wildfire
+    data present them: radii (km, from the fire size at discovery) of 0.05,
+    0.5 or 5 with probabilities 0.5, 0.3, 0.2, and each event's latent
+    location uniform inside its circle (so the centre is the observed point).
+    Returns (centers (N, 2), radii (N,))."""
+    rng = np.random.default_rng(seed)
+    n = w.n
+    radii = rng.choice(np.array([0.05, 0.5, 5.0]), size=n, p=[0.5, 0.3, 0.2])
+    ang = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    rr = radii * np.sqrt(rng.uniform(size=n)) * 0.999
+    centers = w.X - np.stack([rr * np.cos(ang), rr * np.sin(ang)], axis=1)
+    return centers, radii
+
+
 def make_c4(seed: int = 3, n_sets: int = 64, n_min: int = 500, n_max: int = 20_000) -> list:
     """Batched latent-space sets: N log-uniform in [500, 20,000], D uniform in
     {2, 4, 8}, background N(0, I_D) over 365 days; m=0.5, omega=1/day,
