@@ -617,12 +617,6 @@ __global__ void self_excitation_kernel(Work w, double *out)
     out[S.ev0 + w.perm[r]] = lam > 0.0 ? w.theta_rows[r * kPass1ThetaVals + 1] / lam : nan("");
 }
 
-__global__ void fill_nan_kernel(double *p, int64_t n)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = nan("");
-}
-
 }  // namespace
 
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s)
@@ -663,17 +657,6 @@ cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream
 cudaError_t launch_self_excitation(const Work &w, int32_t total_segs, double *out, cudaStream_t s)
 {
     self_excitation_kernel<<<total_segs, kT, 0, s>>>(w, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill_nan(double *p, int64_t n, cudaStream_t s)
-{
-    if (n <= 0)
-        return cudaSuccess;
-    int grid = (int)((n + 255) / 256);
-    if (grid > 1024)
-        grid = 1024;
-    fill_nan_kernel<<<grid, 256, 0, s>>>(p, n);
     return cudaGetLastError();
 }
 

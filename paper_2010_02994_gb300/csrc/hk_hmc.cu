@@ -235,8 +235,6 @@ __global__ void add_caller_term_kernel(Work w, const int64_t *set_row0, const do
     }
 }
 
-__global__ void set_scalar_kernel(double *dst, double v) { *dst = v; }
-
 // Element-wise HMC kernels run 64-thread CTAs: their FP64 updates are few
 // per row, and small CTAs spread them over every SM (FP64 is 1/64 of the
 // FP32 rate on this GPU).
@@ -309,12 +307,6 @@ cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const
                                    int64_t total_rows, const double *ell_add, cudaStream_t s)
 {
     add_caller_term_kernel<<<grid_for(total_rows), kElemThreads, 0, s>>>(w, set_row0, g, g_sorted, total_rows, ell_add);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s)
-{
-    set_scalar_kernel<<<1, 1, 0, s>>>(dst, value);
     return cudaGetLastError();
 }
 

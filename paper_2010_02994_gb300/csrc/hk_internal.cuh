@@ -127,7 +127,6 @@ cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *va
                                   const int64_t *set_ev0, int32_t nsets, unsigned *status, cudaStream_t s);
 cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
                              int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
-cudaError_t launch_pack_x_rows(const Work &w, int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
 
 // hk_pairs_mixed_*.cu
 cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
@@ -156,7 +155,6 @@ cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, d
                                  cudaStream_t s);
 cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,
                               cudaStream_t s);
-cudaError_t launch_fill_nan(double *p, int64_t n, cudaStream_t s);
 cudaError_t launch_self_excitation(const Work &w, int32_t total_segs, double *out, cudaStream_t s);
 
 // hk_hmc.cu
@@ -173,7 +171,6 @@ cudaError_t launch_accept(const double *H0, const double *H1, const double *log_
                           int32_t *accepted, int nsets, cudaStream_t s);
 cudaError_t launch_scatter(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                            const int32_t *accepted, int64_t total_rows, cudaStream_t s);
-cudaError_t launch_set_scalar(double *dst, double value, cudaStream_t s);
 cudaError_t launch_to_caller(const Work &w, const int64_t *set_row0, const double *Xs, double *X_out,
                              int64_t total_rows, cudaStream_t s);
 cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const double *g, double *g_sorted,

@@ -140,36 +140,6 @@ __global__ void pack_kernel(Work w, const double *__restrict__ X, const double *
     }
 }
 
-// Re-pack the coordinate fields from x64 (HMC: the locations moved, the
-// times did not).
-__global__ void pack_x_kernel(Work w, int64_t total_rows, const int64_t *__restrict__ set_row0)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows; r += stride) {
-        const int s = find_set_by(set_row0, w.nsets, r);
-        const SetDesc &S = w.sets[s];
-        const int64_t i = r - S.row0;
-        if (i >= S.n)
-            continue;
-        const int d = S.d;
-        float f[2 * kMaxD];
-        for (int k = 0; k < d; ++k)
-            split_hilo(w.x64[r * kMaxD + k] * S.kx, f[2 * k], f[2 * k + 1]);
-        // rewrite the planes that hold coordinate fields, keeping th/tl
-        const int np = nrec(d);
-        for (int p = 0; p < np; ++p) {
-            float4 v = w.rec[S.rec0 + (int64_t)p * S.npad + i];
-            float *c = reinterpret_cast<float *>(&v);
-            for (int q = 0; q < 4; ++q) {
-                int fld = 4 * p + q;
-                if (fld < 2 * d)
-                    c[q] = f[fld];
-            }
-            w.rec[S.rec0 + (int64_t)p * S.npad + i] = v;
-        }
-    }
-}
-
 int grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -372,12 +342,6 @@ cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_
     // 64-thread CTAs: the FP64 work per row (Lambda, the hi/lo splits) spreads
     // over four times as many SMs at the sizes of the paper's data sets
     pack_kernel<<<grid_for(total_rows, 64), 64, 0, s>>>(w, X, keys_sorted, vals_sorted, total_rows, set_row0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pack_x_rows(const Work &w, int64_t total_rows, const int64_t *set_row0, cudaStream_t s)
-{
-    pack_x_kernel<<<grid_for(total_rows, 256), 256, 0, s>>>(w, total_rows, set_row0);
     return cudaGetLastError();
 }
 
