@@ -106,7 +106,7 @@ struct hawkes_ctx {
     HmcGraph hmc;
     cudaStream_t side[kMaxD + 1] = {};  // forked streams for concurrent per-dimension launches
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxD + 1] = {};
-    int occ[kMaxD + 1][4][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..3][warps]
+    int occ[kMaxD + 1][5][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..4][warps]
     static constexpr int kBuckets = 32;
     int tune_warps[kMaxD + 1][kBuckets] = {};  // 0: no entry
     int tune_ctas[kMaxD + 1][kBuckets] = {};
@@ -231,7 +231,7 @@ bool mixed_range_ok(const SetDesc &S)
 
 // Lay out the sets of one call and build the work list.
 hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t *ev_counts, const int32_t *dims,
-                         const hawkes_params *params, bool fp64, bool theta = false)
+                         const hawkes_params *params, bool fp64, bool theta = false, bool xi = false)
 {
     pl = Plan();
     pl.sets.resize(nsets);
@@ -271,7 +271,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         S.part2_0 = p2;
         S.fpart0 = f1;
         S.fpart2_0 = f2;
-        S.vpc = theta ? kPass1ThetaVals : kPass1Vals;
+        S.vpc = theta ? kPass1ThetaVals : (xi ? kPass1XiVals : kPass1Vals);
         S.seg0 = seg;
         S.nseg = (int32_t)((n + kFinalizeThreads - 1) / kFinalizeThreads);
         // FP64 kernels: enough column splits for about 8 CTAs per SM in total
@@ -285,7 +285,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         x += n * d;
         row += S.npad;
         rec4 += (int64_t)nrec(d) * S.npad;
-        p1 += (int64_t)S.nblk * S.npad * (theta ? kPass1ThetaVals : kPass1Vals);
+        p1 += (int64_t)S.nblk * S.npad * S.vpc;
         p2 += (int64_t)S.nblk * S.npad * d;
         f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
         f2 += (int64_t)S.fsplit * S.npad * d;
@@ -588,6 +588,8 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
             HK_TRY(launch_pass1_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
         else if (pass == 3)
             HK_TRY(launch_pass1_theta_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
+        else if (pass == 4)
+            HK_TRY(launch_pass1_xi_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
         else
             HK_TRY(launch_pass2_mixed(d, wd, items, rg.second, grid, warps, ls), "gradient pass");
         if (fork) {
@@ -615,7 +617,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         ctx->launches_own += want_grad ? 2 * ndims + 4 : ndims + 2;
     if (fp64) {
         HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
-        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, theta, s), "finalize rows");
+        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, theta ? kSumsTheta : kSumsNone, s), "finalize rows");
         HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, false, s), "log-likelihood");
         if (want_grad) {
             HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
@@ -640,7 +642,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     ProfEvent pf{};
     if (ctx->opt_profile)
         prof_begin(ctx, s, pf, 3, 0.0);
-    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, theta, s), "finalize rows");
+    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, theta ? kSumsTheta : kSumsNone, s), "finalize rows");
     HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, theta, s), "FP64 rate fixup");
     if (ctx->opt_profile)
         prof_end(ctx, s, pf);
@@ -763,8 +765,9 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
             for (int wv : {1, 2, 4, 8})
                 ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
     for (int d = 1; d <= kMaxD; ++d)
-        for (int wv : {1, 2, 4, 8})
-            ctx->occ[d][3][wv] = pass_max_ctas_per_sm(d, 3, wv);
+        for (int pass = 3; pass <= 4; ++pass)
+            for (int wv : {1, 2, 4, 8})
+                ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
     Plan pl;
     hawkes_params p{1, 1, 1, 1, 1, 1};
     const int64_t n64 = max_n;
@@ -990,24 +993,25 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = prec == HAWKES_PREC_FP64;
     Plan pl;
-    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64, true)) != HAWKES_OK)
+    // FP64: the rate pass with the parameter-gradient sums carries sum_n' xi_nn';
+    // mixed: a rate pass that keeps only that sum apart (two column planes)
+    if ((st = build_plan(ctx, pl, 1, &n, &d, params, fp64, fp64, !fp64)) != HAWKES_OK)
         return st;
     if ((st = bind_plan(ctx, pl, s)) != HAWKES_OK)
         return st;
     if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
         return st;
-    // the rate pass with the parameter-gradient sums carries sum_n' xi_nn'
-    const bool theta = true;
     const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
     if (fp64) {
-        HK_TRY(launch_pass1_fp64(ctx->w, 0, 1, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
-        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, theta, s), "finalize rows");
+        HK_TRY(launch_pass1_fp64(ctx->w, 0, 1, pl.max_fsplit, pl.max_ftiles, true, s), "FP64 rate pass");
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, kSumsTheta, s), "finalize rows");
         HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, 1, nullptr, false, s), "log-likelihood");
     } else {
-        if ((st = enqueue_pair_pass(ctx, pl, 3, s)) != HAWKES_OK)
+        if ((st = enqueue_pair_pass(ctx, pl, 4, s)) != HAWKES_OK)
             return st;
-        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, theta, s), "finalize rows");
-        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, fix_grid, nullptr, theta, s), "FP64 rate fixup");
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, kSumsXi, s), "finalize rows");
+        // flagged rows get all six sums in FP64, the self-excitation one among them
+        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, fix_grid, nullptr, true, s), "FP64 rate fixup");
     }
     HK_TRY(launch_self_excitation(ctx->w, pl.total_segs, out_prob, s), "self-excitation");
     ctx->launches_own += 4;

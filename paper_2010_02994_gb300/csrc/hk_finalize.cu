@@ -171,6 +171,7 @@ struct PairFp64 {
 
 constexpr double kLog2e = 1.4426950408889634074;
 
+// theta: which row sums the rate pass kept besides the rate (RateSums)
 __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int theta)
 {
     __shared__ double sh[kT];
@@ -205,6 +206,21 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             } else {
                 lam = acc.value();
             }
+        } else if (theta == kSumsXi) {
+            // background and self-excitation sums apart: the rate and sum_n' xi_nn'
+            double v[kPass1XiVals];
+            ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nblk, (int64_t)kPass1XiVals * S.npad,
+                                               v);
+            const double sum = v[0] + v[1];
+            flagged = !(sum >= S.s_min);
+            lam = S.Pmu * sum;
+            if (!flagged) {
+                inv_sum = 1.0 / sum;
+                log_sum = log(sum);
+            }
+            w.w32[r] = flagged ? 0.0f : (float)inv_sum;
+            w.cm32[r] = flagged ? -INFINITY : (float)(S.cxi2_d - log_sum * kLog2e);
+            w.theta_rows[r * kPass1ThetaVals + 1] = S.Pmu * v[1];
         } else if (theta) {
             double v[kMaxD];
             ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
@@ -619,9 +635,9 @@ __global__ void self_excitation_kernel(Work w, double *out)
 
 }  // namespace
 
-cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s)
+cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, cudaStream_t s)
 {
-    finalize_rows_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, theta ? 1 : 0);
+    finalize_rows_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, sums);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,10 @@ constexpr int kMaxD = 8;
 constexpr float kPadTime = 1.0e18f;  // its square stays finite in FP32
 constexpr int kPass1Vals = 1;       // S
 constexpr int kPass1ThetaVals = 6;  // M, Xi, sum mu' q, sum mu' dt^2, sum xi'' dt, sum xi'' q
+constexpr int kPass1XiVals = 2;     // M, Xi
+
+// What the rate pass keeps per row besides the rate.
+enum RateSums : int { kSumsNone = 0, kSumsTheta = 1, kSumsXi = 2 };
 constexpr int kFinalizeThreads = 128;  // rows per finalize segment (one CTA each)
 constexpr int kMaxThetaSets = 1;
 constexpr int kThetaParts = 256;  // CTAs of the Theta-gradient reduction
@@ -133,9 +137,11 @@ cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int3
                                cudaStream_t s);
 cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
                                      int warps, cudaStream_t s);
+cudaError_t launch_pass1_xi_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                                  cudaStream_t s);
 cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s);
-// pass: 1 rates, 2 gradient, 3 rates with Theta sums
+// pass: 1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with the self-excitation sums apart
 size_t pass_smem_bytes(int d, int pass, int warps);
 int pass_max_ctas_per_sm(int d, int pass, int warps);
 
@@ -147,7 +153,7 @@ cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int
                               cudaStream_t s);
 
 // hk_finalize.cu
-cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, bool theta, cudaStream_t s);
+cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, cudaStream_t s);
 cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
                               cudaStream_t s);
 cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream_t s);

@@ -43,12 +43,14 @@
 
 namespace hk {
 
-enum PairKind : int { kRate = 0, kRateTheta = 1, kGrad = 2 };
+// kRateXi: the rate pass that also keeps the self-excitation sum of each row
+// apart (plane 0: background terms, plane 1: self-excitation terms).
+enum PairKind : int { kRate = 0, kRateTheta = 1, kGrad = 2, kRateXi = 3 };
 
 template <int KIND, int D>
 struct KindTraits {
     static constexpr int VR = KIND == kGrad ? D : (KIND == kRateTheta ? 3 : 1);   // values per row
-    static constexpr int VC = KIND == kGrad ? D : (KIND == kRateTheta ? 6 : 1);   // values per column
+    static constexpr int VC = KIND == kGrad ? D : (KIND == kRateTheta ? 6 : (KIND == kRateXi ? 2 : 1));  // per column
     static constexpr int NF = KIND == kGrad ? 2 * D + 3 : 2 * D + 1;              // staged fields
     static constexpr int NPP = (NF + 3) / 4;                                       // staged float4 planes
 };
@@ -109,6 +111,16 @@ __device__ __forceinline__ void pair_update(const float *cf, const float *rx, fl
         part[0] += mu;
         acc[0] += mu;
         acc[0] += xi;
+    } else if (KIND == kRateXi) {
+        float mu = ex2_approx(fmaf(-dt, dt, -q));
+        float xi = ex2_approx(fmaf(-k.rho, q, fmaf(-k.kappa, dt, k.cxi)));
+        if (!valid) {
+            mu = 0.0f;
+            xi = 0.0f;
+        }
+        part[0] += mu;
+        acc[0] += mu;
+        acc[1] += xi;
     } else if (KIND == kRateTheta) {
         const float dt2 = dt * dt;
         float mu = ex2_approx(-q - dt2);

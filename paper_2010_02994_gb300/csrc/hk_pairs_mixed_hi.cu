@@ -44,6 +44,13 @@ cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_pass1_xi_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
+                                  cudaStream_t s)
+{
+    HK_SWITCH_D(d, launch_pass_t<D>(4, w, items, nitems, grid, warps, s))
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
                                cudaStream_t s)
 {

@@ -1,6 +1,7 @@
 // Launch helpers of the mixed pair kernels, instantiated per dimension by
 // hk_pairs_mixed_lo.cu (D = 1..4) and hk_pairs_mixed_hi.cu (D = 5..8).
-// pass: 1 rates, 2 gradient, 3 rates with Theta sums.
+// pass: 1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with the
+// self-excitation sums apart.
 #pragma once
 
 #include <algorithm>
@@ -26,6 +27,8 @@ cudaError_t launch_pass_t(int pass, const Work &w, const WorkItem *items, int ni
         return launch_kind_t<kRate, D>(w, items, nitems, grid, warps, s);
     if (pass == 2)
         return launch_kind_t<kGrad, D>(w, items, nitems, grid, warps, s);
+    if (pass == 4)
+        return launch_kind_t<kRateXi, D>(w, items, nitems, grid, warps, s);
     return launch_kind_t<kRateTheta, D>(w, items, nitems, grid, warps, s);
 }
 
@@ -37,6 +40,8 @@ size_t smem_t(int pass, int warps)
         return pair_smem_bytes<kRate, D, R>(warps);
     if (pass == 2)
         return pair_smem_bytes<kGrad, D, R>(warps);
+    if (pass == 4)
+        return pair_smem_bytes<kRateXi, D, R>(warps);
     return pair_smem_bytes<kRateTheta, D, R>(warps);
 }
 
@@ -71,6 +76,8 @@ int occupancy_t(int pass, int warps)
         return occupancy_kind<kRate, D>(warps);
     if (pass == 2)
         return occupancy_kind<kGrad, D>(warps);
+    if (pass == 4)
+        return occupancy_kind<kRateXi, D>(warps);
     return occupancy_kind<kRateTheta, D>(warps);
 }
 

@@ -125,6 +125,22 @@ def test_self_excitation_probability(ctx, prec):
         assert np.all((got >= 0) & (got <= 1))
 
 
+@pytest.mark.parametrize("d,n", [(1, 700), (3, 650), (5, 520), (8, 600)])
+def test_self_excitation_probability_every_dimension(ctx, d, n):
+    """The mixed path's rate pass that keeps the self-excitation sums apart,
+    in the dimensions the D = 2 cases above do not reach (ragged last block,
+    tied times)."""
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_self_excitation_prob
+
+    w = synth.random_case(80 + d, n, d, ties=2, shuffle=True)
+    lam, mu, xi = oracle.rates(w.t, w.X, w.params, parts=True)
+    got = hawkes_self_excitation_prob(ctx, torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"),
+                                      w.params, precision="mixed").cpu().numpy()
+    assert np.max(np.abs(got - xi / lam)) <= 1e-5
+
+
 def test_parameter_gradient_large_n_mixed_vs_fp64(ctx):
     """At N = 70,000 the Theta pass takes its 4-warp shape (the 8-warp one
     needs more shared memory than a CTA may have): the mixed parameter
