@@ -36,8 +36,8 @@ CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 # one ncu capture (profiles/pair_kernels_n100000_d2.md), valid for the kernel
 # source whose SHA-256 is recorded with it; reported as null otherwise.
 PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", "hk_pairs_mixed.cuh")
-MEASURED_TRAFFIC = {"source_sha256": "ffc9840c84b674a8a483713e64af854db4688b53bdbfc1afc70e1070367b3fd6",
-                    "pass1_rates": 3748608, "pass2_gradient": 24045824}
+MEASURED_TRAFFIC = {"source_sha256": "be6716bb1c901852f5a3e5186a45882da59a25ffafc812325f5d9bb91299e0ac",
+                    "pass1_rates": 3896832, "pass2_gradient": 24310528}
 
 
 def measured_traffic(kernel: str):
