@@ -435,8 +435,23 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     ctx.sync_status()
     pairs = float(sum(n * n for n in sizes))
     m = statistics.median(ms)
+    # the same batch in FP64 (every operation in double), as the accuracy reference
+    hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, precision="fp64", check=False)
+    torch.cuda.synchronize()
+    ms64 = []
+    for _ in range(2):
+        flush_l2(l2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, precision="fp64", check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64.append(a.elapsed_time(b))
+    ctx.sync_status()
+    m64 = statistics.median(ms64)
     out["batched_c4"] = {"sets": len(sets), "events": sum(sizes), "dims": sorted(set(dims)), "ms_per_call": m,
-                         "calls_per_s": 1e3 / m, "pairs_per_s": pairs / (m * 1e-3)}
+                         "calls_per_s": 1e3 / m, "pairs_per_s": pairs / (m * 1e-3),
+                         "fp64_ms_per_call": m64, "fp64_pairs_per_s": pairs / (m64 * 1e-3)}
     ctx.close()
 
     w = synth.make_c2()
