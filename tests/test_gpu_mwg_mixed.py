@@ -296,3 +296,22 @@ def test_largest_block_in_eight_dimensions(prec):
     else:
         assert abs(got - ref) <= bound(w, w.X, idx, Xn)
     s.close()
+
+
+def test_mixed_signed_zero_times():
+    """In the mixed precision the tie indicators compare time bit patterns with
+    the sign cleared, so +0 and -0 are tied as in the FP64 comparison."""
+    w = synth.random_case(62, 300, 2, shuffle=True)
+    t = w.t.copy()
+    t[[3, 50]] = 0.0
+    t[[7, 120]] = -0.0
+    w = dataclasses.replace(w, t=t)
+    s = mixed_state(w, 4)
+    ell0 = oracle.loglik(w.t, w.X, w.params)
+    idx = np.array([3, 7, 50])
+    Xn = w.X[idx] + 0.05
+    X1 = w.X.copy()
+    X1[idx] = Xn
+    ref = oracle.loglik(w.t, X1, w.params) - ell0
+    assert abs(s.delta(idx, Xn).item() - ref) <= bound(w, w.X, idx, Xn)
+    s.close()

@@ -4,6 +4,7 @@ Tolerances (fixed for this method): the FP64 path within 1e-12 (relative for
 ell, relative L2 for the gradient); the mixed path within 1e-6 for ell and
 1e-5 for the gradient.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -126,6 +127,20 @@ def test_single_event_and_all_tied(ctx, prec):
             hawkes_loglik_grad_locations(ctx, t, X, P, precision=prec)
         assert "ZERO_RATE" in str(e.value)
         ctx.sync_status()  # the status is cleared once reported
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_signed_zero_times_tie(ctx, prec):
+    """Times of exactly +0 and -0 are equal (a tie: neither excites the
+    other), and the time sort and the tie runs must treat them so: the keys
+    of the time sort compare bit patterns, with the sign cleared."""
+    w = synth.random_case(61, 400, 2, shuffle=True)
+    t = w.t.copy()
+    t[[3, 50, 199]] = 0.0
+    t[[7, 120]] = -0.0
+    w = dataclasses.replace(w, t=t)
+    assert np.sum(np.signbit(w.t)) == 2
+    assert_close(ctx, w, prec)
 
 
 def test_ragged_block_edges(ctx):
