@@ -106,6 +106,8 @@ struct hawkes_ctx {
     HmcGraph hmc;
     cudaStream_t side[kMaxD + 1] = {};  // forked streams for concurrent per-dimension launches
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxD + 1] = {};
+    cudaStream_t bmds_side = nullptr;  // the BMDS branch of a BMDS-Hawkes leapfrog step
+    cudaEvent_t bmds_fork = nullptr, bmds_join = nullptr;
     int occ[kMaxD + 1][5][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..4][warps]
     static constexpr int kBuckets = 32;
     int tune_warps[kMaxD + 1][kBuckets] = {};  // 0: no entry
@@ -799,6 +801,11 @@ void hawkes_ctx_destroy(hawkes_ctx *ctx)
             cudaEventDestroy(ctx->join_ev[d]);
         }
     }
+    if (ctx->bmds_side) {
+        cudaStreamDestroy(ctx->bmds_side);
+        cudaEventDestroy(ctx->bmds_fork);
+        cudaEventDestroy(ctx->bmds_join);
+    }
     if (ctx->ws.ptr)
         cudaFree(ctx->ws.ptr);
     if (ctx->bmds_ws.ptr)
@@ -1254,26 +1261,49 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
         if (capture)
             HK_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
         // the BMDS term of the potential, evaluated at the current locations
-        auto add_bmds = [&]() -> hawkes_status {
+        // The BMDS term of a step depends only on the locations, so it runs on a
+        // side branch concurrently with the Hawkes evaluation (each leaves SMs
+        // idle in its tail at the influenza size); the two gradients meet in
+        // add_caller_term.  Neither branch writes what the other reads: the
+        // BMDS kernels use their own workspace and buffers, and the Hawkes
+        // evaluation's control-word reset leaves the shared status word alone.
+        if (bmds && !ctx->bmds_side) {
+            HK_TRY(cudaStreamCreateWithFlags(&ctx->bmds_side, cudaStreamNonBlocking), "BMDS stream");
+            HK_TRY(cudaEventCreateWithFlags(&ctx->bmds_fork, cudaEventDisableTiming), "BMDS fork event");
+            HK_TRY(cudaEventCreateWithFlags(&ctx->bmds_join, cudaEventDisableTiming), "BMDS join event");
+        }
+        auto fork_bmds = [&]() -> hawkes_status {
             if (!bmds)
                 return HAWKES_OK;
-            HK_TRY(launch_to_caller(w, ctx->d_set_row0, w.x64, bx, pl.total_rows, es), "BMDS locations");
+            cudaStream_t bs = ctx->bmds_side;
+            HK_TRY(cudaEventRecord(ctx->bmds_fork, es), "BMDS fork");
+            HK_TRY(cudaStreamWaitEvent(bs, ctx->bmds_fork, 0), "BMDS fork wait");
+            HK_TRY(launch_to_caller(w, ctx->d_set_row0, w.x64, bx, pl.total_rows, bs), "BMDS locations");
             ++ctx->launches_own;
             HK_TRY(launch_bmds(bmds->Y, bmds->y_f32, bx, counts[0], dims[0], bmds->sigma2, fp64, ctx->bmds_ws.ptr,
-                               reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, bg, nullptr, es,
+                               reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, bg, nullptr, bs,
                                &ctx->launches_own),
                    "BMDS kernels");
+            HK_TRY(cudaEventRecord(ctx->bmds_join, bs), "BMDS join");
+            return HAWKES_OK;
+        };
+        auto join_bmds = [&]() -> hawkes_status {
+            if (!bmds)
+                return HAWKES_OK;
+            HK_TRY(cudaStreamWaitEvent(es, ctx->bmds_join, 0), "BMDS join wait");
             HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, bg, ctx->hg, pl.total_rows, bl, es), "BMDS gradient");
             ++ctx->launches_own;
             return HAWKES_OK;
         };
         auto body = [&]() -> hawkes_status {
             hawkes_status r;
+            if ((r = fork_bmds()) != HAWKES_OK)
+                return r;
             if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                 return r;
             if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
                 return r;
-            if ((r = add_bmds()) != HAWKES_OK)
+            if ((r = join_bmds()) != HAWKES_OK)
                 return r;
             HK_TRY(launch_energy(w, ctx->hp, d_H0, ctx->hscal + 4 * ns, es), "H0");
             for (int32_t k = 0; k < n_steps; ++k) {
@@ -1281,11 +1311,13 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                                          box ? ctx->hhi : nullptr, d_eps, pl.total_rows, k == 0 ? 1 : 2, !fp64,
                                          d_bad, es),
                        "leapfrog drift");
+                if ((r = fork_bmds()) != HAWKES_OK)
+                    return r;
                 if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                     return r;
                 if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
                     return r;
-                if ((r = add_bmds()) != HAWKES_OK)
+                if ((r = join_bmds()) != HAWKES_OK)
                     return r;
             }
             if (n_steps > 0)
