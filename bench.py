@@ -610,7 +610,7 @@ def main():
 
     import synth
     from paper_2010_02994_gb300 import (HawkesContext, hawkes_loglik_grad_locations, hawkes_self_excitation_prob,
-                                        probe_pipe_rates)
+                                        probe_dfma_rate, probe_pipe_rates)
 
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
@@ -737,8 +737,10 @@ def main():
             tot += e0.elapsed_time(e1)
         ctx.sync_status()
         ms64 = tot / args.fp64_steps
+        dfma = probe_dfma_rate(local)
         fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "pairs_per_s": n * n / (ms64 * 1e-3),
-                "steps": args.fp64_steps}
+                "steps": args.fp64_steps, "dfma_per_sm_clk": dfma,
+                "fp64_tflops_at_max_clock": 2.0 * dfma * sms * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12}
 
     # --- end to end: host buffers, H2D + evaluation + D2H inside the timing --
     t_h = torch.tensor(w.t).pin_memory()

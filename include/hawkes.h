@@ -456,6 +456,11 @@ hawkes_status hawkes_loglik_noalloc(const double *t, const double *X, int64_t n,
 hawkes_status hawkes_probe_pipe_rates(int32_t device, double *fma_per_sm_clk, double *ex2_per_sm_clk,
                                       double *sm_clock_mhz);
 
+/* FP64 FMA results per SM per clock on `device`, measured the same way
+ * (independent chains, SM clock counter); the rate that bounds the FP64
+ * precision path.  Synchronizes the device. */
+hawkes_status hawkes_probe_dfma_rate(int32_t device, double *dfma_per_sm_clk);
+
 /* Library version, e.g. "hawkes 0.1.0 sm_103a". */
 const char *hawkes_version(void);
 

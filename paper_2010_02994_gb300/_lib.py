@@ -36,7 +36,7 @@ EXPORTED = (
     "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
     "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
     "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box", "hawkes_bmds_hmc_trajectory",
-    "hawkes_mwg_set_precision",
+    "hawkes_mwg_set_precision", "hawkes_probe_dfma_rate",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -135,6 +135,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     dpp = ctypes.POINTER(ctypes.c_double)
     lib.hawkes_probe_pipe_rates.argtypes = [i32, dpp, dpp, dpp]
     lib.hawkes_probe_pipe_rates.restype = st
+    lib.hawkes_probe_dfma_rate.argtypes = [i32, dpp]
+    lib.hawkes_probe_dfma_rate.restype = st
     lib.hawkes_version.argtypes = []
     lib.hawkes_version.restype = ctypes.c_char_p
     return lib

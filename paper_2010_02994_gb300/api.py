@@ -315,6 +315,16 @@ def probe_pipe_rates(device: int = 0) -> dict:
     return {"fma_per_sm_clk": f.value, "ex2_per_sm_clk": e.value, "sm_mhz": mhz.value}
 
 
+def probe_dfma_rate(device: int = 0) -> float:
+    """Measured FP64 FMA results per SM per clock (the bound of the FP64 path)."""
+    lib = _lib.load()
+    r = ctypes.c_double()
+    st = lib.hawkes_probe_dfma_rate(int(device), ctypes.byref(r))
+    if st != _lib.HAWKES_OK:
+        raise HawkesError(st, "DFMA probe failed")
+    return r.value
+
+
 def hawkes_batch_hmc_trajectory(ctx: HawkesContext, sizes, dims, t, X, p0, params_list, eps, n_steps: int, log_u,
                                 box_lo=None, box_hi=None, precision="mixed", check: bool = True):
     """One HMC proposal per set (layout as in hawkes_batch_loglik_grad); X is

@@ -1,7 +1,9 @@
-// Pipe-rate probe: FP32 FMA and MUFU ex2 results per SM per clock.
+// Pipe-rate probes: FP32 FMA and MUFU ex2 results per SM per clock, and FP64
+// FMA (DFMA) results per SM per clock.
 //
-// The pair kernels are bound by these two pipes, so their roofline is
-// derived from measured rates rather than datasheet figures.  Each CTA runs
+// The pair kernels are bound by the first two pipes, so their roofline is
+// derived from measured rates rather than datasheet figures; the FP64 rate
+// bounds the FP64 precision path.  Each CTA runs
 // independent dependency chains long enough to hide latency, times itself
 // with the SM clock counter, and reports operations per SM per clock.
 #include <cuda_runtime.h>
@@ -58,7 +60,63 @@ __global__ void probe_kernel(int kind, float seed, float *sink, long long *cycle
         cycles[blockIdx.x] = t1 - t0;
 }
 
+constexpr int kIters64 = 256;  // FP64 runs at a small fraction of the FP32 rate
+
+__global__ void probe_fp64_kernel(double seed, double *sink, long long *cycles)
+{
+    double v[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        v[c] = seed * (double)(threadIdx.x + c + 1) * 1e-6;
+    __syncthreads();
+    const long long t0 = clock64();
+    const double a = 0.999999, b = 1e-7;
+    for (int i = 0; i < kIters64; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            v[c] = fma(v[c], a, b);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        s += v[c];
+    if (s == 12345.678)
+        sink[threadIdx.x] = s;
+    if (threadIdx.x == 0)
+        cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" hawkes_status hawkes_probe_dfma_rate(int32_t device, double *dfma_per_sm_clk)
+{
+    if (cudaSetDevice(device) != cudaSuccess)
+        return HAWKES_ERR_CUDA;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int threads = 512, per_sm = 2, grid = sms * per_sm;
+    double *sink = nullptr;
+    long long *cyc = nullptr;
+    if (cudaMalloc(&sink, sizeof(double) * threads) != cudaSuccess ||
+        cudaMalloc(&cyc, sizeof(long long) * grid) != cudaSuccess) {
+        cudaFree(sink);
+        return HAWKES_ERR_OOM;
+    }
+    probe_fp64_kernel<<<grid, threads>>>(1.0, sink, cyc);  // warm-up
+    probe_fp64_kernel<<<grid, threads>>>(1.0, sink, cyc);
+    std::vector<long long> c(grid);
+    const cudaError_t e = cudaMemcpy(c.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+    cudaFree(sink);
+    cudaFree(cyc);
+    if (e != cudaSuccess)
+        return HAWKES_ERR_CUDA;
+    const double span = (double)*std::max_element(c.begin(), c.end());
+    if (dfma_per_sm_clk)
+        *dfma_per_sm_clk = (double)per_sm * threads * kChains * kIters64 / span;
+    return HAWKES_OK;
+}
 
 extern "C" hawkes_status hawkes_probe_pipe_rates(int32_t device, double *fma_per_sm_clk, double *ex2_per_sm_clk,
                                                  double *sm_clock_mhz)

@@ -261,3 +261,16 @@ def test_far_block_skipping_is_exact(ctx, make):
         ctx.set_option("skip_far_blocks", 0)
     assert skipped[0] == dense[0]
     assert np.array_equal(skipped[1], dense[1])
+
+
+def test_pipe_rate_probes():
+    """The measured rates the rooflines use are finite and plausible for one
+    SM (FP32 FMA up to 128 lanes per clock, MUFU ex2 and FP64 FMA far fewer)."""
+    from paper_2010_02994_gb300 import probe_dfma_rate, probe_pipe_rates
+
+    r = probe_pipe_rates(0)
+    assert 32.0 <= r["fma_per_sm_clk"] <= 160.0
+    assert 4.0 <= r["ex2_per_sm_clk"] <= 64.0
+    assert 100.0 <= r["sm_mhz"] <= 4000.0
+    dfma = probe_dfma_rate(0)
+    assert 0.0 < dfma <= 64.0
