@@ -517,7 +517,7 @@ def run_workload_calls(name: str, calls: int) -> int:
     import synth
     from paper_2010_02994_gb300 import (HawkesContext, HawkesMwG, hawkes_batch_loglik_grad,
                                         hawkes_bmds_hmc_trajectory, hawkes_bmds_loglik_grad,
-                                        hmc_leapfrog_trajectory)
+                                        hawkes_loglik_grad_locations, hmc_leapfrog_trajectory)
 
     dev = torch.device("cuda", 0)
     if name in ("bmds", "bmds_f64y"):
@@ -564,6 +564,15 @@ def run_workload_calls(name: str, calls: int) -> int:
             hmc_leapfrog_trajectory(ctx, t, X, p0, w.params, 2e-3, 4, 0.0, lo, hi, check=False)
         ctx.sync_status()
         ctx.close()
+    elif name == "fp64_c2":
+        # the FP64 path (location gradient) on the gunfire-like events, N = 10,000, D = 2
+        w = synth.make_c2()
+        ctx = HawkesContext(device=0, max_n=w.n, max_d=w.d)
+        t, X = torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev)
+        for _ in range(calls):
+            hawkes_loglik_grad_locations(ctx, t, X, w.params, precision="fp64", check=False)
+        ctx.sync_status()
+        ctx.close()
     else:
         sets = synth.make_c4()
         sizes, dims = [w.n for w in sets], [w.d for w in sets]
@@ -594,7 +603,7 @@ def main():
                     help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
     ap.add_argument("--workload", default=None,
                     choices=["bmds", "bmds_f64y", "mwg1", "mwg32", "mwg32_mixed", "bmds_hmc", "hmc_c2",
-                             "batched_c4"],
+                             "batched_c4", "fp64_c2"],
                     help="with --kernels-only: run warmup + steps calls of that other workload instead "
                          "(for profiler captures); prints no JSON")
     args = ap.parse_args()
@@ -737,9 +746,29 @@ def main():
             tot += e0.elapsed_time(e1)
         ctx.sync_status()
         ms64 = tot / args.fp64_steps
+        # the ordered layout (every ordered pair, CUDA's exp) on the same inputs
+        ctx.set_option("fp64_ordered", 1)
+        step("fp64")
+        torch.cuda.synchronize()
+        flush_l2(l2)
+        e0.record(stream)
+        step("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ord = e0.elapsed_time(e1)
+        ctx.set_option("fp64_ordered", 0)
+        ctx.sync_status()
         dfma = probe_dfma_rate(local)
+        # FP64 operations per unordered pair in the symmetric kernels when
+        # every exponential is needed: rate pass 2D + 25, gradient pass 4D + 25
+        # (two 8-operation exponentials each); exponentials that round to zero
+        # for a whole warp are skipped, so spread-out data needs fewer
+        ops = 6 * d + 50
+        dense_ms = 0.5 * n * (n - 1) * ops / (dfma * sms * MAX_SM_MHZ_NOMINAL * 1e6) * 1e3
         fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "pairs_per_s": n * n / (ms64 * 1e-3),
-                "steps": args.fp64_steps, "dfma_per_sm_clk": dfma,
+                "steps": args.fp64_steps, "layout": "symmetric (each unordered pair once)",
+                "ordered_layout_ms_per_step": ms_ord, "dfma_per_sm_clk": dfma,
+                "fp64_ops_per_unordered_pair_dense": ops, "dense_fp64_issue_bound_ms_at_max_clock": dense_ms,
                 "fp64_tflops_at_max_clock": 2.0 * dfma * sms * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12}
 
     # --- end to end: host buffers, H2D + evaluation + D2H inside the timing --

@@ -117,14 +117,21 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            contribution is exactly zero, so results are
  *                            bit-identical to the dense evaluation, but the
  *                            number of pairs evaluated depends on the data
- *                            (default 0: every pair is evaluated)            */
+ *                            (default 0: every pair is evaluated)
+ *   HAWKES_OPT_FP64_ORDERED  1: the FP64 path evaluates every ordered pair
+ *                            with CUDA's exp() (the layout it falls back to
+ *                            when the symmetric kernels' partial slots, one
+ *                            per 256-row block and row, would pass 16 GiB);
+ *                            0 (default): each unordered pair once, with a
+ *                            table-driven FP64 exp2 (Tang's method)         */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,
     HAWKES_OPT_PROFILE = 3,
     HAWKES_OPT_TIMES_SORTED = 4,
     HAWKES_OPT_MIXED_FIXUP_EXP = 5,
-    HAWKES_OPT_SKIP_FAR_BLOCKS = 6
+    HAWKES_OPT_SKIP_FAR_BLOCKS = 6,
+    HAWKES_OPT_FP64_ORDERED = 7
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 
@@ -456,10 +463,22 @@ hawkes_status hawkes_loglik_noalloc(const double *t, const double *X, int64_t n,
 hawkes_status hawkes_probe_pipe_rates(int32_t device, double *fma_per_sm_clk, double *ex2_per_sm_clk,
                                       double *sm_clock_mhz);
 
-/* FP64 FMA results per SM per clock on `device`, measured the same way
- * (independent chains, SM clock counter); the rate that bounds the FP64
- * precision path.  Synchronizes the device. */
+/* FP64 FMA results per SM per clock on `device` (independent chains): the
+ * whole kernel is timed with events and divided by the SM clock, read from
+ * the clock counter against the global timer.  On this GPU DADD and DMUL
+ * run at the same rate, so this is the rate that bounds the FP64 precision
+ * path.  Synchronizes the device. */
 hawkes_status hawkes_probe_dfma_rate(int32_t device, double *dfma_per_sm_clk);
+
+/* Evaluate the base-2 exponential of the symmetric FP64 pair kernels (Tang's
+ * table-driven method: a 256-entry table of 2^(j/256) and a degree-4 Taylor
+ * polynomial of 2^f - 1 for |f| <= 2^-9) at n arguments, so that it can be
+ * checked against the host's exp2:  out[i] = 2^y[i] for y[i] <= 0, rounded
+ * once also where the result is subnormal; y[i] < -1100 (-inf included)
+ * gives 0 and y[i] > 0 gives 1.  y, out: device arrays of n doubles on the
+ * current device; work is enqueued on `stream`.  n = 0 does nothing; n < 0
+ * or a null array returns HAWKES_ERR_INVALID_ARG. */
+hawkes_status hawkes_probe_exp2_fp64(const double *y, double *out, int64_t n, hawkes_stream stream);
 
 /* Library version, e.g. "hawkes 0.1.0 sm_103a". */
 const char *hawkes_version(void);

@@ -11,6 +11,6 @@ from .api import (HawkesContext, HawkesError, HawkesMwG, hawkes_batch_hmc_trajec
                   hawkes_loglik_noalloc,
                   hawkes_self_excitation_prob,
                   hmc_leapfrog_trajectory, params_struct,
-                  probe_dfma_rate, probe_pipe_rates,
+                  probe_dfma_rate, probe_exp2_fp64, probe_pipe_rates,
                   version)
 from .autograd import HawkesLogLik, hawkes_loglik_autograd  # noqa: F401,E402

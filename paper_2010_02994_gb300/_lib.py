@@ -24,7 +24,7 @@ STATUS_NAMES = {
 }
 PREC = {"mixed": 0, "fp64": 1}
 OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5,
-           "skip_far_blocks": 6}
+           "skip_far_blocks": 6, "fp64_ordered": 7}
 
 # every function declared in include/hawkes.h
 EXPORTED = (
@@ -36,7 +36,7 @@ EXPORTED = (
     "hawkes_bmds_loglik_grad", "hawkes_bmds_workspace_bytes", "hawkes_mwg_create", "hawkes_mwg_destroy",
     "hawkes_mwg_last_error", "hawkes_mwg_delta", "hawkes_mwg_step", "hawkes_mwg_refresh", "hawkes_mwg_read",
     "hawkes_mwg_sync_status", "hawkes_mwg_propose_circle", "hawkes_mwg_propose_box", "hawkes_bmds_hmc_trajectory",
-    "hawkes_mwg_set_precision", "hawkes_probe_dfma_rate",
+    "hawkes_mwg_set_precision", "hawkes_probe_dfma_rate", "hawkes_probe_exp2_fp64",
 )
 NOALLOC_MAX_N = 8192  # HAWKES_NOALLOC_MAX_N
 
@@ -137,6 +137,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.hawkes_probe_pipe_rates.restype = st
     lib.hawkes_probe_dfma_rate.argtypes = [i32, dpp]
     lib.hawkes_probe_dfma_rate.restype = st
+    lib.hawkes_probe_exp2_fp64.argtypes = [vp, vp, i64, vp]
+    lib.hawkes_probe_exp2_fp64.restype = st
     lib.hawkes_version.argtypes = []
     lib.hawkes_version.restype = ctypes.c_char_p
     return lib

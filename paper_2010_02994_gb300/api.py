@@ -325,6 +325,21 @@ def probe_dfma_rate(device: int = 0) -> float:
     return r.value
 
 
+def probe_exp2_fp64(y: torch.Tensor) -> torch.Tensor:
+    """2^y by the FP64 pair kernels' exponential (Tang's table-driven method),
+    for a CUDA float64 tensor y; y <= 0 is the meaningful range."""
+    if not (y.is_cuda and y.dtype == torch.float64):
+        raise ValueError("y must be a CUDA float64 tensor")
+    y = y.contiguous()
+    out = torch.empty_like(y)
+    lib = _lib.load()
+    st = lib.hawkes_probe_exp2_fp64(ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()), y.numel(),
+                                    ctypes.c_void_p(torch.cuda.current_stream(y.device).cuda_stream))
+    if st != _lib.HAWKES_OK:
+        raise HawkesError(st, "exp2 probe failed")
+    return out
+
+
 def hawkes_batch_hmc_trajectory(ctx: HawkesContext, sizes, dims, t, X, p0, params_list, eps, n_steps: int, log_u,
                                 box_lo=None, box_hi=None, precision="mixed", check: bool = True):
     """One HMC proposal per set (layout as in hawkes_batch_loglik_grad); X is

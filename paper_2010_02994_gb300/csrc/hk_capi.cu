@@ -75,6 +75,7 @@ struct Plan {
     int64_t total_F1 = 0, total_F2 = 0;
     int32_t total_segs = 0, max_fsplit = 1;
     int64_t max_ftiles = 1;
+    bool fp64_sym = false;  // FP64 passes: symmetric kernels over the work items
     double pairs = 0.0;  // unordered pairs over all sets
 };
 
@@ -97,6 +98,7 @@ struct hawkes_ctx {
     DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
     // options
     int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
+    int opt_fp64_ordered = 0;
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
     double prof_ms[kStages] = {};
@@ -250,6 +252,17 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
             pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d, theta);
             ctx->cur_ctas_by_d[d] = ctx->tune_ctas[d][size_bucket(nmax_by_d[d])];
         }
+    // FP64: the symmetric kernels keep one partial slot per row block and
+    // row, (6 + d) doubles each; they are used while that stays within
+    // kSymSlotBudget, the ordered kernels (a few column splits) beyond it
+    if (fp64) {
+        double sym_bytes = 0.0;
+        for (int s = 0; s < nsets; ++s) {
+            const double nb = (double)((ev_counts[s] + kSymRows - 1) / kSymRows);
+            sym_bytes += nb * nb * kSymRows * (kPass1ThetaVals + dims[s]) * sizeof(double);
+        }
+        pl.fp64_sym = ctx->opt_fp64_ordered == 0 && sym_bytes <= kSymSlotBudget;
+    }
     int64_t ev = 0, x = 0, row = 0, rec4 = 0, p1 = 0, p2 = 0, f1 = 0, f2 = 0;
     int32_t seg = 0;
     for (int s = 0; s < nsets; ++s) {
@@ -261,7 +274,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         if (!fp64 && !mixed_range_ok(S))
             return fail(ctx, HAWKES_ERR_INVALID_ARG,
                         "parameters outside the range of the mixed-precision path; use HAWKES_PREC_FP64");
-        const int B = fp64 ? kFp64Rows : 32 * rows_per_lane(d) * pl.warps_by_d[d];
+        const int B = fp64 ? (pl.fp64_sym ? kSymRows : kFp64Rows) : 32 * rows_per_lane(d) * pl.warps_by_d[d];
         S.B = B;
         S.nblk = (int32_t)((n + B - 1) / B);
         S.npad = S.nblk * B;
@@ -280,17 +293,21 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         const int64_t ftiles = (n + kFp64Rows - 1) / kFp64Rows;
         int64_t fs = std::max<int64_t>(1, (8LL * ctx->sm_count) / std::max<int64_t>(1, ftiles * nsets));
         fs = std::min<int64_t>(fs, ftiles);
-        S.fsplit = (int32_t)std::max<int64_t>(1, fs);
+        S.fsplit = pl.fp64_sym ? S.nblk : (int32_t)std::max<int64_t>(1, fs);
         pl.max_fsplit = std::max(pl.max_fsplit, S.fsplit);
         pl.max_ftiles = std::max(pl.max_ftiles, ftiles);
         ev += n;
         x += n * d;
         row += S.npad;
         rec4 += (int64_t)nrec(d) * S.npad;
-        p1 += (int64_t)S.nblk * S.npad * S.vpc;
-        p2 += (int64_t)S.nblk * S.npad * d;
-        f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
-        f2 += (int64_t)S.fsplit * S.npad * d;
+        // partial slots: FP32 for the mixed path, FP64 for the FP64 path
+        if (!fp64) {
+            p1 += (int64_t)S.nblk * S.npad * S.vpc;
+            p2 += (int64_t)S.nblk * S.npad * d;
+        } else {
+            f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
+            f2 += (int64_t)S.fsplit * S.npad * d;
+        }
         seg += S.nseg;
         pl.pairs += 0.5 * (double)n * (double)(n - 1);
     }
@@ -307,7 +324,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         pl.set_ev0[s] = s < nsets ? pl.sets[s].ev0 : ev;
         pl.set_row0[s] = s < nsets ? pl.sets[s].row0 : row;
     }
-    if (!fp64) {
+    if (!fp64 || pl.fp64_sym) {
         // work items grouped by dimension; diagonal blocks (half the work) last
         for (int d = 1; d <= kMaxD; ++d) {
             const int first = (int)pl.items.size();
@@ -602,6 +619,41 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
     return HAWKES_OK;
 }
 
+// One FP64 pair pass (1: rates, 2: gradient): the symmetric kernels, one
+// launch per dimension, or the ordered kernels.  Returns the launches made.
+int fp64_pass_launches(const Plan &pl)
+{
+    if (!pl.fp64_sym)
+        return 1;
+    int k = 0;
+    for (int d = 1; d <= kMaxD; ++d)
+        k += pl.item_range_by_d[d].second > 0 ? 1 : 0;
+    return k;
+}
+
+hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool theta, cudaStream_t s)
+{
+    const Work &w = ctx->w;
+    const int32_t ns = (int32_t)pl.sets.size();
+    if (!pl.fp64_sym) {
+        if (pass == 1)
+            HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
+        else
+            HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
+        return HAWKES_OK;
+    }
+    for (int d = 1; d <= kMaxD; ++d) {
+        const int first = pl.item_range_by_d[d].first, count = pl.item_range_by_d[d].second;
+        if (count == 0)
+            continue;
+        if (pass == 1)
+            HK_TRY(launch_pass1_fp64_sym(d, w, ctx->d_items + first, count, theta, s), "FP64 rate pass");
+        else
+            HK_TRY(launch_pass2_fp64_sym(d, w, ctx->d_items + first, count, s), "FP64 gradient pass");
+    }
+    return HAWKES_OK;
+}
+
 // Pass 1 .. ell (and pass 2 .. gradient) on packed rows.
 hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
                            double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr)
@@ -614,15 +666,18 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     for (int d = 1; d <= kMaxD; ++d)
         ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
     if (fp64)
-        ctx->launches_own += want_grad ? 5 : 3;
+        ctx->launches_own += (want_grad ? 3 : 2) + (want_grad ? 2 : 1) * fp64_pass_launches(pl);
     else
         ctx->launches_own += want_grad ? 2 * ndims + 4 : ndims + 2;
     if (fp64) {
-        HK_TRY(launch_pass1_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, theta, s), "FP64 rate pass");
+        hawkes_status st = enqueue_fp64_pass(ctx, pl, 1, theta, s);
+        if (st != HAWKES_OK)
+            return st;
         HK_TRY(launch_finalize_rows(w, pl.total_segs, true, theta ? kSumsTheta : kSumsNone, s), "finalize rows");
         HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, false, s), "log-likelihood");
         if (want_grad) {
-            HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
+            if ((st = enqueue_fp64_pass(ctx, pl, 2, false, s)) != HAWKES_OK)
+                return st;
             HK_TRY(launch_finalize_grad(w, pl.total_segs, true, out_grad, g_sorted, s), "finalize gradient");
         }
         if (theta) {
@@ -872,6 +927,9 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
     case HAWKES_OPT_SKIP_FAR_BLOCKS:
         ctx->opt_skip = value ? 1 : 0;
         return HAWKES_OK;
+    case HAWKES_OPT_FP64_ORDERED:
+        ctx->opt_fp64_ordered = value ? 1 : 0;
+        return HAWKES_OK;
     case HAWKES_OPT_MIXED_FIXUP_EXP:
         if (value < -120 || value > 0)
             return fail(ctx, HAWKES_ERR_INVALID_ARG, "fixup exponent must be in [-120, 0]");
@@ -1010,7 +1068,8 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
         return st;
     const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
     if (fp64) {
-        HK_TRY(launch_pass1_fp64(ctx->w, 0, 1, pl.max_fsplit, pl.max_ftiles, true, s), "FP64 rate pass");
+        if ((st = enqueue_fp64_pass(ctx, pl, 1, true, s)) != HAWKES_OK)
+            return st;
         HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, kSumsTheta, s), "finalize rows");
         HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, 1, nullptr, false, s), "log-likelihood");
     } else {

@@ -152,6 +152,15 @@ cudaError_t launch_pass1_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int
 cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int32_t max_fsplit, int64_t max_nblk,
                               cudaStream_t s);
 
+// hk_pairs_fp64_sym.cu: one CTA per pair block {I, J} (I <= J) of kSymRows
+// rows, dimension d; slot K of a row of block R holds block K's terms, so a
+// set's FP64 partials take nblk slots (fsplit = nblk).
+constexpr int kSymRows = 256;
+constexpr double kSymSlotBudget = 16.0 * 1024.0 * 1024.0 * 1024.0;  // bytes of partial slots
+cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, bool theta,
+                                  cudaStream_t s);
+cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, cudaStream_t s);
+
 // hk_finalize.cu
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, cudaStream_t s);
 cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
