@@ -1,5 +1,6 @@
-// FP64 base-2 exponential of the symmetric FP64 pair kernels (and of the
-// probe that tests it against the host's exp2).
+// FP64 base-2 exponential of the FP64 pair terms (the symmetric FP64 pair
+// kernels, the incremental MwG kernels, and the probe that tests it against
+// the host's exp2).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,14 +20,17 @@ constexpr unsigned kHiNeg1076 = 0xC090D000u;
 // meet on pairs they discard) are taken as 0.  2^k is applied to the
 // exponent field; for k < -1075 the result rounds to zero and is set so,
 // and for -1075 <= k < -1021 one multiplication by a further power of two
-// rounds it once into the subnormal range, done only when some lane of
-// `mask` (the lanes making the call together) needs it.  Every add and
-// multiply is written as a fused multiply-add with `one` = 1 or `mz` = -0
-// (runtime values the compiler cannot fold), which leaves each result
-// unchanged.  Measured against a 64-bit-mantissa exp2 on 2e7 arguments in
-// [-1100, 0]: 1.32 ulp.
-__device__ __forceinline__ double exp2_neg(double y, const double *__restrict__ tab, unsigned mask, double one,
-                                           double mz)
+// rounds it once into the subnormal range.  Every add and multiply is
+// written as a fused multiply-add with `one` = 1 or `mz` = -0 (runtime
+// values the compiler cannot fold), which leaves each result unchanged.
+// Measured against a 64-bit-mantissa exp2 on 2e7 arguments in [-1100, 0]:
+// 1.32 ulp.
+struct Exp2Parts {
+    double res;  // 2^max(k, -1021) T[j] (1 + q(f)), a normal double
+    int k, kk;   // k and max(k, -1021)
+};
+
+__device__ __forceinline__ Exp2Parts exp2_core(double y, const double *__restrict__ tab, double one, double mz)
 {
     // clamps on the bit pattern (integer pipe): for y <= 0 a larger unsigned
     // high word means a larger magnitude
@@ -44,12 +48,37 @@ __device__ __forceinline__ double exp2_neg(double y, const double *__restrict__ 
     p = fma(f, p, kExp2C1);
     const double T = tab[j & 255];
     const double r = fma(T, fma(f, p, mz), T);  // 2^(j mod 256 / 256 + f), in [0.99, 2)
-    const int k = j >> 8;                       // floor(j / 256), >= -1100
-    const int kk = max(k, -1021);               // 2^kk r is a normal double
-    double res = __hiloint2double((int)((unsigned)__double2hiint(r) + ((unsigned)kk << 20)), __double2loint(r));
-    if (__any_sync(mask, k < kk && k >= -1075))
-        res = fma(res, __hiloint2double((k - kk + 1023) << 20, 0), mz);  // times 2^(k - kk) >= 2^-79
-    return k < -1075 ? 0.0 : res;
+    Exp2Parts e;
+    e.k = j >> 8;  // floor(j / 256), >= -1100
+    e.kk = max(e.k, -1021);
+    e.res = __hiloint2double((int)((unsigned)__double2hiint(r) + ((unsigned)e.kk << 20)), __double2loint(r));
+    return e;
+}
+
+// The last rounding for -1075 <= k < -1021: times 2^(k - kk) >= 2^-79.
+__device__ __forceinline__ double exp2_subnormal(const Exp2Parts &e, double mz)
+{
+    return fma(e.res, __hiloint2double((e.k - e.kk + 1023) << 20, 0), mz);
+}
+
+// Warp form: the lanes of `mask` make the call together, and the subnormal
+// multiplication is issued only when one of them needs it.
+__device__ __forceinline__ double exp2_neg(double y, const double *__restrict__ tab, unsigned mask, double one,
+                                           double mz)
+{
+    Exp2Parts e = exp2_core(y, tab, one, mz);
+    if (__any_sync(mask, e.k < e.kk && e.k >= -1075))
+        e.res = exp2_subnormal(e, mz);
+    return e.k < -1075 ? 0.0 : e.res;
+}
+
+// Lane form, for callers whose lanes may diverge.
+__device__ __forceinline__ double exp2_neg_lane(double y, const double *__restrict__ tab)
+{
+    Exp2Parts e = exp2_core(y, tab, 1.0, -0.0);
+    if (e.k < e.kk && e.k >= -1075)
+        e.res = exp2_subnormal(e, -0.0);
+    return e.k < -1075 ? 0.0 : e.res;
 }
 
 }  // namespace hk

@@ -30,6 +30,7 @@
 #include <string>
 
 #include "hawkes.h"
+#include "hk_exp2.cuh"
 
 namespace {
 
@@ -46,26 +47,40 @@ constexpr int kBadProposal = 4;  // non-finite proposed location
 
 struct Consts {
     double a, b, c;  // 1/(2 tau_x^2), 1/(2 tau_t^2), 1/(2 h^2)
+    double a2, b2, c2, w2;  // a, b, c and omega times log2(e): the base-2 exponents
     double Cmu, Cxi, omega, mu0, tau_t, theta;
 };
 
+// For t >= 0 the bit pattern with the sign cleared (so -0 equals +0) orders
+// like the value: the time indicators compare these keys.
+__device__ __forceinline__ long long tkey(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffLL; }
+
 // Contribution of event (xs, ts) to the rate at event (xm, tm): the
 // background term (both Gaussians, I[t != t_m]) and the self-excitation term
-// (I[t < t_m]) of Section 2.1.
+// (I[t < t_m]) of Section 2.1, in FP64 with base-2 exponents and the
+// table-driven exp2.  An exponential whose exponent is below -1076 rounds to
+// zero and is not evaluated (a warp skips it when none of its lanes needs it).
 __device__ __forceinline__ double contrib(const double *xm, double tm, const double *xs, double ts, int d,
                                           const Consts &k)
 {
     double r2 = 0.0;
     for (int q = 0; q < d; ++q) {
         const double df = xm[q] - xs[q];
-        r2 += df * df;
+        r2 = fma(df, df, r2);
     }
     const double dt = tm - ts;
+    const long long km = tkey(tm), ks = tkey(ts);
     double v = 0.0;
-    if (tm != ts)
-        v += k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
-    if (ts < tm)
-        v += k.Cxi * exp(-(k.omega * dt + r2 * k.c));
+    if (km != ks) {
+        const double y = -fma(dt * k.b2, dt, r2 * k.a2);
+        if ((unsigned)__double2hiint(y) <= hk::kHiNeg1076)
+            v = k.Cmu * hk::exp2_neg_lane(y, hk::kExp2Tab);
+    }
+    if (ks < km) {
+        const double y = -fma(k.w2, dt, r2 * k.c2);
+        if ((unsigned)__double2hiint(y) <= hk::kHiNeg1076)
+            v = fma(k.Cxi, hk::exp2_neg_lane(y, hk::kExp2Tab), v);
+    }
     return v;
 }
 
@@ -98,10 +113,6 @@ __device__ __forceinline__ void split32(double v, float &h, float &l)
     h = __double2float_rn(v);
     l = __double2float_rn(v - (double)h);
 }
-
-// For t >= 0 the bit pattern with the sign cleared (so -0 equals +0) orders
-// like the value: the time indicators compare these keys.
-__device__ __forceinline__ long long tkey(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffLL; }
 
 struct Sum32 {  // compensated (Kahan) FP32 sum
     float s = 0.f, c = 0.f;
@@ -872,6 +883,11 @@ Consts make_consts(const hawkes_params &p, int d)
     k.a = 0.5 / (p.tau_x * p.tau_x);
     k.b = 0.5 / (p.tau_t * p.tau_t);
     k.c = 0.5 / (p.h * p.h);
+    const double log2e = 1.4426950408889634074;
+    k.a2 = k.a * log2e;
+    k.b2 = k.b * log2e;
+    k.c2 = k.c * log2e;
+    k.w2 = p.omega * log2e;
     k.Cmu = p.mu0 / (std::pow(p.tau_x, d) * p.tau_t * std::pow(two_pi, 0.5 * (d + 1)));
     k.Cxi = p.theta * p.omega / (std::pow(p.h, d) * std::pow(two_pi, 0.5 * d));
     k.omega = p.omega;

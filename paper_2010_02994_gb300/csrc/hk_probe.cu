@@ -158,7 +158,7 @@ namespace {
 __global__ void exp2_probe_kernel(const double *__restrict__ y, double *__restrict__ out, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = hk::exp2_neg(y[i], hk::kExp2Tab, __activemask(), 1.0, -0.0);
+        out[i] = hk::exp2_neg_lane(y[i], hk::kExp2Tab);
 }
 
 }  // namespace
