@@ -84,10 +84,12 @@ typedef void *hawkes_stream; /* cudaStream_t */
 /* ------------------------------------------------------------ context -- */
 
 /* Create a context on CUDA device `device` whose device workspace holds
- * problems of up to max_n events (summed over the sets of a batch) in up to
- * max_d <= 8 dimensions.  Larger calls grow the workspace on demand, which
- * allocates device memory at that call.  On success *ctx owns the workspace
- * until hawkes_ctx_destroy. */
+ * mixed-precision problems of up to max_n events (summed over the sets of a
+ * batch) in up to max_d <= 8 dimensions.  Larger calls grow the workspace on
+ * demand, which allocates device memory at that call; so does the first
+ * HAWKES_PREC_FP64 call, whose partial sums take (6 + d) doubles per event
+ * and 256-event block (about 2.5 GB at n = 1e5, d = 2).  On success *ctx owns
+ * the workspace until hawkes_ctx_destroy. */
 hawkes_status hawkes_ctx_create(hawkes_ctx **ctx, int32_t device, int64_t max_n, int32_t max_d);
 
 /* Release a context and its device memory.  The caller must have finished
