@@ -769,6 +769,8 @@ def main():
                 "steps": args.fp64_steps, "layout": "symmetric (each unordered pair once)",
                 "ordered_layout_ms_per_step": ms_ord, "dfma_per_sm_clk": dfma,
                 "fp64_ops_per_unordered_pair_dense": ops, "dense_fp64_issue_bound_ms_at_max_clock": dense_ms,
+                "note": "the dense bound assumes every exponential is evaluated; terms that round to zero "
+                        "in FP64 are skipped exactly, so spread-out data runs below it",
                 "fp64_tflops_at_max_clock": 2.0 * dfma * sms * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12}
 
     # --- end to end: host buffers, H2D + evaluation + D2H inside the timing --
