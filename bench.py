@@ -760,10 +760,10 @@ def main():
         ctx.sync_status()
         dfma = probe_dfma_rate(local)
         # FP64 operations per unordered pair in the symmetric kernels when
-        # every exponential is needed: rate pass 2D + 25, gradient pass 4D + 25
-        # (two 8-operation exponentials each); exponentials that round to zero
+        # every exponential is needed: rate pass 2D + 23, gradient pass 4D + 23
+        # (two 7-operation exponentials each); exponentials that round to zero
         # for a whole warp are skipped, so spread-out data needs fewer
-        ops = 6 * d + 50
+        ops = 6 * d + 46
         dense_ms = 0.5 * n * (n - 1) * ops / (dfma * sms * MAX_SM_MHZ_NOMINAL * 1e6) * 1e3
         fp64 = {"evals_per_s": 1e3 / ms64, "ms_per_step": ms64, "pairs_per_s": n * n / (ms64 * 1e-3),
                 "steps": args.fp64_steps, "layout": "symmetric (each unordered pair once)",

@@ -472,9 +472,9 @@ hawkes_status hawkes_probe_pipe_rates(int32_t device, double *fma_per_sm_clk, do
  * path.  Synchronizes the device. */
 hawkes_status hawkes_probe_dfma_rate(int32_t device, double *dfma_per_sm_clk);
 
-/* Evaluate the base-2 exponential of the symmetric FP64 pair kernels (Tang's
- * table-driven method: a 256-entry table of 2^(j/256) and a degree-4 Taylor
- * polynomial of 2^f - 1 for |f| <= 2^-9) at n arguments, so that it can be
+/* Evaluate the base-2 exponential of the FP64 pair terms (Tang's
+ * table-driven method: a 2048-entry table of 2^(j/2048) and a degree-3 Taylor
+ * polynomial of 2^f - 1 for |f| <= 2^-12) at n arguments, so that it can be
  * checked against the host's exp2:  out[i] = 2^y[i] for y[i] <= 0, rounded
  * once also where the result is subnormal; y[i] < -1100 (-inf included)
  * gives 0 and y[i] > 0 gives 1.  y, out: device arrays of n doubles on the

@@ -22,14 +22,14 @@
 // excluded pairs are decided on integer ranks (n >= tie_end[m] holds exactly
 // for m < n with t_m < t_n), the exponentials are base-2 with the exponents
 // folded into the constants and evaluated by Tang's table-driven method
-// (exp2_neg, 8 FP64 operations), and work whose result rounds to zero is
+// (exp2_neg, 7 FP64 operations), and work whose result rounds to zero is
 // skipped, which leaves every sum unchanged: a term of a 32 x 32 chunk (a
 // warp's rows against 32 columns) whose smallest time gap alone puts its
 // exponent below -1076, and an exponential that no live lane of a warp
 // needs above 2^-1076.  Every add and multiply is written as a fused multiply-add
 // with a runtime one or negative zero (same results; the all-FMA stream
-// measured 5% faster than the mixed one).  A pair costs at most 2D + 25 FP64
-// operations in the rate pass and 4D + 25 in the gradient pass, against
+// measured 5% faster than the mixed one).  A pair costs at most 2D + 23 FP64
+// operations in the rate pass and 4D + 23 in the gradient pass, against
 // about 100 per unordered pair (D = 2) for the ordered kernels with CUDA's
 // exp().
 #include <climits>
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__
 {
     constexpr int VR = SymVals<KIND, D>::R;
     constexpr int VC = SymVals<KIND, D>::C;
-    __shared__ double tab[kExp2TabSize];
+    const double *tab = kExp2Tab;  // 16 KB, read through L1
     __shared__ double ct[kB];
     __shared__ double cx[D][kB];
     __shared__ double cA[KIND == 2 ? kB : 1];
@@ -200,8 +200,6 @@ __global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__
     // rounding of c' r^2), as an unsigned bit pattern
     const unsigned long long r2_xi = (unsigned long long)__double_as_longlong(1076.0 / cp * (1.0 + 0x1p-40));
 
-    for (int i = tid; i < kExp2TabSize; i += kB)
-        tab[i] = kExp2Tab[i];
     {
         const int m = E * kB + tid;
         const bool ok = m < S.n;

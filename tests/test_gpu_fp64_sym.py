@@ -45,8 +45,8 @@ def test_exp2_within_two_ulp_of_host():
         -1022.0 - rng.uniform(0.0, 54.0, 200_000),           # subnormal results
         -np.ldexp(rng.uniform(0.5, 1.0, 100_000), -rng.integers(1, 60, 100_000)),  # tiny |y|
         -np.arange(0, 1101, dtype=np.float64),               # integers: exact powers of two
-        -np.arange(0, 2048, dtype=np.float64) / 256.0,       # the table's nodes
-        -(np.arange(0, 2048, dtype=np.float64) + 0.5) / 256.0,  # midway between nodes
+        -np.arange(0, 16384, dtype=np.float64) / 2048.0,     # the table's nodes
+        -(np.arange(0, 16384, dtype=np.float64) + 0.5) / 2048.0,  # midway between nodes
     ]
     y = np.concatenate(parts)
     got = probe_exp2_fp64(torch.tensor(y, device="cuda")).cpu().numpy()
