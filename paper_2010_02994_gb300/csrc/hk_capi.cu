@@ -619,8 +619,8 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
     return HAWKES_OK;
 }
 
-// One FP64 pair pass (1: rates, 2: gradient): the symmetric kernels, one
-// launch per dimension, or the ordered kernels.  Returns the launches made.
+// Kernel launches one FP64 pair pass makes: one per dimension for the
+// symmetric kernels, one for the ordered kernels.
 int fp64_pass_launches(const Plan &pl)
 {
     if (!pl.fp64_sym)
@@ -631,6 +631,9 @@ int fp64_pass_launches(const Plan &pl)
     return k;
 }
 
+// One FP64 pair pass (1: rates, with the Theta sums when theta; 2: gradient):
+// the symmetric kernels over the plan's work items of each dimension, or the
+// ordered kernels over all sets.
 hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool theta, cudaStream_t s)
 {
     const Work &w = ctx->w;
@@ -660,7 +663,6 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
 {
     const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
-    const int32_t ns = (int32_t)pl.sets.size();
     const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
     int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
