@@ -125,11 +125,12 @@ def test_self_excitation_probability(ctx, prec):
         assert np.all((got >= 0) & (got <= 1))
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
 @pytest.mark.parametrize("d,n", [(1, 700), (3, 650), (5, 520), (8, 600)])
-def test_self_excitation_probability_every_dimension(ctx, d, n):
-    """The mixed path's rate pass that keeps the self-excitation sums apart,
-    in the dimensions the D = 2 cases above do not reach (ragged last block,
-    tied times)."""
+def test_self_excitation_probability_every_dimension(ctx, d, n, prec):
+    """The rate pass that keeps the self-excitation sums apart (mixed) or the
+    FP64 rate pass with the parameter-gradient sums, in the dimensions the
+    D = 2 cases above do not reach (ragged last block, tied times)."""
     import torch
 
     from paper_2010_02994_gb300 import hawkes_self_excitation_prob
@@ -137,8 +138,8 @@ def test_self_excitation_probability_every_dimension(ctx, d, n):
     w = synth.random_case(80 + d, n, d, ties=2, shuffle=True)
     lam, mu, xi = oracle.rates(w.t, w.X, w.params, parts=True)
     got = hawkes_self_excitation_prob(ctx, torch.tensor(w.t, device="cuda"), torch.tensor(w.X, device="cuda"),
-                                      w.params, precision="mixed").cpu().numpy()
-    assert np.max(np.abs(got - xi / lam)) <= 1e-5
+                                      w.params, precision=prec).cpu().numpy()
+    assert np.max(np.abs(got - xi / lam)) <= (1e-5 if prec == "mixed" else 1e-12)
 
 
 def test_parameter_gradient_large_n_mixed_vs_fp64(ctx):
