@@ -19,6 +19,11 @@
 //   A row n of block I receives its partial from the pair block {I, J} in
 //   slot J; each slot has exactly one writer, so every sum below is taken
 //   in a fixed order and the results are deterministic.
+//   F1, F2  the FP64 path's partials, FP64, in the same slot-major layout
+//         (F1[fpart0 + (slot*V + v)*npad + i], V = 6 with the Theta sums,
+//         else 1; F2[fpart2_0 + (slot*D + k)*npad + i]), fsplit slots: one
+//         per row block for the symmetric kernels, a few column splits for
+//         the ordered ones.  A plan holds P1/P2 or F1/F2, not both.
 #pragma once
 
 #include <cuda_runtime.h>
