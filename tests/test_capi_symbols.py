@@ -71,3 +71,15 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
         finally:
             _lib._lib = None
+
+
+def test_binding_option_names_match_the_header():
+    """Every HAWKES_OPT_* value of the header has a Python option name with the
+    same number, and the binding names no value the header lacks."""
+    from paper_2010_02994_gb300 import _lib
+
+    src = open(os.path.join(ROOT, "include", "hawkes.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    header = {name.lower(): int(v) for name, v in re.findall(r"HAWKES_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", src)}
+    assert header, "no HAWKES_OPT_* values found"
+    assert _lib.OPTIONS == header
