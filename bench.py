@@ -33,8 +33,8 @@ MAX_SM_MHZ_NOMINAL = 2070.0  # GB300 maximum SM clock
 CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 
 # DRAM bytes (read + write) per launch of each pair kernel at N=1e5, D=2, from
-# one ncu capture (profiles/pair_kernels_n100000_d2.md), valid for the kernel
-# source whose SHA-256 is recorded with it; reported as null otherwise.
+# one ncu capture of the kernel source whose SHA-256 is recorded with it;
+# reported as null once the source has changed.
 PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", "hk_pairs_mixed.cuh")
 MEASURED_TRAFFIC = {"source_sha256": "be6716bb1c901852f5a3e5186a45882da59a25ffafc812325f5d9bb91299e0ac",
                     "pass1_rates": 3896832, "pass2_gradient": 24310528}

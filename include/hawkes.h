@@ -29,7 +29,7 @@
  *     results are written to device memory.
  *   - The returned status reports argument errors found on the host.
  *     Errors found on the device (non-finite or negative inputs, a zero
- *     rate, a timed-out device wait) are recorded in a sticky per-context
+ *     rate) are recorded in a sticky per-context
  *     device status; hawkes_ctx_sync_status() waits for the stream and
  *     returns it.  Outputs of a call that records a device error are NaN.
  *   - A context is used by one host thread at a time; calls that share a
@@ -73,7 +73,8 @@ typedef enum {
     HAWKES_ERR_INVALID_ARG = 1,  /* bad size, pointer, parameter or option   */
     HAWKES_ERR_ZERO_RATE = 2,    /* some lambda_n == 0: ell = -inf, grad NaN */
     HAWKES_ERR_CUDA = 3,         /* a CUDA runtime call failed               */
-    HAWKES_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up       */
+    /* 4 is unused: no kernel of the library waits on another CTA, stream or
+     * device, so there is no device-side wait that could time out.         */
     HAWKES_ERR_OOM = 5,          /* device workspace could not be allocated  */
     HAWKES_ERR_INVALID_DATA = 6  /* non-finite X or t, or some t_n < 0       */
 } hawkes_status;
@@ -435,22 +436,26 @@ hawkes_status hawkes_batch_loglik_grad(hawkes_ctx *ctx, int32_t n_sets, const in
  * would bypass), and real-time or embedded callers that forbid allocation
  * after start-up, cannot create a hawkes_ctx, whose workspace is allocated.
  *
- * hawkes_loglik_noalloc computes ell of Eq. (1) for up to
- * HAWKES_NOALLOC_MAX_N events in FP64 (ordered pairs, the arithmetic of
- * HAWKES_PREC_FP64) and calls no cudaMalloc, cudaFree or allocating library
- * routine.  Its scratch is a fixed array of HAWKES_NOALLOC_MAX_N * 16 + 32
- * doubles (about 1 MiB) in the library's static device memory, which every
- * GPU that loads the library holds until the process exits.
+ * hawkes_loglik_noalloc computes the same log-likelihood as hawkes_loglik
+ * in HAWKES_PREC_FP64 (every operation in double, here over ordered pairs)
+ * for up to HAWKES_NOALLOC_MAX_N events, and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch is a fixed array of
+ * HAWKES_NOALLOC_MAX_N * 16 + 32 doubles (about 1 MiB) in the library's
+ * static device memory, which every GPU that loads the library holds until
+ * the process exits.
  *   t, X: device [n], [n*d] (row-major), on the calling thread's current
  *         CUDA device; any time order.  1 <= n <= HAWKES_NOALLOC_MAX_N,
  *         1 <= d <= 8; larger n returns HAWKES_ERR_INVALID_ARG.
  *   out_loglik: device [1]; -inf for a zero rate; NaN when some t_n is
  *         negative or not finite or some coordinate is not finite.
- * Work is enqueued on `stream`.  The first call on a device looks up the
- * device address of the scratch array (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  Every call shares the one scratch
- * array: calls whose work overlaps on the GPU (different streams, no
- * ordering between them) race and give wrong results. */
+ * Work is enqueued on `stream`.  The first call in each CUDA context (the
+ * device's primary context, or a context the caller made current) looks up
+ * the device address of the scratch array in that context
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call in a context shares the one scratch array and leaves its
+ * contents behind; the status word is cleared by each call.  Calls whose work
+ * overlaps on the GPU (different streams, no ordering between them) race and
+ * give wrong results. */
 #define HAWKES_NOALLOC_MAX_N 8192
 hawkes_status hawkes_loglik_noalloc(const double *t, const double *X, int64_t n, int32_t d,
                                     const hawkes_params *params, hawkes_stream stream, double *out_loglik);

@@ -68,6 +68,7 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_grad_locations.argtypes = [i64, i32, dp, dp, pp, dp, dp, i32]
     lib.oracle_grad_rows.argtypes = [i64, i32, dp, dp, pp, dp, i64, lp, dp, i32]
     lib.oracle_grad_params.argtypes = [i64, i32, dp, dp, pp, dp, dp, i32]
+    lib.oracle_grad_params_scaled.argtypes = [i64, i32, dp, dp, pp, dp, dp, dp, i32]
     lib.oracle_hmc_trajectory.argtypes = [i64, i32, dp, dp, dp, dp, dp, pp, ctypes.c_double, i32,
                                           ctypes.c_double, dp, dp, dp, dp,
                                           ctypes.POINTER(ctypes.c_int32), i32]
@@ -84,7 +85,7 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_box_proposals.restype = ctypes.c_int
     lib.oracle_max_threads.restype = i32
     for name in ("oracle_rates", "oracle_rates_rows", "oracle_loglik", "oracle_grad_locations",
-                 "oracle_grad_rows", "oracle_grad_params", "oracle_hmc_trajectory"):
+                 "oracle_grad_rows", "oracle_grad_params", "oracle_grad_params_scaled", "oracle_hmc_trajectory"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -212,6 +213,23 @@ class Oracle:
         _check(self.lib.oracle_grad_params(n, d, _dp(t), _dp(X), ctypes.byref(p), _dp(lam), _dp(out),
                                            nthreads), "grad_params")
         return out
+
+    def grad_params_scaled(self, t, X, params, lam=None, nthreads: int = 0):
+        """(d ell / d Theta, scale): scale[k] sums the magnitudes of the terms
+        component k is summed from (the pair-term pieces over lambda_n and the
+        derivatives of Lambda_n), the size a rounding error of the row sums is
+        relative to.  The gradient is the one grad_params returns."""
+        t, X = _prep(t, X)
+        n, d = X.shape
+        if lam is None:
+            lam = self.rates(t, X, params, nthreads)
+        lam = _as_f64(lam)
+        out = np.empty(6)
+        scale = np.empty(6)
+        p = params_struct(params)
+        _check(self.lib.oracle_grad_params_scaled(n, d, _dp(t), _dp(X), ctypes.byref(p), _dp(lam), _dp(out),
+                                                  _dp(scale), nthreads), "grad_params_scaled")
+        return out, scale
 
     def loglik_and_grad(self, t, X, params, nthreads: int = 0):
         """(ell, d ell / d X, lambda)."""
@@ -349,6 +367,10 @@ def grad_rows(*a, **k):
 
 def grad_params(*a, **k):
     return default().grad_params(*a, **k)
+
+
+def grad_params_scaled(*a, **k):
+    return default().grad_params_scaled(*a, **k)
 
 
 def loglik_and_grad(*a, **k):

@@ -365,15 +365,26 @@ int oracle_grad_rows(int64_t n, int32_t d, const double *t, const double *X,
  *   d/d h     = sum_n lambda_n^-1 sum_n' xi_{nn'} (r^2/h^3 - D/h)
  * lam must hold lambda_n for all rows.
  */
-int oracle_grad_params(int64_t n, int32_t d, const double *t, const double *X,
-                       const oracle_params *p, const double *lam, double *out6,
-                       int32_t nthreads)
+/*
+ * d ell / d Theta and, when scale6 is not NULL, the magnitude of the terms
+ * each component is summed from: for component k, the sum over rows of
+ * lambda_n^-1 sum_n' (|first piece| + |second piece|) of the pair terms
+ * below, plus the absolute values of the Lambda derivatives.  That is the
+ * quantity a rounding error in the row sums is relative to, whatever
+ * cancellation the total itself shows (near the data-generating Theta each
+ * score is a sum of N terms of either sign).  The total is computed exactly
+ * as without the scale.
+ */
+static int grad_params_impl(int64_t n, int32_t d, const double *t, const double *X,
+                            const oracle_params *p, const double *lam, double *out6,
+                            double *scale6, int32_t nthreads)
 {
     if (n < 1 || d < 1 || !params_ok(p) || !t || !X || !lam || !out6)
         return ORACLE_ERR_ARG;
-    double *rowv = (double *)malloc(sizeof(double) * 6 * n);
+    double *rowv = (double *)malloc(sizeof(double) * 12 * n);
     if (!rowv)
         return ORACLE_ERR_ARG;
+    double *rowm = rowv + 6 * n;
     double tx = p->tau_x, tt = p->tau_t, h = p->h, w = p->omega;
 #ifdef _OPENMP
     if (nthreads > 0)
@@ -381,9 +392,9 @@ int oracle_grad_params(int64_t n, int32_t d, const double *t, const double *X,
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
     for (int64_t i = 0; i < n; ++i) {
-        nsum a[6];
+        nsum a[6], b[6];
         for (int k = 0; k < 6; ++k)
-            a[k].s = a[k].c = 0.0;
+            a[k].s = a[k].c = b[k].s = b[k].c = 0.0;
         const double *xi_ = X + i * d;
         for (int64_t m = 0; m < n; ++m) {
             const double *xm = X + m * d;
@@ -397,30 +408,70 @@ int oracle_grad_params(int64_t n, int32_t d, const double *t, const double *X,
             nadd(&a[3], xi / p->theta);
             nadd(&a[4], xi * (1.0 / w - dt));
             nadd(&a[5], xi * (r2 / (h * h * h) - (double)d / h));
+            if (scale6) {
+                nadd(&b[0], mu / p->mu0);
+                nadd(&b[1], mu * (r2 / (tx * tx * tx) + (double)d / tx));
+                nadd(&b[2], mu * (dt * dt / (tt * tt * tt) + 1.0 / tt));
+                nadd(&b[3], xi / p->theta);
+                nadd(&b[4], xi * (1.0 / w + fabs(dt)));
+                nadd(&b[5], xi * (r2 / (h * h * h) + (double)d / h));
+            }
         }
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < 6; ++k) {
             rowv[6 * i + k] = nval(&a[k]) / lam[i];
+            rowm[6 * i + k] = scale6 ? nval(&b[k]) / lam[i] : 0.0;
+        }
     }
     (void)nthreads;
     double T = max_time(n, t);
-    nsum s[6];
+    nsum s[6], sm[6];
     for (int k = 0; k < 6; ++k)
-        s[k].s = s[k].c = 0.0;
+        s[k].s = s[k].c = sm[k].s = sm[k].c = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         double a_ = T - t[i];
         for (int k = 0; k < 6; ++k)
             nadd(&s[k], rowv[6 * i + k]);
-        nadd(&s[0], -(Phi(a_ / tt) - Phi(-t[i] / tt)));
-        nadd(&s[2], p->mu0 * (phi_d(a_ * a_ / (tt * tt), 1) * a_ +
-                              phi_d(t[i] * t[i] / (tt * tt), 1) * t[i]) /
-                        (tt * tt));
-        nadd(&s[3], -(1.0 - exp(-w * a_)));
-        nadd(&s[4], -p->theta * a_ * exp(-w * a_));
+        double l0 = -(Phi(a_ / tt) - Phi(-t[i] / tt));
+        double l2 = p->mu0 * (phi_d(a_ * a_ / (tt * tt), 1) * a_ + phi_d(t[i] * t[i] / (tt * tt), 1) * t[i]) /
+                    (tt * tt);
+        double l3 = -(1.0 - exp(-w * a_));
+        double l4 = -p->theta * a_ * exp(-w * a_);
+        nadd(&s[0], l0);
+        nadd(&s[2], l2);
+        nadd(&s[3], l3);
+        nadd(&s[4], l4);
+        if (scale6) {
+            for (int k = 0; k < 6; ++k)
+                nadd(&sm[k], rowm[6 * i + k]);
+            nadd(&sm[0], fabs(l0));
+            nadd(&sm[2], fabs(l2));
+            nadd(&sm[3], fabs(l3));
+            nadd(&sm[4], fabs(l4));
+        }
     }
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 6; ++k) {
         out6[k] = nval(&s[k]);
+        if (scale6)
+            scale6[k] = nval(&sm[k]);
+    }
     free(rowv);
     return ORACLE_OK;
+}
+
+int oracle_grad_params(int64_t n, int32_t d, const double *t, const double *X,
+                       const oracle_params *p, const double *lam, double *out6,
+                       int32_t nthreads)
+{
+    return grad_params_impl(n, d, t, X, p, lam, out6, NULL, nthreads);
+}
+
+int oracle_grad_params_scaled(int64_t n, int32_t d, const double *t, const double *X,
+                              const oracle_params *p, const double *lam, double *out6,
+                              double *scale6, int32_t nthreads)
+{
+    if (!scale6)
+        return ORACLE_ERR_ARG;
+    return grad_params_impl(n, d, t, X, p, lam, out6, scale6, nthreads);
 }
 
 /* ------------------------------------------------------------------ HMC -- */

@@ -18,7 +18,6 @@ STATUS_NAMES = {
     1: "HAWKES_ERR_INVALID_ARG",
     2: "HAWKES_ERR_ZERO_RATE",
     3: "HAWKES_ERR_CUDA",
-    4: "HAWKES_ERR_TIMEOUT",
     5: "HAWKES_ERR_OOM",
     6: "HAWKES_ERR_INVALID_DATA",
 }

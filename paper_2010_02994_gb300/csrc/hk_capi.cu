@@ -897,8 +897,6 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream)
         return fail(ctx, HAWKES_ERR_INVALID_DATA,
                     (st & kStNotSorted) ? "times are not sorted although HAWKES_OPT_TIMES_SORTED is set"
                                         : "non-finite location or time, or a negative time");
-    if (st & kStTimeout)
-        return fail(ctx, HAWKES_ERR_TIMEOUT, "a device-side wait timed out");
     if (st & kStZeroRate)
         return fail(ctx, HAWKES_ERR_ZERO_RATE, "some rate lambda_n is zero: ell = -inf, gradient undefined");
     ctx->err.clear();

@@ -49,7 +49,6 @@ constexpr int kThetaParts = 256;  // CTAs of the Theta-gradient reduction
 enum : unsigned {
     kStInvalidData = 1u,
     kStZeroRate = 2u,
-    kStTimeout = 4u,
     kStNotSorted = 8u,
 };
 

@@ -1,5 +1,5 @@
-// hawkes_loglik_noalloc: the log-likelihood of Eq. (1) without any device
-// memory allocation.
+// hawkes_loglik_noalloc: the FP64 log-likelihood of hawkes_loglik without any
+// device memory allocation (the paper has no counterpart of this entry point).
 //
 // Some callers cannot call cudaMalloc: code that runs inside a framework or
 // plugin host that owns every device allocation (a custom allocator or memory
@@ -15,6 +15,7 @@
 // term merged into one exp, partial sums added in a fixed order.  Times need
 // not be sorted (each ordered pair applies the indicators of Section 2.1
 // directly), so no sort and no other scratch is needed.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,7 +27,6 @@ namespace {
 
 constexpr int kTile = 128;      // rows per CTA and columns per staged tile
 constexpr int kMaxSplit = 16;   // column splits
-constexpr int kMaxDevices = 64;
 constexpr int kMaxDim = 8;
 constexpr int kFinishThreads = 1024;
 constexpr size_t kScratchDoubles = (size_t)kMaxSplit * HAWKES_NOALLOC_MAX_N + 32;
@@ -35,24 +35,80 @@ constexpr size_t kScratchDoubles = (size_t)kMaxSplit * HAWKES_NOALLOC_MAX_N + 32
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on `dev` (the current device),
-// looked up once per device.  In host code the array's name only stands in
-// for the symbol; kernels must be given this address.
-hawkes_status scratch_on_device(int dev, double **out)
+// The scratch array's device address belongs to the CUDA context that loaded
+// the library's module: the primary context of a device, a context that the
+// host program created itself on the same device, or the primary context
+// created again after cudaDeviceReset all have their own copy.  So the
+// address is cached per context, keyed by the context's ID (unique for the
+// life of the process), not per device number.  The driver entry points are
+// fetched through the runtime, so the library needs no link to libcuda.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+constexpr int kMaxContexts = 64;
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+ScratchEntry g_cache[kMaxContexts] = {};
+int g_cached = 0;
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+bool g_entry_points_tried = false;
+
+// ID of the calling thread's current context; false if there is none (or the
+// driver offers no cuCtxGetId), in which case nothing is cached.
+bool current_context_id(unsigned long long *id)
+{
+    if (!g_entry_points_tried) {
+        g_entry_points_tried = true;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        cudaGetLastError();
+    }
+    if (!g_get_current || !g_get_id)
+        return false;
+    CUcontext c = nullptr;
+    if (g_get_current(&c) != CUDA_SUCCESS || !c)
+        return false;
+    return g_get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the calling thread's current
+// context (its device is current), looked up once per context.  In host
+// code the array's name only stands in for the symbol; kernels must be
+// given this address.
+hawkes_status scratch_in_current_context(double **out)
 {
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return HAWKES_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<double *>(p);
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (have_id)
+        for (int k = 0; k < g_cached; ++k)
+            if (g_cache[k].ctx_id == id) {
+                *out = g_cache[k].ptr;
+                return HAWKES_OK;
+            }
+    // the lookup also makes the device's primary context current if no
+    // context was current yet
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return HAWKES_ERR_CUDA;
     }
-    *out = g_scratch_ptr[dev];
+    if (!have_id)
+        have_id = current_context_id(&id);
+    if (have_id && g_cached < kMaxContexts)
+        g_cache[g_cached++] = {id, static_cast<double *>(p)};
+    *out = static_cast<double *>(p);
     return HAWKES_OK;
 }
 
@@ -198,10 +254,10 @@ extern "C" hawkes_status hawkes_loglik_noalloc(const double *t, const double *X,
         if (!(x > 0.0) || !std::isfinite(x))
             return HAWKES_ERR_INVALID_ARG;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    if (cudaGetDevice(&dev) != cudaSuccess)
         return HAWKES_ERR_CUDA;
     double *scratch = nullptr;
-    hawkes_status st = scratch_on_device(dev, &scratch);
+    hawkes_status st = scratch_in_current_context(&scratch);
     if (st != HAWKES_OK)
         return st;
     double *part = scratch;

@@ -313,6 +313,47 @@ def pin_theta_zero(o):
     return worst < 1e-12, f"max rel err {worst:.3e}"
 
 
+def pin_theta_score_scale(o):
+    """The magnitude scale of the Theta score (the tolerance scale of the GPU
+    comparisons): each component sums the same pieces as the score, with
+    absolute values, so score and scale differ by twice the pieces of one
+    sign.  Those are fixed by the background and self-excitation parts of
+    lambda_n (M_n, Xi_n, pinned by rate_parts) and by closed forms with
+    scipy's Phi:
+      mu0:   scale - g = 2 sum [Phi(a/tau_t) - Phi(-t/tau_t)],  scale + g = 2 sum M/(mu0 lambda)
+      tau_x: (scale - g) tau_x = 2 D sum M/lambda
+      tau_t: (scale - g) tau_t = 2 sum M/lambda
+      theta: scale - g = 2 sum [1 - e^(-omega a)],             scale + g = 2 sum Xi/(theta lambda)
+      omega: (scale + g) omega = 2 sum Xi/lambda
+      h:     (scale - g) h = 2 D sum Xi/lambda
+    and the scale bounds |g| in every component."""
+    worst = 0.0
+    bound_ok = True
+    for seed, n, d in ((41, 30, 2), (42, 25, 3), (43, 40, 1)):
+        w = synth.random_case(seed, n, d, shuffle=True, ties=1)
+        P = w.params
+        lam, M, Xi = o.rates(w.t, w.X, P, parts=True)
+        g, sc = o.grad_params_scaled(w.t, w.X, P, lam)
+        g_plain = o.grad_params(w.t, w.X, P, lam)
+        bound_ok &= bool(np.array_equal(g, g_plain)) and bool(np.all(sc >= np.abs(g) * (1 - 1e-14)))
+        T = w.t.max()
+        a = T - w.t
+        Sphi = float(np.sum(stats.norm.cdf(a / P["tau_t"]) - stats.norm.cdf(-w.t / P["tau_t"])))
+        SM, SX = float(np.sum(M / lam)), float(np.sum(Xi / lam))
+        S1 = float(np.sum(1.0 - np.exp(-P["omega"] * a)))
+        checks = [
+            (sc[0] - g[0], 2 * Sphi), (sc[0] + g[0], 2 * SM / P["mu0"]),
+            ((sc[1] - g[1]) * P["tau_x"], 2 * d * SM),
+            ((sc[2] - g[2]) * P["tau_t"], 2 * SM),
+            (sc[3] - g[3], 2 * S1), (sc[3] + g[3], 2 * SX / P["theta"]),
+            ((sc[4] + g[4]) * P["omega"], 2 * SX),
+            ((sc[5] - g[5]) * P["h"], 2 * d * SX),
+        ]
+        for got, ref in checks:
+            worst = max(worst, abs(got - ref) / max(abs(ref), 1e-300))
+    return bound_ok and worst < 1e-12, f"bound {bound_ok}, max rel err {worst:.3e}"
+
+
 def pin_row_subsets(o):
     w = synth.random_case(20, 30, 2, shuffle=True)
     lam = o.rates(w.t, w.X, w.params)
@@ -607,6 +648,7 @@ ALL_PINS = {
     "euler": pin_euler,
     "permutation": pin_permutation,
     "theta_zero": pin_theta_zero,
+    "theta_score_scale": pin_theta_score_scale,
     "row_subsets": pin_row_subsets,
     "hmc_reversible": pin_hmc_reversible,
     "hmc_energy_order": pin_hmc_energy_order,

@@ -97,18 +97,41 @@ def c5_reference():
     ell = float(np.sum(np.log(lam)) - np.sum(Lam))
     rows = np.sort(np.random.default_rng(5).choice(w.n, size=2000, replace=False))
     g_rows = oracle.grad_rows(w.t, w.X, w.params, lam, rows)
-    return w, ell, rows, g_rows
+    return w, ell, rows, g_rows, lam
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_large_workload_sampled_rows(ctx, c5_reference, prec):
-    w, ell_ref, rows, g_rows = c5_reference
+    w, ell_ref, rows, g_rows, _ = c5_reference
     ell, g = gpu_eval(ctx, w, prec)
     tl, tg = TOL[prec]
     assert abs(ell - ell_ref) / abs(ell_ref) <= tl
     assert rel_l2(g[rows], g_rows) <= tg
     # translation invariance holds at every size: sum_n grad_n = 0
     assert np.all(np.abs(g.sum(axis=0)) <= 1e-6 * np.abs(g).sum(axis=0))
+
+
+@pytest.mark.slow
+def test_large_workload_parameter_gradient(ctx, c5_reference):
+    """The N = 100,000 workload's d ell / d Theta in both precisions against
+    the oracle (all rows), each component within the precision's tolerance
+    relative to the magnitude of the terms it is summed from (the score
+    itself is a sum of N terms of either sign near the data-generating Theta,
+    so it cancels far below that magnitude)."""
+    import torch
+
+    from paper_2010_02994_gb300 import hawkes_loglik_grad_locations
+
+    w, ell_ref, _, _, lam = c5_reference
+    gp_ref, scale = oracle.grad_params_scaled(w.t, w.X, w.params, lam)
+    t = torch.tensor(w.t, device="cuda")
+    X = torch.tensor(w.X, device="cuda")
+    for prec, tol in (("mixed", 1e-6), ("fp64", 1e-12)):
+        ell, _, gp = hawkes_loglik_grad_locations(ctx, t, X, w.params, precision=prec, grad_params=True)
+        err = np.abs(gp.cpu().numpy() - gp_ref) / scale
+        assert np.all(err <= tol), (prec, err, gp.cpu().numpy(), gp_ref)
+        assert abs(ell.item() - ell_ref) <= TOL[prec][0] * abs(ell_ref)
+        print(f"c5 grad_params {prec}: max error / scale {np.max(err):.2e}")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -28,7 +28,10 @@ MUTANTS = {
     "Lambda_decay_dropped": ("p->theta * (exp(-p->omega * a) - 1.0);", "p->theta * (exp(-a) - 1.0);"),
     "Lambda_lower_limit_dropped": ("(Phi(a / p->tau_t) - Phi(-t[i] / p->tau_t))", "(Phi(a / p->tau_t) - 0.5)"),
     "window_end_is_last_not_max": ("        if (t[i] > T)\n            T = t[i];\n", ""),
-    "theta_grad_Phi_term_dropped": ("nadd(&s[0], -(Phi(a_ / tt) - Phi(-t[i] / tt)));", ""),
+    "theta_grad_Phi_term_dropped": ("double l0 = -(Phi(a_ / tt) - Phi(-t[i] / tt));", "double l0 = 0.0;"),
+    "theta_scale_Lambda_part_dropped": ("            nadd(&sm[3], fabs(l3));\n", ""),
+    "theta_scale_piece_sign": ("nadd(&b[1], mu * (r2 / (tx * tx * tx) + (double)d / tx));",
+                               "nadd(&b[1], mu * (r2 / (tx * tx * tx) - (double)d / tx));"),
     "omega_grad_sign": ("nadd(&a[4], xi * (1.0 / w - dt));", "nadd(&a[4], xi * (1.0 / w + dt));"),
     "tau_t_grad_boundary_term_dropped": ("phi_d(t[i] * t[i] / (tt * tt), 1) * t[i]) /", "0.0) /"),
     "rate_parts_swapped": ("nadd(&s_mu, mu);\n        nadd(&s_xi, xi);", "nadd(&s_mu, xi);\n        nadd(&s_xi, mu);"),
