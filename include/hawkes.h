@@ -106,7 +106,15 @@ const char *hawkes_last_error(const hawkes_ctx *ctx);
 hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
 
 /* Tuning and profiling options (hawkes_ctx_set_option):
- *   HAWKES_OPT_BLOCK_WARPS   warps per CTA of the pair kernels (0 = tuned)
+ *   HAWKES_OPT_BLOCK_WARPS   row groups of warps per CTA of the mixed pair
+ *                            kernels, which set the pair block size (32 x
+ *                            rows-per-lane x row groups events; 0 = tuned)
+ *   HAWKES_OPT_COL_GROUPS    column groups of warps per CTA of the rate and
+ *                            gradient passes, which split each pair block's
+ *                            columns (1, 2 or 4, with row groups x column
+ *                            groups <= 8; 0 = chosen per pass: the most that
+ *                            keep blocks x warps within 48 per SM, so that
+ *                            small problems still fill the SMs with warps)
  *   HAWKES_OPT_CTAS_PER_SM   persistent CTAs per SM (0 = occupancy limit)
  *   HAWKES_OPT_PROFILE       1: time every pair-kernel launch with events
  *   HAWKES_OPT_TIMES_SORTED  1: the caller promises t is non-decreasing and
@@ -134,13 +142,15 @@ enum {
     HAWKES_OPT_TIMES_SORTED = 4,
     HAWKES_OPT_MIXED_FIXUP_EXP = 5,
     HAWKES_OPT_SKIP_FAR_BLOCKS = 6,
-    HAWKES_OPT_FP64_ORDERED = 7
+    HAWKES_OPT_FP64_ORDERED = 7,
+    HAWKES_OPT_COL_GROUPS = 8
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 
 /* Kernel timing collected while HAWKES_OPT_PROFILE is on (waits for the
  * recorded events).  kernel: 0 = rate pass (lambda row sums), 1 = gradient
- * pass, 2 = validation + time sort + packing, 3 = rate finalization (ell),
+ * pass, 2 = validation + time sort + packing, 3 = rate finalization (ell,
+ * with the FP64 recompute of rows whose mixed-precision rate underflows),
  * 4 = gradient finalization.  Returns the summed device time in ms, the
  * number of launches and the number of unordered event pairs those launches
  * processed (0 for stages 2-4). */
@@ -157,22 +167,28 @@ hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64
 /* ----------------------------------------------------------- autotuner -- */
 
 /* Tile shape of the mixed pair kernels for one dimension d and one size
- * bucket (bucket = ceil(log2 n)): warps per CTA (1, 2, 4 or 8; the pair block
- * is 32 x rows-per-lane x warps events square) and the cap on persistent CTAs
+ * bucket (bucket = ceil(log2 n)): row groups of warps per CTA (1, 2, 4 or 8;
+ * the pair block is 32 x rows-per-lane x row groups events square), column
+ * groups (1, 2 or 4, splitting the block's columns over more warps; 0 =
+ * chosen per pass as for HAWKES_OPT_COL_GROUPS; row groups x column groups
+ * <= 8) and the cap on persistent CTAs
  * per SM (0 = as many as fit).  Entries set here or found by hawkes_autotune
- * are used whenever HAWKES_OPT_BLOCK_WARPS / HAWKES_OPT_CTAS_PER_SM are 0. */
-hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t ctas_per_sm);
+ * are used whenever HAWKES_OPT_BLOCK_WARPS / HAWKES_OPT_CTAS_PER_SM are 0
+ * and the entry still leaves three pair blocks per SM at the call's size. */
+hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t col_groups,
+                                    int32_t ctas_per_sm);
 hawkes_status hawkes_ctx_get_tuning(const hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t *warps,
-                                    int32_t *ctas_per_sm);
+                                    int32_t *col_groups, int32_t *ctas_per_sm);
 
-/* Time every tile shape for the caller's data (t, X as in
- * hawkes_loglik_grad_locations; mixed precision) with CUDA events on
- * `stream`, store the fastest for (d, bucket of n) in the context, and
- * return it.  Synchronizes the stream; out_ms (nullable) receives the
- * fastest evaluation time. */
+/* Time every tile shape (row groups, column groups, CTA cap) for the
+ * caller's data (t, X as in hawkes_loglik_grad_locations; mixed precision)
+ * with CUDA events on `stream`, store the fastest for (d, bucket of n) in
+ * the context, and return it.  The options it sets while timing are put
+ * back.  Allocates (and frees) one output buffer and synchronizes the
+ * stream; out_ms (nullable) receives the fastest evaluation time. */
 hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
                               const hawkes_params *params, hawkes_stream stream, int32_t *best_warps,
-                              int32_t *best_ctas_per_sm, double *out_ms);
+                              int32_t *best_col_groups, int32_t *best_ctas_per_sm, double *out_ms);
 
 /* ------------------------------------------------------- log-likelihood -- */
 

@@ -23,7 +23,7 @@ STATUS_NAMES = {
 }
 PREC = {"mixed": 0, "fp64": 1}
 OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5,
-           "skip_far_blocks": 6, "fp64_ordered": 7}
+           "skip_far_blocks": 6, "fp64_ordered": 7, "col_groups": 8}
 
 # every function declared in include/hawkes.h
 EXPORTED = (
@@ -123,11 +123,11 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                                                 dp]
     lib.hawkes_batch_hmc_trajectory.restype = st
     ip = ctypes.POINTER(i32)
-    lib.hawkes_ctx_set_tuning.argtypes = [vp, i32, i32, i32, i32]
+    lib.hawkes_ctx_set_tuning.argtypes = [vp, i32, i32, i32, i32, i32]
     lib.hawkes_ctx_set_tuning.restype = st
-    lib.hawkes_ctx_get_tuning.argtypes = [vp, i32, i32, ip, ip]
+    lib.hawkes_ctx_get_tuning.argtypes = [vp, i32, i32, ip, ip, ip]
     lib.hawkes_ctx_get_tuning.restype = st
-    lib.hawkes_autotune.argtypes = [vp, dp, dp, i64, i32, pp, vp, ip, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.hawkes_autotune.argtypes = [vp, dp, dp, i64, i32, pp, vp, ip, ip, ip, ctypes.POINTER(ctypes.c_double)]
     lib.hawkes_autotune.restype = st
     lib.hawkes_loglik_noalloc.argtypes = [dp, dp, i64, i32, pp, vp, dp]
     lib.hawkes_loglik_noalloc.restype = st

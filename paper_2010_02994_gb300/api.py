@@ -70,9 +70,10 @@ class HawkesContext:
             _tuning.load_into(self)
 
     def get_tuning(self, d: int, bucket: int):
-        w, c = ctypes.c_int32(), ctypes.c_int32()
-        self.check(self.lib.hawkes_ctx_get_tuning(self.handle, int(d), int(bucket), ctypes.byref(w), ctypes.byref(c)))
-        return {"warps": w.value, "ctas_per_sm": c.value}
+        w, wc, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self.check(self.lib.hawkes_ctx_get_tuning(self.handle, int(d), int(bucket), ctypes.byref(w), ctypes.byref(wc),
+                                                  ctypes.byref(c)))
+        return {"warps": w.value, "col_groups": wc.value, "ctas_per_sm": c.value}
 
     def close(self):
         if getattr(self, "handle", None):

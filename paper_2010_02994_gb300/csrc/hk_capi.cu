@@ -70,7 +70,7 @@ struct Plan {
     std::vector<int64_t> set_ev0;        // nsets+1
     std::vector<int64_t> set_row0;       // nsets+1
     std::vector<std::pair<int, int>> item_range_by_d;  // [d] -> (first, count)
-    std::vector<int> warps_by_d;
+    std::vector<int> wr_by_d, wc_by_d;  // pair-kernel shape per dimension: row groups, column groups (0 = per pass)
     int64_t n_total = 0, x_total = 0, total_rows = 0, total_rec4 = 0, total_P1 = 0, total_P2 = 0;
     int64_t total_F1 = 0, total_F2 = 0;
     int32_t total_segs = 0, max_fsplit = 1;
@@ -97,7 +97,7 @@ struct hawkes_ctx {
     DeviceBuffer bmds_ws;  // BMDS partial-sum slots
     DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
     // options
-    int opt_warps = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
+    int opt_warps = 0, opt_cols = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
     int opt_fp64_ordered = 0;
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
@@ -110,9 +110,11 @@ struct hawkes_ctx {
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxD + 1] = {};
     cudaStream_t bmds_side = nullptr;  // the BMDS branch of a BMDS-Hawkes leapfrog step
     cudaEvent_t bmds_fork = nullptr, bmds_join = nullptr;
-    int occ[kMaxD + 1][5][9] = {};  // CTAs per SM of the pair kernels: [d][pass 1..4][warps]
+    // CTAs per SM of the pair kernels: [d][pass 1..4][log2 wr][log2 wc] (-1: not yet asked)
+    int occ[kMaxD + 1][5][4][4];
     static constexpr int kBuckets = 32;
-    int tune_warps[kMaxD + 1][kBuckets] = {};  // 0: no entry
+    int tune_warps[kMaxD + 1][kBuckets] = {};  // row groups; 0: no entry
+    int tune_cols[kMaxD + 1][kBuckets] = {};   // column groups
     int tune_ctas[kMaxD + 1][kBuckets] = {};
     int cur_ctas_by_d[kMaxD + 1] = {};         // CTA cap per dimension for the current plan
     std::vector<char> uploaded;     // bytes of the plan last copied to the device
@@ -171,31 +173,82 @@ int size_bucket(int64_t n)
     return b;
 }
 
-int choose_warps(const hawkes_ctx *ctx, int64_t n, int d, bool theta)
+int ilog2_small(int v) { return v >= 8 ? 3 : v >= 4 ? 2 : v >= 2 ? 1 : 0; }
+
+// CTAs of shape (wr, wc) that fit on one SM for pass `pass` in d dimensions
+// (asked from the runtime once, then cached; 0 if the shape does not fit).
+int occupancy(hawkes_ctx *ctx, int d, int pass, int wr, int wc)
 {
-    if (ctx->opt_warps > 0)
-        return ctx->opt_warps;
+    int &o = ctx->occ[d][pass][ilog2_small(wr)][ilog2_small(wc)];
+    if (o < 0)
+        o = pass_max_ctas_per_sm(d, pass, wr, wc);
+    return o;
+}
+
+// A shape (wr row groups, wc column groups) is valid when it has at most 8
+// warps, every column group sweeps whole 32-column chunks, and its shared
+// memory lets it run (and, without `tuned`, leaves room for two CTAs per SM).
+bool shape_ok(hawkes_ctx *ctx, int d, int wr, int wc, bool theta, size_t smem_cap)
+{
+    if (wr * wc > 8 || wc > 4 || wc > rows_per_lane(d) * wr)
+        return false;
+    if (pass_smem_bytes(d, 2, wr, wc) > smem_cap || (theta && pass_smem_bytes(d, 3, wr, wc) > smem_cap))
+        return false;
+    return occupancy(ctx, d, 2, wr, wc) > 0 && (!theta || occupancy(ctx, d, 3, wr, wc) > 0);
+}
+
+// Pair-kernel shape for sets of up to n events in d dimensions: row groups
+// (the block size B = 32 rows_per_lane(d) wr is the largest that still gives
+// every SM several pair blocks, at least three per SM in all) and column
+// groups (0: chosen per pass by pass_cols).  An explicit option, or a tuned
+// entry that still gives three blocks per SM at this size, takes precedence.
+void choose_shape(hawkes_ctx *ctx, int64_t n, int d, bool theta, int &wr_out, int &wc_out)
+{
     const int R = rows_per_lane(d);
     auto items_for = [&](int wv) {
         const int64_t B = 32LL * R * wv;
         const int64_t T = (n + B - 1) / B;
         return T * (T + 1) / 2;
     };
-    // a tuned shape (measured at one size of its octave) is kept only while
-    // it leaves at least three pair blocks per SM at this size
-    const int tw = ctx->tune_warps[d][size_bucket(n)];
-    if (tw > 0 && pass_smem_bytes(d, 2, tw) <= 200 * 1024 &&
-        (!theta || pass_smem_bytes(d, 3, tw) <= 200 * 1024) && items_for(tw) >= 3LL * ctx->sm_count)
-        return tw;
-    const int candidates[4] = {8, 4, 2, 1};
-    for (int wv : candidates) {
-        // shared memory per CTA must leave room for two CTAs per SM
-        if (pass_smem_bytes(d, 2, wv) > 110 * 1024 || (theta && pass_smem_bytes(d, 3, wv) > 110 * 1024))
-            continue;
-        if (items_for(wv) >= 3LL * ctx->sm_count)
-            return wv;
+    wc_out = ctx->opt_cols;
+    if (ctx->opt_warps > 0) {
+        wr_out = ctx->opt_warps;
+        return;
     }
-    return 1;
+    const int tw = ctx->tune_warps[d][size_bucket(n)], tc = ctx->tune_cols[d][size_bucket(n)];
+    if (tw > 0 && shape_ok(ctx, d, tw, std::max(1, tc), theta, 200 * 1024) && items_for(tw) >= 3LL * ctx->sm_count) {
+        wr_out = tw;
+        if (wc_out == 0)
+            wc_out = tc;
+        return;
+    }
+    for (int wv : {8, 4, 2, 1}) {
+        if (!shape_ok(ctx, d, wv, 1, theta, 110 * 1024))
+            continue;
+        if (items_for(wv) >= 3LL * ctx->sm_count || wv == 1) {
+            wr_out = wv;
+            return;
+        }
+    }
+    wr_out = 1;
+}
+
+// Column groups of one pair pass with wr row groups over nitems blocks: the
+// most (1, 2 or 4; only the rate and gradient passes split columns) that
+// keep the warp tasks (blocks x warps) within 48 per SM.  At small N this
+// gives the SMs more warps than one warp row per block would (at N = 1e4,
+// D = 2 both passes measured fastest with four); at large N the blocks alone
+// fill the SMs and the row groups already take all eight warps.
+int pass_cols(hawkes_ctx *ctx, int d, int pass, int wr, int64_t nitems)
+{
+    if (pass != 1 && pass != 2)
+        return 1;
+    int best = 1;
+    for (int wc = 2; wc <= 4; wc *= 2)
+        if (shape_ok(ctx, d, wr, wc, false, 110 * 1024) && occupancy(ctx, d, pass, wr, wc) > 0 &&
+            nitems * wr * wc <= 48LL * ctx->sm_count)
+            best = wc;
+    return best;
 }
 
 // Fill the derived fields of one set.
@@ -220,8 +273,11 @@ void describe_set(SetDesc &S, int64_t n, int d, const hawkes_params &p, double f
     const double cxi1 = std::log2(p.theta * p.omega * std::pow(p.tau_x, d) * p.tau_t * std::sqrt(kTwoPi) /
                                   (p.mu0 * std::pow(p.h, d)));
     S.rho = (float)rho;
-    S.kappa = (float)(p.omega * kLog2e / S.kt);
+    const double kappa = p.omega * kLog2e / S.kt;
+    S.kappa = (float)kappa;
+    S.kappa_lo = (float)(kappa - (double)S.kappa);
     S.cxi1 = (float)cxi1;
+    S.cxi1_lo = (float)(cxi1 - (double)S.cxi1);
     S.cxi2 = (float)(cxi1 + std::log2(rho));
     S.cxi2_d = cxi1 + std::log2(rho);
     S.s_min = std::ldexp(1.0, (int)fixup_exp);
@@ -242,14 +298,15 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
     pl.set_ev0.resize(nsets + 1);
     pl.set_row0.resize(nsets + 1);
     pl.item_range_by_d.assign(kMaxD + 1, {0, 0});
-    pl.warps_by_d.assign(kMaxD + 1, 0);
+    pl.wr_by_d.assign(kMaxD + 1, 0);
+    pl.wc_by_d.assign(kMaxD + 1, 0);
     // the block size is chosen per dimension from the largest set of that dimension
     std::vector<int64_t> nmax_by_d(kMaxD + 1, 0);
     for (int s = 0; s < nsets; ++s)
         nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
     for (int d = 1; d <= kMaxD; ++d)
         if (nmax_by_d[d] > 0) {
-            pl.warps_by_d[d] = choose_warps(ctx, nmax_by_d[d], d, theta);
+            choose_shape(ctx, nmax_by_d[d], d, theta, pl.wr_by_d[d], pl.wc_by_d[d]);
             ctx->cur_ctas_by_d[d] = ctx->tune_ctas[d][size_bucket(nmax_by_d[d])];
         }
     // FP64: the symmetric kernels keep one partial slot per row block and
@@ -274,7 +331,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         if (!fp64 && !mixed_range_ok(S))
             return fail(ctx, HAWKES_ERR_INVALID_ARG,
                         "parameters outside the range of the mixed-precision path; use HAWKES_PREC_FP64");
-        const int B = fp64 ? (pl.fp64_sym ? kSymRows : kFp64Rows) : 32 * rows_per_lane(d) * pl.warps_by_d[d];
+        const int B = fp64 ? (pl.fp64_sym ? kSymRows : kFp64Rows) : 32 * rows_per_lane(d) * pl.wr_by_d[d];
         S.B = B;
         S.nblk = (int32_t)((n + B - 1) / B);
         S.npad = S.nblk * B;
@@ -384,6 +441,7 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
         c.take<double>(pl.total_rows * kMaxD);
     c.take<double>((4 + kEnergyParts) * ns + 8);
     c.take<int32_t>(2 * ns + 8);
+    c.take<int32_t>(ns);
     return c.off + 256;
 }
 
@@ -462,6 +520,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     ctx->hhi = c.take<double>(pl.total_rows * kMaxD);
     ctx->hscal = c.take<double>((4 + kEnergyParts) * ns + 8);
     ctx->hint = c.take<int32_t>(2 * ns + 8);
+    w.set_done = c.take<int32_t>(ns);
     w.set_flags = ctx->ctl + kCtlSetFlags;
     w.set_cmmax = ctx->ctl + kCtlSetFlags + ctx->ctl_sets;
     w.skip_far = ctx->opt_skip;
@@ -484,6 +543,9 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     if (bytes == ctx->uploaded)
         return HAWKES_OK;
     ctx->uploaded.swap(bytes);
+    // the per-set segment tickets start at zero and every evaluation leaves
+    // them at zero; a new layout clears them once
+    HK_TRY(cudaMemsetAsync(w.set_done, 0, sizeof(int32_t) * ns, stream), "clear tickets");
     HK_TRY(cudaMemcpyAsync(ctx->d_sets, pl.sets.data(), sizeof(SetDesc) * ns, cudaMemcpyHostToDevice, stream),
            "upload set descriptors");
     if (!pl.items.empty())
@@ -499,9 +561,9 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     return HAWKES_OK;
 }
 
-int persistent_grid(hawkes_ctx *ctx, int d, int pass, int warps, int nitems)
+int persistent_grid(hawkes_ctx *ctx, int d, int pass, int wr, int wc, int nitems)
 {
-    int per_sm = ctx->occ[d][pass][warps];
+    int per_sm = occupancy(ctx, d, pass, wr, wc);
     if (ctx->opt_ctas > 0)
         per_sm = std::min(per_sm, ctx->opt_ctas);
     else if (ctx->cur_ctas_by_d[d] > 0)
@@ -557,22 +619,11 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
     return HAWKES_OK;
 }
 
-// Reset the per-evaluation control words (used between HMC evaluations).
-hawkes_status enqueue_eval_reset(hawkes_ctx *ctx, const Plan &pl, cudaStream_t s)
-{
-    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0,
-                           sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + pl.sets.size()), s),
-           "reset control words");
-    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlSetFlags + ctx->ctl_sets, 0, sizeof(int32_t) * pl.sets.size(), s),
-           "reset bounds");
-    return HAWKES_OK;
-}
-
-// One pair pass (1 rates, 2 gradient, 3 rates with Theta sums) over every
-// dimension of the plan.  Each dimension is one persistent launch with its
-// own work counter; with several dimensions the launches run concurrently
-// on forked streams (joined back into s), so that the GPU fills one
-// dimension's tail with another's blocks.
+// One pair pass (1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with
+// the self-excitation sums apart) over every dimension of the plan.  Each
+// dimension is one persistent launch with its own work counter; with several
+// dimensions the launches run concurrently on forked streams (joined back
+// into s), so that the GPU fills one dimension's tail with another's blocks.
 hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaStream_t s)
 {
     int ndims = 0;
@@ -593,24 +644,19 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
         const auto rg = pl.item_range_by_d[d];
         if (rg.second == 0)
             continue;
-        const int warps = pl.warps_by_d[d];
-        const int grid = persistent_grid(ctx, d, pass, warps, rg.second);
+        const int wr = pl.wr_by_d[d];
+        const int wc = (pass == 1 || pass == 2) && pl.wc_by_d[d] > 0 ? pl.wc_by_d[d] : pass_cols(ctx, d, pass, wr, rg.second);
+        const int grid = persistent_grid(ctx, d, pass, wr, wc, rg.second);
         Work wd = ctx->w;
-        wd.counters = ctx->ctl + kCtlDimCounters + 2 * d;  // [0] work taken, [1] CTAs done
+        wd.pair_ctr = ctx->ctl + kCtlDimCounters + 2 * d;  // [0] work taken, [1] CTAs done
         cudaStream_t ls = s;
         if (fork) {
             ls = ctx->side[d];
             HK_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev, 0), "fork wait");
         }
         const WorkItem *items = ctx->d_items + rg.first;
-        if (pass == 1)
-            HK_TRY(launch_pass1_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
-        else if (pass == 3)
-            HK_TRY(launch_pass1_theta_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
-        else if (pass == 4)
-            HK_TRY(launch_pass1_xi_mixed(d, wd, items, rg.second, grid, warps, ls), "rate pass");
-        else
-            HK_TRY(launch_pass2_mixed(d, wd, items, rg.second, grid, warps, ls), "gradient pass");
+        HK_TRY(launch_pair_pass_mixed(pass, d, wd, items, rg.second, grid, wr, wc, ls),
+               pass == 2 ? "gradient pass" : "rate pass");
         if (fork) {
             HK_TRY(cudaEventRecord(ctx->join_ev[d], ls), "join");
             HK_TRY(cudaStreamWaitEvent(s, ctx->join_ev[d], 0), "join wait");
@@ -657,65 +703,49 @@ hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool 
     return HAWKES_OK;
 }
 
-// Pass 1 .. ell (and pass 2 .. gradient) on packed rows.
+// Pass 1 .. ell (and pass 2 .. gradient) on packed rows:
+//   rate pass (with the six Theta sums when wanted), finalize rows (rates,
+//   FP64 recompute of flagged rows, ell per set), Theta gradient, gradient
+//   pass, finalize gradient.
 hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
                            double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr)
 {
     const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
-    const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
     int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
         ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
-    if (fp64)
-        ctx->launches_own += (want_grad ? 3 : 2) + (want_grad ? 2 : 1) * fp64_pass_launches(pl);
-    else
-        ctx->launches_own += want_grad ? 2 * ndims + 4 : ndims + 2;
-    if (fp64) {
-        hawkes_status st = enqueue_fp64_pass(ctx, pl, 1, theta, s);
-        if (st != HAWKES_OK)
-            return st;
-        HK_TRY(launch_finalize_rows(w, pl.total_segs, true, theta ? kSumsTheta : kSumsNone, s), "finalize rows");
-        HK_TRY(launch_fixup_rows(w, pl.total_segs, 1, out_loglik, false, s), "log-likelihood");
-        if (want_grad) {
-            if ((st = enqueue_fp64_pass(ctx, pl, 2, false, s)) != HAWKES_OK)
-                return st;
-            HK_TRY(launch_finalize_grad(w, pl.total_segs, true, out_grad, g_sorted, s), "finalize gradient");
-        }
-        if (theta) {
-            ++ctx->launches_own;
-            HK_TRY(launch_theta_grad(w, pl.n_total, out_grad_params, s), "parameter gradient");
-        }
-        return HAWKES_OK;
-    }
+    const int pass_launches = fp64 ? fp64_pass_launches(pl) : ndims;
+    ctx->launches_own += (want_grad ? 2 : 1) * (pass_launches + 1) + (theta ? 2 : 0);
+    hawkes_status st;
     {
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 0, pl.pairs);
-        hawkes_status st = enqueue_pair_pass(ctx, pl, theta ? 3 : 1, s);
+        st = fp64 ? enqueue_fp64_pass(ctx, pl, 1, theta, s) : enqueue_pair_pass(ctx, pl, theta ? 3 : 1, s);
         if (st != HAWKES_OK)
             return st;
         if (ctx->opt_profile)
             prof_end(ctx, s, pe);
     }
-    ProfEvent pf{};
-    if (ctx->opt_profile)
-        prof_begin(ctx, s, pf, 3, 0.0);
-    HK_TRY(launch_finalize_rows(w, pl.total_segs, false, theta ? kSumsTheta : kSumsNone, s), "finalize rows");
-    HK_TRY(launch_fixup_rows(w, pl.total_segs, fix_grid, out_loglik, theta, s), "FP64 rate fixup");
-    if (ctx->opt_profile)
-        prof_end(ctx, s, pf);
-    if (theta) {
-        ++ctx->launches_own;
-        HK_TRY(launch_theta_grad(w, pl.n_total, out_grad_params, s), "parameter gradient");
+    {
+        ProfEvent pf{};
+        if (ctx->opt_profile)
+            prof_begin(ctx, s, pf, 3, 0.0);
+        HK_TRY(launch_finalize_rows(w, pl.total_segs, fp64, theta ? kSumsTheta : kSumsNone, out_loglik, s),
+               "finalize rows");
+        if (ctx->opt_profile)
+            prof_end(ctx, s, pf);
     }
+    if (theta)
+        HK_TRY(launch_theta_grad(w, pl.n_total, out_grad_params, s), "parameter gradient");
     if (!want_grad)
         return HAWKES_OK;
     {
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 1, pl.pairs);
-        hawkes_status st = enqueue_pair_pass(ctx, pl, 2, s);
+        st = fp64 ? enqueue_fp64_pass(ctx, pl, 2, false, s) : enqueue_pair_pass(ctx, pl, 2, s);
         if (st != HAWKES_OK)
             return st;
         if (ctx->opt_profile)
@@ -724,8 +754,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     ProfEvent pg{};
     if (ctx->opt_profile)
         prof_begin(ctx, s, pg, 4, 0.0);
-    HK_TRY(launch_finalize_grad(w, pl.total_segs, false, out_grad, g_sorted, s), "finalize gradient");
-    HK_TRY(launch_fixup_grad(w, pl.total_segs, fix_grid, out_grad, g_sorted, s), "FP64 gradient fixup");
+    HK_TRY(launch_finalize_grad(w, pl.total_segs, fp64, out_grad, g_sorted, s), "finalize gradient");
     if (ctx->opt_profile)
         prof_end(ctx, s, pg);
     return HAWKES_OK;
@@ -819,14 +848,13 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
         return HAWKES_ERR_OOM;
     }
     ctx->ctl_sets = 64;
+    // occupancy of every pair-kernel shape, asked now (it also sets each
+    // kernel's shared-memory limit) rather than during a stream capture
     for (int d = 1; d <= kMaxD; ++d)
-        for (int pass = 1; pass <= 2; ++pass)
-            for (int wv : {1, 2, 4, 8})
-                ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
-    for (int d = 1; d <= kMaxD; ++d)
-        for (int pass = 3; pass <= 4; ++pass)
-            for (int wv : {1, 2, 4, 8})
-                ctx->occ[d][pass][wv] = pass_max_ctas_per_sm(d, pass, wv);
+        for (int pass = 1; pass <= 4; ++pass)
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b)
+                    ctx->occ[d][pass][a][b] = (1 << (a + b)) <= 8 ? pass_max_ctas_per_sm(d, pass, 1 << a, 1 << b) : 0;
     Plan pl;
     hawkes_params p{1, 1, 1, 1, 1, 1};
     const int64_t n64 = max_n;
@@ -913,6 +941,11 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
             return fail(ctx, HAWKES_ERR_INVALID_ARG, "block warps must be 0, 1, 2, 4 or 8");
         ctx->opt_warps = (int)value;
         return HAWKES_OK;
+    case HAWKES_OPT_COL_GROUPS:
+        if (value != 0 && value != 1 && value != 2 && value != 4)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "column groups must be 0, 1, 2 or 4");
+        ctx->opt_cols = (int)value;
+        return HAWKES_OK;
     case HAWKES_OPT_CTAS_PER_SM:
         if (value < 0 || value > 32)
             return fail(ctx, HAWKES_ERR_INVALID_ARG, "CTAs per SM must be in [0, 32]");
@@ -992,26 +1025,32 @@ hawkes_status hawkes_ctx_launch_count(const hawkes_ctx *ctx, int64_t *own, int64
     return HAWKES_OK;
 }
 
-hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t ctas_per_sm)
+hawkes_status hawkes_ctx_set_tuning(hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t warps, int32_t col_groups,
+                                    int32_t ctas_per_sm)
 {
     if (!ctx)
         return HAWKES_ERR_INVALID_ARG;
-    if (d < 1 || d > kMaxD || bucket < 0 || bucket >= hawkes_ctx::kBuckets ||
-        !(warps == 0 || warps == 1 || warps == 2 || warps == 4 || warps == 8) || ctas_per_sm < 0 ||
-        ctas_per_sm > 32)
+    auto pow2_le8 = [](int32_t v) { return v == 1 || v == 2 || v == 4 || v == 8; };
+    if (d < 1 || d > kMaxD || bucket < 0 || bucket >= hawkes_ctx::kBuckets || !(warps == 0 || pow2_le8(warps)) ||
+        !(col_groups == 0 || (pow2_le8(col_groups) && col_groups <= 4)) ||
+        (int64_t)warps * std::max(1, col_groups) > 8 ||
+        ctas_per_sm < 0 || ctas_per_sm > 32)
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "tuning entry out of range");
     ctx->tune_warps[d][bucket] = warps;
+    ctx->tune_cols[d][bucket] = col_groups;
     ctx->tune_ctas[d][bucket] = ctas_per_sm;
     return HAWKES_OK;
 }
 
 hawkes_status hawkes_ctx_get_tuning(const hawkes_ctx *ctx, int32_t d, int32_t bucket, int32_t *warps,
-                                    int32_t *ctas_per_sm)
+                                    int32_t *col_groups, int32_t *ctas_per_sm)
 {
     if (!ctx || d < 1 || d > kMaxD || bucket < 0 || bucket >= hawkes_ctx::kBuckets)
         return HAWKES_ERR_INVALID_ARG;
     if (warps)
         *warps = ctx->tune_warps[d][bucket];
+    if (col_groups)
+        *col_groups = ctx->tune_cols[d][bucket];
     if (ctas_per_sm)
         *ctas_per_sm = ctx->tune_ctas[d][bucket];
     return HAWKES_OK;
@@ -1066,21 +1105,18 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
         return st;
     if ((st = enqueue_prep(ctx, pl, t, X, s)) != HAWKES_OK)
         return st;
-    const int fix_grid = fp64 ? 1 : std::max(1, 2 * ctx->sm_count);
     if (fp64) {
         if ((st = enqueue_fp64_pass(ctx, pl, 1, true, s)) != HAWKES_OK)
             return st;
-        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, kSumsTheta, s), "finalize rows");
-        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, 1, nullptr, false, s), "log-likelihood");
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, true, kSumsTheta, nullptr, s), "finalize rows");
     } else {
         if ((st = enqueue_pair_pass(ctx, pl, 4, s)) != HAWKES_OK)
             return st;
-        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, kSumsXi, s), "finalize rows");
         // flagged rows get all six sums in FP64, the self-excitation one among them
-        HK_TRY(launch_fixup_rows(ctx->w, pl.total_segs, fix_grid, nullptr, true, s), "FP64 rate fixup");
+        HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, kSumsXi, nullptr, s), "finalize rows");
     }
     HK_TRY(launch_self_excitation(ctx->w, pl.total_segs, out_prob, s), "self-excitation");
-    ctx->launches_own += 4;
+    ctx->launches_own += 3 + (fp64 ? fp64_pass_launches(pl) - 1 : 0);
     return enqueue_nan_on_invalid(ctx, out_prob, n, nullptr, 0, s);
 }
 
@@ -1159,7 +1195,7 @@ hawkes_status hawkes_loglik_grad_locations(hawkes_ctx *ctx, const double *t, con
 
 hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X, int64_t n, int32_t d,
                               const hawkes_params *params, hawkes_stream stream, int32_t *best_warps,
-                              int32_t *best_ctas_per_sm, double *out_ms)
+                              int32_t *best_col_groups, int32_t *best_ctas_per_sm, double *out_ms)
 {
     hawkes_status st = check_common(ctx, t, X, n, d, params, HAWKES_PREC_MIXED);
     if (st != HAWKES_OK)
@@ -1168,40 +1204,46 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     double *out = nullptr;
     HK_TRY(cudaMalloc(&out, sizeof(double) * (1 + n * d)), "autotune output");
-    const int saved_w = ctx->opt_warps, saved_c = ctx->opt_ctas, saved_p = ctx->opt_profile;
+    const int saved_w = ctx->opt_warps, saved_wc = ctx->opt_cols, saved_c = ctx->opt_ctas, saved_p = ctx->opt_profile;
     ctx->opt_profile = 0;
     double best = 1e300;
-    int bw = 0, bc = 0;
+    int bw = 0, bwc = 0, bc = 0;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     for (int wv : {1, 2, 4, 8}) {
-        if (pass_smem_bytes(d, 2, wv) > 200 * 1024)
-            continue;
-        const int max_c = std::max(1, ctx->occ[d][2][wv]);
-        // caps: as many as fit (0), then powers of two below that
-        for (int cv = 0; cv < max_c; cv = cv == 0 ? 1 : 2 * cv) {
-            ctx->opt_warps = wv;
-            ctx->opt_ctas = cv;
-            float ms = 0.0f, tot = 0.0f;
-            st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out, out + 1,
-                                              nullptr);
-            for (int rep = 0; rep < 3 && st == HAWKES_OK; ++rep) {
-                cudaEventRecord(a, s);
-                st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out,
-                                                  out + 1, nullptr);
-                cudaEventRecord(b, s);
-                cudaEventSynchronize(b);
-                cudaEventElapsedTime(&ms, a, b);
-                tot += ms;
+        for (int wc : {0, 1, 2, 4}) {  // 0: column groups chosen per pass
+            if (!shape_ok(ctx, d, wv, std::max(1, wc), false, 200 * 1024))
+                continue;
+            const int max_c = std::max(1, occupancy(ctx, d, 2, wv, std::max(1, wc)));
+            // caps: as many as fit (0), then powers of two below that
+            for (int cv = 0; cv < max_c; cv = cv == 0 ? 1 : 2 * cv) {
+                ctx->opt_warps = wv;
+                ctx->opt_cols = wc;
+                ctx->opt_ctas = cv;
+                float ms = 0.0f, tot = 0.0f;
+                st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out, out + 1,
+                                                  nullptr);
+                for (int rep = 0; rep < 3 && st == HAWKES_OK; ++rep) {
+                    cudaEventRecord(a, s);
+                    st = hawkes_loglik_grad_locations(ctx, t, X, n, d, params, HAWKES_PREC_MIXED, stream, out,
+                                                      out + 1, nullptr);
+                    cudaEventRecord(b, s);
+                    cudaEventSynchronize(b);
+                    cudaEventElapsedTime(&ms, a, b);
+                    tot += ms;
+                }
+                if (st != HAWKES_OK)
+                    break;
+                if (tot / 3.0 < best) {
+                    best = tot / 3.0;
+                    bw = wv;
+                    bwc = wc;
+                    bc = cv;
+                }
             }
             if (st != HAWKES_OK)
                 break;
-            if (tot / 3.0 < best) {
-                best = tot / 3.0;
-                bw = wv;
-                bc = cv;
-            }
         }
         if (st != HAWKES_OK)
             break;
@@ -1209,6 +1251,7 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->opt_warps = saved_w;
+    ctx->opt_cols = saved_wc;
     ctx->opt_ctas = saved_c;
     ctx->opt_profile = saved_p;
     cudaStreamSynchronize(s);
@@ -1218,9 +1261,12 @@ hawkes_status hawkes_autotune(hawkes_ctx *ctx, const double *t, const double *X,
     if (bw == 0)
         return fail(ctx, HAWKES_ERR_INVALID_ARG, "no tile shape fits this dimension");
     ctx->tune_warps[d][size_bucket(n)] = bw;
+    ctx->tune_cols[d][size_bucket(n)] = bwc;
     ctx->tune_ctas[d][size_bucket(n)] = bc;
     if (best_warps)
         *best_warps = bw;
+    if (best_col_groups)
+        *best_col_groups = bwc;
     if (best_ctas_per_sm)
         *best_ctas_per_sm = bc;
     if (out_ms)
@@ -1356,9 +1402,10 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
         };
         auto body = [&]() -> hawkes_status {
             hawkes_status r;
+            // the first evaluation follows the prologue, whose reset of the
+            // per-evaluation control words precedes the graph; each later one
+            // follows a drift kernel that clears them
             if ((r = fork_bmds()) != HAWKES_OK)
-                return r;
-            if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                 return r;
             if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
                 return r;
@@ -1371,8 +1418,6 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                                          d_bad, es),
                        "leapfrog drift");
                 if ((r = fork_bmds()) != HAWKES_OK)
-                    return r;
-                if ((r = enqueue_eval_reset(ctx, pl, es)) != HAWKES_OK)
                     return r;
                 if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
                     return r;

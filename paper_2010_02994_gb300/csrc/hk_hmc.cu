@@ -71,12 +71,22 @@ __device__ bool reflect(double &x, double &p, double lo, double hi)
 // kicks = number of (eps/2) g half-kicks before the drift (1 for the first
 // step, 2 afterwards: the previous step's closing kick and this step's
 // opening kick, done as two separate roundings).  Repacks the mixed-path
-// records of the moved coordinates when `repack`.
+// records of the moved coordinates when `repack`.  The first CTA also clears
+// the per-evaluation control words (flagged-row count, per-set flags and
+// skip bounds) for the evaluation that follows the drift.
 __global__ void kick_drift_kernel(Work w, const int64_t *set_row0, double *__restrict__ p,
                                   const double *__restrict__ g, const double *__restrict__ lo,
                                   const double *__restrict__ hi, const double *__restrict__ eps_dev,
                                   int64_t total_rows, int kicks, int repack, int32_t *refl_bad)
 {
+    if (blockIdx.x == 0) {
+        for (int k = threadIdx.x; k < w.nsets; k += blockDim.x) {
+            w.set_flags[k] = 0;
+            w.set_cmmax[k] = 0;
+        }
+        if (threadIdx.x == 0)
+            w.counters[2] = 0;
+    }
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int set = set_of_row(w, set_row0, r);

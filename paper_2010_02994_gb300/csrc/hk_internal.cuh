@@ -41,7 +41,8 @@ constexpr int kPass1XiVals = 2;     // M, Xi
 
 // What the rate pass keeps per row besides the rate.
 enum RateSums : int { kSumsNone = 0, kSumsTheta = 1, kSumsXi = 2 };
-constexpr int kFinalizeThreads = 128;  // rows per finalize segment (one CTA each)
+constexpr int kSegRows = 64;             // rows per finalize segment
+constexpr int kFinalizeThreads = kSegRows;  // threads of a standalone finalize CTA (one segment each)
 constexpr int kMaxThetaSets = 1;
 constexpr int kThetaParts = 256;  // CTAs of the Theta-gradient reduction
 
@@ -67,12 +68,13 @@ struct SetDesc {
     int64_t fpart2_0; // first double of the set's FP64 gradient partial slots
     int32_t n, d, npad, nblk, B, vpc;
     int32_t item0, nitems;  // the set's work items (in the item list)
-    int32_t seg0;           // first finalize CTA of the set
-    int32_t nseg;           // finalize CTAs of the set
+    int32_t seg0;           // first finalize segment of the set
+    int32_t nseg;           // finalize segments of the set (kSegRows rows each)
     int32_t fsplit;         // column splits of the FP64 pair kernels
     int32_t pad_;
     // mixed-path exponent constants (base 2; see the pass kernels)
     float rho, kappa, cxi1, cxi2;
+    float kappa_lo, cxi1_lo;  // low words: kappa + kappa_lo and cxi1 + cxi1_lo are the FP64 values
     double cxi2_d;    // c_xi1 + log2(rho) in FP64
     // FP64 constants
     double kx, kt;    // coordinate scalings sqrt(log2(e)/2)/tau_x and /tau_t
@@ -107,16 +109,18 @@ struct Work {
     double *F1;          // FP64 pair-kernel partials (rates)
     double *F2;          // FP64 pair-kernel partials (gradients)
     double *theta_rows;  // per-row Theta-gradient sums (kPass1ThetaVals per row, FP64)
-    int32_t *seg_count;  // flagged rows found by each finalize CTA
-    int32_t *seg_rows;   // their set-relative rows (kFinalizeThreads slots per CTA)
-    double *seg_sum;     // each finalize CTA's sum of lnl over its unflagged rows
+    int32_t *seg_count;  // flagged rows of each finalize segment
+    int32_t *seg_rows;   // their set-relative rows (kSegRows slots per segment)
+    double *seg_sum;     // each segment's sum of lnl over its unflagged rows
     double *set_loglik;  // ell per set
     double *theta_parts; // kThetaParts x 6 partial sums of the Theta gradient
-    int32_t *set_flags;  // bit 0: some rate of the set is zero
+    int32_t *set_flags;  // bit 0: some rate of the set is zero; bit 1: the set has flagged rows
     int32_t *set_cmmax;  // per set: max(0, max_n cm32[n]) as float bits (gradient-pass skip bound)
     int32_t skip_far;    // skip pair blocks whose kernel values all underflow
-    int32_t *counters;   // [0] work items taken, [1] CTAs done, [2] flagged rows, [3] fixup CTAs done
+    int32_t *counters;   // [2] flagged rows of the evaluation, [3] fixup CTAs done
+    int32_t *pair_ctr;   // a pair launch's own [0] work items taken, [1] CTAs done
     unsigned *status;    // sticky device status
+    int32_t *set_done;   // finalized segments per set: the last segment's CTA writes ell (returns to zero)
 };
 
 // ------------------------------------------------------------ launchers --
@@ -136,18 +140,13 @@ cudaError_t launch_identity_order(const double *t, double *keys_out, int32_t *va
 cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_sorted, const int32_t *vals_sorted,
                              int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
 
-// hk_pairs_mixed_*.cu
-cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                               cudaStream_t s);
-cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
-                                     int warps, cudaStream_t s);
-cudaError_t launch_pass1_xi_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                                  cudaStream_t s);
-cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                               cudaStream_t s);
-// pass: 1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with the self-excitation sums apart
-size_t pass_smem_bytes(int d, int pass, int warps);
-int pass_max_ctas_per_sm(int d, int pass, int warps);
+// hk_pairs_mixed_*.cu.  pass: 1 rates, 2 gradient, 3 rates with Theta
+// sums, 4 rates with the self-excitation sums apart.  Shape: wr row groups
+// (block size 32 rows_per_lane(d) wr) and wc column groups of warps.
+cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+                                   int wr, int wc, cudaStream_t s);
+size_t pass_smem_bytes(int d, int pass, int wr, int wc);
+int pass_max_ctas_per_sm(int d, int pass, int wr, int wc);
 
 // hk_pairs_fp64.cu
 constexpr int kFp64Rows = 128;  // rows per CTA of the FP64 pair kernels
@@ -166,14 +165,15 @@ cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const WorkItem *items, i
 cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, cudaStream_t s);
 
 // hk_finalize.cu
-cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, cudaStream_t s);
-cudaError_t launch_fixup_rows(const Work &w, int32_t total_segs, int32_t grid, double *out_loglik, bool theta,
-                              cudaStream_t s);
+// Rates, ell per set (out_loglik, nullable) and the FP64 recompute of the
+// flagged rows, one CTA per segment; sums: the rate pass's extra row sums.
+cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,
+                                 cudaStream_t s);
 cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream_t s);
+// Gradient rows from the pass-2 slots (with the flagged rows' FP64 terms
+// and own gradients), in the caller's layout and sorted; one CTA per segment.
 cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
                                  cudaStream_t s);
-cudaError_t launch_fixup_grad(const Work &w, int32_t total_segs, int32_t grid, double *out_grad, double *g_sorted,
-                              cudaStream_t s);
 cudaError_t launch_self_excitation(const Work &w, int32_t total_segs, double *out, cudaStream_t s);
 
 // hk_hmc.cu

@@ -1,21 +1,21 @@
-// Mixed pair kernels for D = 5..8, and the dispatch on D.
+// Mixed pair kernels for D = 7, 8, and the dispatch on D.
 #include "hk_pairs_mixed_launch.cuh"
 
 namespace hk {
-HK_INSTANTIATE_MIXED(5)
-HK_INSTANTIATE_MIXED(6)
 HK_INSTANTIATE_MIXED(7)
 HK_INSTANTIATE_MIXED(8)
 
 #define HK_EXTERN_MIXED(D)                                                                                      \
-    extern template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int,           \
+    extern template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, int,      \
                                                  cudaStream_t);                                                \
-    extern template size_t smem_t<D>(int, int);                                                                 \
-    extern template int occupancy_t<D>(int, int);
+    extern template size_t smem_t<D>(int, int, int);                                                            \
+    extern template int occupancy_t<D>(int, int, int);
 HK_EXTERN_MIXED(1)
 HK_EXTERN_MIXED(2)
 HK_EXTERN_MIXED(3)
 HK_EXTERN_MIXED(4)
+HK_EXTERN_MIXED(5)
+HK_EXTERN_MIXED(6)
 
 #define HK_SWITCH_D(d, EXPR)                                                                                   \
     switch (d) {                                                                                               \
@@ -30,43 +30,22 @@ HK_EXTERN_MIXED(4)
     default: break;                                                                                            \
     }
 
-cudaError_t launch_pass1_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                               cudaStream_t s)
+cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+                                   int wr, int wc, cudaStream_t s)
 {
-    HK_SWITCH_D(d, launch_pass_t<D>(1, w, items, nitems, grid, warps, s))
+    HK_SWITCH_D(d, launch_pass_t<D>(pass, w, items, nitems, grid, wr, wc, s))
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_pass1_theta_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
-                                     int warps, cudaStream_t s)
+size_t pass_smem_bytes(int d, int pass, int wr, int wc)
 {
-    HK_SWITCH_D(d, launch_pass_t<D>(3, w, items, nitems, grid, warps, s))
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_pass1_xi_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                                  cudaStream_t s)
-{
-    HK_SWITCH_D(d, launch_pass_t<D>(4, w, items, nitems, grid, warps, s))
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_pass2_mixed(int d, const Work &w, const WorkItem *items, int32_t nitems, int grid, int warps,
-                               cudaStream_t s)
-{
-    HK_SWITCH_D(d, launch_pass_t<D>(2, w, items, nitems, grid, warps, s))
-    return cudaErrorInvalidValue;
-}
-
-size_t pass_smem_bytes(int d, int pass, int warps)
-{
-    HK_SWITCH_D(d, smem_t<D>(pass, warps))
+    HK_SWITCH_D(d, smem_t<D>(pass, wr, wc))
     return 0;
 }
 
-int pass_max_ctas_per_sm(int d, int pass, int warps)
+int pass_max_ctas_per_sm(int d, int pass, int wr, int wc)
 {
-    HK_SWITCH_D(d, occupancy_t<D>(pass, warps))
+    HK_SWITCH_D(d, occupancy_t<D>(pass, wr, wc))
     return 0;
 }
 

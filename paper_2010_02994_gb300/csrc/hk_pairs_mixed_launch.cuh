@@ -1,7 +1,8 @@
 // Launch helpers of the mixed pair kernels, instantiated per dimension by
 // hk_pairs_mixed_lo.cu (D = 1..4) and hk_pairs_mixed_hi.cu (D = 5..8).
 // pass: 1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with the
-// self-excitation sums apart.
+// self-excitation sums apart.  A shape is (wr, wc): wr row groups of 32 R
+// rows (block size B = 32 R wr) and wc column groups, wr * wc <= 8 warps.
 #pragma once
 
 #include <algorithm>
@@ -10,80 +11,117 @@
 
 namespace hk {
 
-template <int KIND, int D>
-cudaError_t launch_kind_t(const Work &w, const WorkItem *items, int nitems, int grid, int warps, cudaStream_t s)
+// Column groups are a template parameter (1, 2 or 4; a runtime count costs
+// the hot loop about twenty registers); only the rate and gradient passes
+// split columns, the passes with extra row sums run one column group.
+template <int KIND>
+constexpr bool kind_splits_columns()
+{
+    return KIND == kRate || KIND == kGrad;
+}
+
+template <int KIND, int D, int WC>
+cudaError_t launch_wc_t(const Work &w, const WorkItem *items, int nitems, int grid, int wr, cudaStream_t s)
 {
     constexpr int R = rows_per_lane(D);
-    const size_t smem = pair_smem_bytes<KIND, D, R>(warps);
-    pair_kernel<KIND, D, R><<<grid, warps * 32, smem, s>>>(w, items, nitems);
+    const size_t smem = pair_smem_bytes<KIND, D, R>(wr * WC, WC);
+    pair_kernel<KIND, D, R, WC><<<grid, wr * WC * 32, smem, s>>>(w, items, nitems);
     return cudaGetLastError();
 }
 
+template <int KIND, int D>
+cudaError_t launch_kind_t(const Work &w, const WorkItem *items, int nitems, int grid, int wr, int wc,
+                          cudaStream_t s)
+{
+    if (!kind_splits_columns<KIND>() || wc == 1)
+        return launch_wc_t<KIND, D, 1>(w, items, nitems, grid, wr, s);
+    if (wc == 2)
+        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 2 : 1>(w, items, nitems, grid, wr, s);
+    if (wc == 4)
+        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 4 : 1>(w, items, nitems, grid, wr, s);
+    return cudaErrorInvalidValue;
+}
+
 template <int D>
-cudaError_t launch_pass_t(int pass, const Work &w, const WorkItem *items, int nitems, int grid, int warps,
+cudaError_t launch_pass_t(int pass, const Work &w, const WorkItem *items, int nitems, int grid, int wr, int wc,
                           cudaStream_t s)
 {
     if (pass == 1)
-        return launch_kind_t<kRate, D>(w, items, nitems, grid, warps, s);
+        return launch_kind_t<kRate, D>(w, items, nitems, grid, wr, wc, s);
     if (pass == 2)
-        return launch_kind_t<kGrad, D>(w, items, nitems, grid, warps, s);
+        return launch_kind_t<kGrad, D>(w, items, nitems, grid, wr, wc, s);
     if (pass == 4)
-        return launch_kind_t<kRateXi, D>(w, items, nitems, grid, warps, s);
-    return launch_kind_t<kRateTheta, D>(w, items, nitems, grid, warps, s);
+        return launch_kind_t<kRateXi, D>(w, items, nitems, grid, wr, 1, s);
+    return launch_kind_t<kRateTheta, D>(w, items, nitems, grid, wr, 1, s);
 }
 
 template <int D>
-size_t smem_t(int pass, int warps)
+size_t smem_t(int pass, int wr, int wc)
 {
     constexpr int R = rows_per_lane(D);
     if (pass == 1)
-        return pair_smem_bytes<kRate, D, R>(warps);
+        return pair_smem_bytes<kRate, D, R>(wr * wc, wc);
     if (pass == 2)
-        return pair_smem_bytes<kGrad, D, R>(warps);
+        return pair_smem_bytes<kGrad, D, R>(wr * wc, wc);
     if (pass == 4)
-        return pair_smem_bytes<kRateXi, D, R>(warps);
-    return pair_smem_bytes<kRateTheta, D, R>(warps);
+        return pair_smem_bytes<kRateXi, D, R>(wr, 1);
+    return pair_smem_bytes<kRateTheta, D, R>(wr, 1);
 }
 
-template <int KIND, int D>
-int occupancy_kind(int warps)
+// Allow the largest dynamic shared memory any shape of this kernel needs
+// (capped at the per-CTA maximum; static shared memory counts against the
+// same maximum), and return how many CTAs of wr row groups fit on one SM.
+template <int KIND, int D, int WC>
+int occupancy_wc(int wr)
 {
     constexpr int R = rows_per_lane(D);
-    const size_t smem = pair_smem_bytes<KIND, D, R>(warps);
-    // the largest any warp count needs, capped at the per-CTA maximum (some
-    // 8-warp shapes exceed it; the shape choice never selects those)
-    // (static shared memory counts against the same per-CTA maximum)
+    const size_t smem = pair_smem_bytes<KIND, D, R>(wr * WC, WC);
     int dev = 0, cap = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, pair_kernel<KIND, D, R>);
-    const size_t smem_max = std::min<size_t>(pair_smem_bytes<KIND, D, R>(8), (size_t)cap - fa.sharedSizeBytes);
+    cudaFuncGetAttributes(&fa, pair_kernel<KIND, D, R, WC>);
+    size_t largest = 0;
+    for (int a = 1; a * WC <= 8; a *= 2)
+        largest = std::max(largest, pair_smem_bytes<KIND, D, R>(a * WC, WC));
+    const size_t smem_max = std::min<size_t>(largest, (size_t)cap - fa.sharedSizeBytes);
     if (smem > smem_max)
         return 0;
-    cudaFuncSetAttribute(pair_kernel<KIND, D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaFuncSetAttribute(pair_kernel<KIND, D, R, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<KIND, D, R>, warps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<KIND, D, R, WC>, wr * WC * 32, smem);
     return nb;
 }
 
-// Allow the largest dynamic shared memory any warp count needs, and return
-// how many CTAs of `warps` warps fit on one SM.
-template <int D>
-int occupancy_t(int pass, int warps)
+template <int KIND, int D>
+int occupancy_kind(int wr, int wc)
 {
-    if (pass == 1)
-        return occupancy_kind<kRate, D>(warps);
-    if (pass == 2)
-        return occupancy_kind<kGrad, D>(warps);
-    if (pass == 4)
-        return occupancy_kind<kRateXi, D>(warps);
-    return occupancy_kind<kRateTheta, D>(warps);
+    if (!kind_splits_columns<KIND>() || wc == 1)
+        return occupancy_wc<KIND, D, 1>(wr);
+    if (wc == 2)
+        return occupancy_wc<KIND, D, kind_splits_columns<KIND>() ? 2 : 1>(wr);
+    if (wc == 4)
+        return occupancy_wc<KIND, D, kind_splits_columns<KIND>() ? 4 : 1>(wr);
+    return 0;
 }
 
-#define HK_INSTANTIATE_MIXED(D)                                                                               \
-    template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, cudaStream_t);  \
-    template size_t smem_t<D>(int, int);                                                                        \
-    template int occupancy_t<D>(int, int);
+// CTAs of shape (wr, wc) that fit on one SM (the passes with extra row sums
+// always run one column group).
+template <int D>
+int occupancy_t(int pass, int wr, int wc)
+{
+    if (pass == 1)
+        return occupancy_kind<kRate, D>(wr, wc);
+    if (pass == 2)
+        return occupancy_kind<kGrad, D>(wr, wc);
+    if (pass == 4)
+        return occupancy_kind<kRateXi, D>(wr, 1);
+    return occupancy_kind<kRateTheta, D>(wr, 1);
+}
+
+#define HK_INSTANTIATE_MIXED(D)                                                                                \
+    template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, int, cudaStream_t); \
+    template size_t smem_t<D>(int, int, int);                                                                    \
+    template int occupancy_t<D>(int, int, int);
 
 }  // namespace hk

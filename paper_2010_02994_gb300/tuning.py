@@ -1,7 +1,9 @@
 """Tile-shape tuning table: measure with the library's autotuner, keep as JSON.
 
 The table maps a GPU name to entries {"d": D, "bucket": ceil(log2 N),
-"warps": W, "ctas_per_sm": C, "ms": t}.  `load_into(ctx)` copies the entries
+"warps": W, "col_groups": G, "ctas_per_sm": C, "ms": t}: W row groups of
+warps (the pair block size), G column groups, at most C persistent CTAs per
+SM.  Entries without "col_groups" predate the column groups and are skipped.  `load_into(ctx)` copies the entries
 for the context's GPU into the context; `autotune(ctx, t, X, params)` times
 every shape on the caller's data, stores the best in the context, and
 `save(...)` writes the table.  The timing itself runs in the library
@@ -39,10 +41,10 @@ def read(path: str = DEFAULT_PATH) -> dict:
 
 def load_into(ctx: HawkesContext, path: str = DEFAULT_PATH) -> int:
     """Copy the table's entries for this GPU into the context; returns how many."""
-    entries = read(path).get(gpu_name(ctx.device), [])
+    entries = [e for e in read(path).get(gpu_name(ctx.device), []) if "col_groups" in e]
     for e in entries:
         ctx.check(ctx.lib.hawkes_ctx_set_tuning(ctx.handle, int(e["d"]), int(e["bucket"]), int(e["warps"]),
-                                                int(e["ctas_per_sm"])))
+                                                int(e["col_groups"]), int(e["ctas_per_sm"])))
     return len(entries)
 
 
@@ -51,11 +53,12 @@ def autotune(ctx: HawkesContext, t, X, params) -> dict:
     t = _dev_f64(t, "t")
     X = _dev_f64(X, "X")
     n, d, X = _shape(t, X)
-    w, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    w, wc, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     p = params_struct(params)
     ctx.check(ctx.lib.hawkes_autotune(ctx.handle, _ptr(t), _ptr(X), n, d, ctypes.byref(p), ctx.stream(),
-                                      ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)))
-    return {"d": d, "bucket": bucket(n), "n": n, "warps": w.value, "ctas_per_sm": c.value, "ms": ms.value}
+                                      ctypes.byref(w), ctypes.byref(wc), ctypes.byref(c), ctypes.byref(ms)))
+    return {"d": d, "bucket": bucket(n), "n": n, "warps": w.value, "col_groups": wc.value, "ctas_per_sm": c.value,
+            "ms": ms.value}
 
 
 def save(entries: list, device: int = 0, path: str = DEFAULT_PATH) -> None:
@@ -101,8 +104,8 @@ def main(argv=None) -> int:
             t, X = _random_events(n, d, 17 * d + n, dev)
             e = autotune(ctx, t, X, params)
             entries.append(e)
-            print(f"d={d} n={n} bucket={e['bucket']}: warps={e['warps']} ctas/SM={e['ctas_per_sm']} "
-                  f"{e['ms']:.4f} ms", flush=True)
+            print(f"d={d} n={n} bucket={e['bucket']}: warps={e['warps']} col_groups={e['col_groups']} "
+                  f"ctas/SM={e['ctas_per_sm']} {e['ms']:.4f} ms", flush=True)
     save(entries, args.device, args.out)
     ctx.close()
     return 0

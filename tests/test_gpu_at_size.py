@@ -199,14 +199,16 @@ def test_autotuner_on_a_batch_set():
 
     before = run()
     res = tuning.autotune(ctx, t, X, w.params)
-    assert res["warps"] in (1, 2, 4, 8) and res["ctas_per_sm"] >= 0 and res["ms"] > 0
-    assert ctx.get_tuning(w.d, tuning.bucket(w.n)) == {"warps": res["warps"], "ctas_per_sm": res["ctas_per_sm"]}
+    assert res["warps"] in (1, 2, 4, 8) and res["col_groups"] in (0, 1, 2, 4) and res["ctas_per_sm"] >= 0
+    assert res["warps"] * max(1, res["col_groups"]) <= 8 and res["ms"] > 0
+    assert ctx.get_tuning(w.d, tuning.bucket(w.n)) == {k: res[k] for k in ("warps", "col_groups", "ctas_per_sm")}
     after = run()
     ctx.set_option("block_warps", res["warps"])
+    ctx.set_option("col_groups", res["col_groups"])
     ctx.set_option("ctas_per_sm", res["ctas_per_sm"])
     explicit = run()
-    ctx.set_option("block_warps", 0)
-    ctx.set_option("ctas_per_sm", 0)
+    for name in ("block_warps", "col_groups", "ctas_per_sm"):
+        ctx.set_option(name, 0)
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     T = math.ceil(w.n / (32 * _rows_per_lane(w.d) * res["warps"]))
     expected = explicit if T * (T + 1) // 2 >= 3 * sm else before
