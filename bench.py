@@ -62,6 +62,18 @@ def pass_bound_cycles(d: int, which: str, fma_rate: float, ex2_rate: float) -> f
     return max((f1 + f2) / fma_rate, (e1 + e2) / ex2_rate)
 
 
+def eval_roofline(achieved_per_s: float, work_cycles: float, sms: int, clock_mhz: float, unit: str,
+                  basis: str) -> dict:
+    """Roofline of a whole call (trajectory, batch) against the FP32/MUFU
+    bound: work_cycles is the sum over its evaluations of unordered pairs x
+    SM-cycles per pair (pass_bound_cycles / bmds_bound_cycles); everything
+    else the call does (sorting, finalizing, leapfrog updates) counts as
+    time, not work."""
+    peak = sms * clock_mhz * 1e6 / work_cycles
+    return {"bound": "alu", "unit": unit, "achieved": achieved_per_s, "peak": peak, "frac": achieved_per_s / peak,
+            "basis": basis}
+
+
 def bmds_bound_cycles(d: int, fma_rate: float, ex2_rate: float) -> float:
     """SM cycles per unordered pair of the BMDS pair term (Eq. (4)) with its
     location and variance gradients: 4D+40 FP32 ops (difference, square,
@@ -368,7 +380,8 @@ def mwg_workload(dev, stream, l2) -> dict:
     return res
 
 
-def bmds_hawkes_hmc_workload(dev, stream, l2, steps: int = 20) -> dict:
+def bmds_hawkes_hmc_workload(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz: float, sms: int,
+                             steps: int = 20) -> dict:
     """HMC over the latent locations of the BMDS-Hawkes model (the influenza
     application): N = 4,733, D = 6, potential -ell - ell_B, `steps` leapfrog
     steps per trajectory (one CUDA graph), mixed precision with FP32 Y.  The
@@ -393,8 +406,14 @@ def bmds_hawkes_hmc_workload(dev, stream, l2, steps: int = 20) -> dict:
                                                        "mixed", check=False), stream, l2, reps=10, warm=2)
     ctx.sync_status()
     ctx.close()
+    pairs = w.n * (w.n - 1) / 2
+    work = (steps + 1) * pairs * (pass_bound_cycles(w.d, "eval", fma_rate, ex2_rate)
+                                  + bmds_bound_cycles(w.d, fma_rate, ex2_rate))
     return {"workload": w.name, "n": w.n, "d": w.d, "leapfrog_steps": steps, "precision": "mixed, FP32 Y",
             "ms_per_trajectory": m, "trajectories_per_s": 1e3 / m, "gradient_evals_per_s": (steps + 1) * 1e3 / m,
+            "roofline": eval_roofline(1e3 / m, work, sms, clock_mhz, "trajectories/s",
+                                      f"{steps + 1} Hawkes (6D+19 FP32, 4 ex2) and BMDS (4D+40 FP32, 4 MUFU) "
+                                      f"evaluations per trajectory, measured per-SM rates, {clock_mhz:.0f} MHz"),
             "paper_context": "80 M states / ~10 days = ~93 states/s on a Titan V, leapfrog steps not stated"}
 
 
@@ -412,7 +431,8 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
 
     out = {"bmds_influenza_like": bmds_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz, sms),
            "mwg_gunfire_like": mwg_workload(dev, stream, l2),
-           "bmds_hawkes_hmc_influenza_like": bmds_hawkes_hmc_workload(dev, stream, l2)}
+           "bmds_hawkes_hmc_influenza_like": bmds_hawkes_hmc_workload(dev, stream, l2, fma_rate, ex2_rate, clock_mhz,
+                                                                      sms)}
     sets = synth.make_c4()
     sizes = [w.n for w in sets]
     dims = [w.d for w in sets]
@@ -449,8 +469,13 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
         ms64.append(a.elapsed_time(b))
     ctx.sync_status()
     m64 = statistics.median(ms64)
+    # the bound of a call: each set's unordered pairs at its dimension's per-pair bound
+    c4_work = sum(n * (n - 1) / 2 * pass_bound_cycles(d, "eval", fma_rate, ex2_rate) for n, d in zip(sizes, dims))
     out["batched_c4"] = {"sets": len(sets), "events": sum(sizes), "dims": sorted(set(dims)), "ms_per_call": m,
                          "calls_per_s": 1e3 / m, "pairs_per_s": pairs / (m * 1e-3),
+                         "roofline": eval_roofline(1e3 / m, c4_work, sms, clock_mhz, "calls/s",
+                                                   "sum over the 64 sets of N(N-1)/2 x (6D+19)/FMA-rate SM-cycles "
+                                                   f"(the FP32 bound at D = 2, 4, 8), {clock_mhz:.0f} MHz"),
                          "fp64_ms_per_call": m64, "fp64_pairs_per_s": pairs / (m64 * 1e-3)}
     ctx.close()
 
@@ -478,8 +503,12 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
         ms.append(a.elapsed_time(b))
     ctx.sync_status()
     m = statistics.median(ms)
+    c2_work = (steps + 1) * w.n * (w.n - 1) / 2 * pass_bound_cycles(w.d, "eval", fma_rate, ex2_rate)
     out["hmc_c2"] = {"n": w.n, "d": w.d, "leapfrog_steps": steps, "ms_per_trajectory": m,
-                     "trajectories_per_s": 1e3 / m, "grad_evals_per_s": (steps + 1) * 1e3 / m}
+                     "trajectories_per_s": 1e3 / m, "grad_evals_per_s": (steps + 1) * 1e3 / m,
+                     "roofline": eval_roofline(1e3 / m, c2_work, sms, clock_mhz, "trajectories/s",
+                                               f"{steps + 1} evaluations x N(N-1)/2 pairs x (6D+19)/FMA-rate "
+                                               f"SM-cycles, {clock_mhz:.0f} MHz")}
     ctx.close()
     # one HMC proposal per set over the 64 sets of c4 (unconstrained, 20 steps, one graph)
     ctx = HawkesContext(device=dev.index or 0, max_n=sum(sizes), max_d=8)
@@ -503,7 +532,9 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     ctx.sync_status()
     m = statistics.median(ms)
     out["batched_hmc_c4"] = {"sets": len(sets), "events": sum(sizes), "leapfrog_steps": 20, "ms_per_call": m,
-                             "set_trajectories_per_s": len(sets) * 1e3 / m}
+                             "set_trajectories_per_s": len(sets) * 1e3 / m,
+                             "roofline": eval_roofline(1e3 / m, 21 * c4_work, sms, clock_mhz, "calls/s",
+                                                       "21 evaluations of every set per call, bound as batched_c4")}
     ctx.close()
     return out
 

@@ -31,11 +31,10 @@ std::string g_create_err;
 constexpr double kLog2e = 1.4426950408889634073599246810019;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-// control block (int32 words): [0] status, [4..7] kernel counters, [16..34)
-// work/done counters of the pair kernel of each dimension, [40..) set flags,
+// control block (int32 words): [0] status, [16..34) work/done counters of
+// the pair kernel of each dimension, [40..) set flags,
 // then one skip bound per set
 constexpr int kCtlStatus = 0;
-constexpr int kCtlCounters = 4;
 constexpr int kCtlDimCounters = 16;
 constexpr int kCtlSetFlags = 40;
 
@@ -521,10 +520,10 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     ctx->hscal = c.take<double>((4 + kEnergyParts) * ns + 8);
     ctx->hint = c.take<int32_t>(2 * ns + 8);
     w.set_done = c.take<int32_t>(ns);
+    w.sm_count = ctx->sm_count;
     w.set_flags = ctx->ctl + kCtlSetFlags;
     w.set_cmmax = ctx->ctl + kCtlSetFlags + ctx->ctl_sets;
     w.skip_far = ctx->opt_skip;
-    w.counters = ctx->ctl + kCtlCounters;
     w.status = reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus);
     // Upload the plan, unless the device already holds exactly this plan at
     // these addresses.  Copies from pageable memory are staged before the
@@ -595,9 +594,9 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
     ProfEvent pe{};
     if (ctx->opt_profile)
         prof_begin(ctx, s, pe, 2, 0.0);
-    // per-evaluation control words: flagged-row count, fixup counter, set flags and bounds
-    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlCounters + 2, 0, sizeof(int32_t) * (kCtlSetFlags - kCtlCounters - 2 + ns),
-                           s),
+    // per-evaluation control words: the pair kernels' work counters (zero
+    // after every launch; cleared here as well), the set flags and bounds
+    HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlDimCounters, 0, sizeof(int32_t) * (kCtlSetFlags - kCtlDimCounters + ns), s),
            "reset control words");
     HK_TRY(cudaMemsetAsync(ctx->ctl + kCtlSetFlags + ctx->ctl_sets, 0, sizeof(int32_t) * ns, s), "reset bounds");
     HK_TRY(launch_validate_keys(t, X, pl.n_total, pl.x_total, ctx->keys_a, ctx->vals_a, ctx->d_set_ev0, ns,

@@ -3,11 +3,16 @@
 // whose mixed-precision rate is too small to trust in FP32 (hk_rows.cuh),
 // the parameter gradient and the self-excitation probabilities.
 //
-// One CTA of kSegRows threads finalizes one segment of kSegRows rows.  Its
-// flagged rows are recomputed by the same CTA right after (they are rare:
-// none of the paper-shaped workloads has any), so no separate fixup launch
-// is needed; the CTA that finishes a set's last segment (a per-set ticket)
-// writes the set's ell, so the sets of a batch are summed in parallel.
+// F CTAs of kSegRows threads finalize one segment of kSegRows rows (grid
+// (segments, F)).  Each of them sums the segment's slots and so finds the
+// same flagged rows; the first writes the rows' results, and the flagged
+// rows' FP64 work is dealt round-robin to the F CTAs.  F is 1 when there are
+// enough segments to fill the GPU (none of the paper-shaped workloads has a
+// flagged row) and larger for small problems, so that data with many
+// isolated events still spreads its FP64 recomputation over the SMs; no
+// separate fixup launch is needed.  The CTA that finishes a set's last
+// segment (a per-set ticket over all its CTAs) writes the set's ell, so the
+// sets of a batch are summed in parallel.
 #include <algorithm>
 #include <cmath>
 
@@ -23,7 +28,6 @@ static_assert(kT == kSegRows, "a standalone finalize CTA handles one segment");
 
 // ------------------------------------------------------ finalize rows --
 
-constexpr double kLog2e = 1.4426950408889634074;
 
 // The six parameter-gradient row sums of one row in FP64 (natural units).
 __device__ void theta_sums_fp64(const Work &w, const SetDesc &S, int i, double *sh, double *out6)
@@ -57,17 +61,17 @@ __device__ void theta_sums_fp64(const Work &w, const SetDesc &S, int i, double *
         out6[q] = cta_sum(acc[q].value(), sh, kT);
 }
 
-// One segment of kSegRows rows per CTA, one row per thread.  fp64: the FP64
-// path's slots; else the mixed path's, with the rate pass's extra row sums
-// (RateSums: none, the six parameter-gradient sums, or the self-excitation
-// sum apart).
+// One row per thread.  fp64: the FP64 path's slots; else the mixed path's,
+// with the rate pass's extra row sums (RateSums: none, the six
+// parameter-gradient sums, or the self-excitation sum apart).
 __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int sums, double *out_loglik)
 {
     __shared__ double s_lnl[kT];
     __shared__ double sh[kT];
     __shared__ int s_fl[kT];
     __shared__ int s_last;
-    const int g = blockIdx.x;
+    const int g = blockIdx.x, f = blockIdx.y, F = gridDim.y;
+    const bool writer = f == 0;
     const int s = set_of_segment(w, g);
     const SetDesc &S = w.sets[s];
     const int i = (g - S.seg0) * kT + threadIdx.x;
@@ -76,11 +80,23 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
     double lnl_v = 0.0;
     float cmv = 0.0f;
     if (active && !fp64 && sums == kSumsNone) {
-        const RowRate rr = finalize_rate_row(w, S, s, i);
+        const RowRate rr = finalize_rate_row(w, S, s, i, writer);
         flagged = rr.flagged;
         lnl_v = rr.lnl;
-        if (!flagged)
+        if (!flagged && writer)
             cmv = fmaxf(w.cm32[S.row0 + i], 0.0f);
+    } else if (active && !writer) {
+        // only the flag: the first CTA of the segment stores the results
+        if (!fp64) {
+            double v[kMaxD];
+            if (sums == kSumsXi)
+                ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                                                   (int64_t)kPass1XiVals * S.npad, v);
+            else
+                ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                                                      (int64_t)kPass1ThetaVals * S.npad, v);
+            flagged = !(v[0] + v[1] >= S.s_min);
+        }
     } else if (active) {
         const int64_t r = S.row0 + i;
         double lam, inv_sum = 0.0, log_sum = 0.0;
@@ -89,12 +105,12 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
             Nsum acc;
             Nsum th[kPass1ThetaVals];
             for (int sp = 0; sp < S.fsplit; ++sp) {
-                const double *F = w.F1 + S.fpart0 + (int64_t)sp * V * S.npad + i;
+                const double *Fp = w.F1 + S.fpart0 + (int64_t)sp * V * S.npad + i;
                 if (sums == kSumsTheta) {
                     for (int v = 0; v < kPass1ThetaVals; ++v)
-                        th[v].add(F[(int64_t)v * S.npad]);
+                        th[v].add(Fp[(int64_t)v * S.npad]);
                 } else {
-                    acc.add(F[0]);
+                    acc.add(Fp[0]);
                 }
             }
             if (sums == kSumsTheta) {
@@ -159,13 +175,14 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
     s_lnl[threadIdx.x] = lnl_v;
     s_fl[threadIdx.x] = flagged ? 1 : 0;
     __syncthreads();
-    if (threadIdx.x < 32)
+    if (writer && threadIdx.x < 32)
         segment_finish(w, s, g, (g - S.seg0) * kT, s_lnl, s_fl);
     __syncthreads();
-    // this segment's flagged rows, in row order: FP64 rates over all events
-    // (and the six parameter-gradient sums when the rate pass kept them)
-    for (int k = 0; k < kT; ++k) {
-        if (!s_fl[k])
+    // this segment's flagged rows, in row order, dealt round-robin to the F
+    // CTAs: FP64 rates over all events (and the six parameter-gradient sums
+    // when the rate pass kept them)
+    for (int k = 0, nf = 0; k < kT; ++k) {
+        if (!s_fl[k] || nf++ % F != f)
             continue;
         const int fi = (g - S.seg0) * kT + k;
         if (sums == kSumsTheta || sums == kSumsXi) {
@@ -181,7 +198,7 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0)
-        s_last = atomicAdd(&w.set_done[s], 1) == S.nseg - 1;
+        s_last = atomicAdd(&w.set_done[s], 1) == S.nseg * F - 1;
     __syncthreads();
     if (s_last) {
         __threadfence();
@@ -202,15 +219,15 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
 __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, double *out_grad, double *g_sorted)
 {
     __shared__ double sh[kT];
-    const int g = blockIdx.x;
+    const int g = blockIdx.x, f = blockIdx.y, F = gridDim.y;
     const int s = set_of_segment(w, g);
     const SetDesc &S = w.sets[s];
     const int i = (g - S.seg0) * kT + threadIdx.x;
     const bool zero_rate = (w.set_flags[s] & 1) != 0;
-    if (i == 0 && zero_rate)
+    if (i == 0 && f == 0 && zero_rate)
         atomicOr(w.status, kStZeroRate);
     if (fp64) {
-        if (i >= S.n)
+        if (i >= S.n || f != 0)
             return;
         const int d = S.d;
         const int64_t r = S.row0 + i;
@@ -239,10 +256,11 @@ __global__ void __launch_bounds__(kT) finalize_grad_kernel(Work w, int fp64, dou
         }
         return;
     }
-    if (i < S.n && w.w32[S.row0 + i] != 0.0f)
+    if (f == 0 && i < S.n && w.w32[S.row0 + i] != 0.0f)
         finalize_grad_row(w, S, s, i, out_grad, g_sorted);
+    // the segment's flagged rows, dealt round-robin to its F CTAs
     const int cnt = w.seg_count[g];
-    for (int k = 0; k < cnt; ++k)
+    for (int k = f; k < cnt; k += F)
         fixup_grad_row(w, S, s, w.seg_rows[(int64_t)g * kSegRows + k], out_grad, g_sorted, sh, kT);
 }
 
@@ -314,17 +332,29 @@ __global__ void self_excitation_kernel(Work w, double *out)
 
 }  // namespace
 
+// CTAs per segment: enough for about four CTAs per SM in all (mixed path;
+// the FP64 path has no flagged rows).
+static int ctas_per_segment(const Work &w, int32_t total_segs, bool fp64)
+{
+    if (fp64)
+        return 1;
+    const int64_t want = 4LL * std::max(1, w.sm_count);
+    return (int)std::min<int64_t>(32, std::max<int64_t>(1, (want + total_segs - 1) / total_segs));
+}
+
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,
                                  cudaStream_t s)
 {
-    finalize_rows_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, sums, out_loglik);
+    const dim3 grid(total_segs, ctas_per_segment(w, total_segs, fp64));
+    finalize_rows_kernel<<<grid, kT, 0, s>>>(w, fp64 ? 1 : 0, sums, out_loglik);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_grad(const Work &w, int32_t total_segs, bool fp64, double *out_grad, double *g_sorted,
                                  cudaStream_t s)
 {
-    finalize_grad_kernel<<<total_segs, kT, 0, s>>>(w, fp64 ? 1 : 0, out_grad, g_sorted);
+    const dim3 grid(total_segs, ctas_per_segment(w, total_segs, fp64));
+    finalize_grad_kernel<<<grid, kT, 0, s>>>(w, fp64 ? 1 : 0, out_grad, g_sorted);
     return cudaGetLastError();
 }
 

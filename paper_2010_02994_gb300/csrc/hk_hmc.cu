@@ -72,8 +72,8 @@ __device__ bool reflect(double &x, double &p, double lo, double hi)
 // step, 2 afterwards: the previous step's closing kick and this step's
 // opening kick, done as two separate roundings).  Repacks the mixed-path
 // records of the moved coordinates when `repack`.  The first CTA also clears
-// the per-evaluation control words (flagged-row count, per-set flags and
-// skip bounds) for the evaluation that follows the drift.
+// the per-evaluation control words (per-set flags and skip bounds) for the
+// evaluation that follows the drift.
 __global__ void kick_drift_kernel(Work w, const int64_t *set_row0, double *__restrict__ p,
                                   const double *__restrict__ g, const double *__restrict__ lo,
                                   const double *__restrict__ hi, const double *__restrict__ eps_dev,
@@ -84,8 +84,6 @@ __global__ void kick_drift_kernel(Work w, const int64_t *set_row0, double *__res
             w.set_flags[k] = 0;
             w.set_cmmax[k] = 0;
         }
-        if (threadIdx.x == 0)
-            w.counters[2] = 0;
     }
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total_rows;
          r += (int64_t)gridDim.x * blockDim.x) {

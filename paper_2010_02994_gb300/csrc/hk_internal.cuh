@@ -117,10 +117,10 @@ struct Work {
     int32_t *set_flags;  // bit 0: some rate of the set is zero; bit 1: the set has flagged rows
     int32_t *set_cmmax;  // per set: max(0, max_n cm32[n]) as float bits (gradient-pass skip bound)
     int32_t skip_far;    // skip pair blocks whose kernel values all underflow
-    int32_t *counters;   // [2] flagged rows of the evaluation, [3] fixup CTAs done
     int32_t *pair_ctr;   // a pair launch's own [0] work items taken, [1] CTAs done
     unsigned *status;    // sticky device status
-    int32_t *set_done;   // finalized segments per set: the last segment's CTA writes ell (returns to zero)
+    int32_t *set_done;   // finalizing CTAs done per set: the last one writes ell (returns to zero)
+    int32_t sm_count;    // SMs of the device
 };
 
 // ------------------------------------------------------------ launchers --

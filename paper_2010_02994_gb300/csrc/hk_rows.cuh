@@ -176,12 +176,15 @@ struct RowRate {
 
 // Rate of row i of set s from its pass-1 slots (mixed path, no extra sums):
 // lambda_n, 1/lambda_n (FP64 and FP32), the gradient pass's column constant,
-// log lambda_n - Lambda_n.  Flagged rows only get w32 = 0 and cm32 = -inf.
-__device__ __forceinline__ RowRate finalize_rate_row(const Work &w, const SetDesc &S, int s, int i)
+// log lambda_n - Lambda_n, stored when `write`.  Flagged rows only get
+// w32 = 0 and cm32 = -inf.
+__device__ __forceinline__ RowRate finalize_rate_row(const Work &w, const SetDesc &S, int s, int i, bool write)
 {
     const int64_t r = S.row0 + i;
     const double sum = ordered_strided_sum(w.P1 + S.part0 + i, S.nblk, S.npad);
     RowRate out{!(sum >= S.s_min), 0.0};
+    if (!write)
+        return out;
     if (out.flagged) {
         w.w32[r] = 0.0f;
         w.cm32[r] = -INFINITY;
@@ -204,9 +207,8 @@ __device__ __forceinline__ RowRate finalize_rate_row(const Work &w, const SetDes
 // the segment's kSegRows = 64 values in row order (lnl[k], flagged[k] for
 // row seg_first + k; rows past the set are given as not flagged, lnl 0):
 // lane l adds rows l and l + 32, then a butterfly over the lanes.  Writes
-// seg_sum[g], seg_count[g] and seg_rows[g * kSegRows ..] (set-relative rows),
-// adds the flagged count to the evaluation's total and marks set s as having
-// flagged rows.
+// seg_sum[g], seg_count[g] and seg_rows[g * kSegRows ..] (set-relative rows)
+// and marks set s as having flagged rows.
 __device__ __forceinline__ void segment_finish(const Work &w, int s, int g, int seg_first, const double *lnl,
                                                const int *flagged)
 {
@@ -225,10 +227,8 @@ __device__ __forceinline__ void segment_finish(const Work &w, int s, int g, int 
         const int cnt = __popc(b0) + __popc(b1);
         w.seg_count[g] = cnt;
         w.seg_sum[g] = tot;
-        if (cnt) {
-            atomicAdd(&w.counters[2], cnt);
+        if (cnt)
             atomicOr(&w.set_flags[s], 2);
-        }
     }
 }
 
@@ -309,12 +309,12 @@ __device__ __forceinline__ void finalize_grad_row(const Work &w, const SetDesc &
     const int d = S.d;
     const int64_t r = S.row0 + i;
     double gv[kMaxD];
-    // one coordinate at a time: sixteen loads in flight each, few registers
+    // all coordinates together: eight slots of each in flight per round trip
+    ordered_strided_sums_d(d, w.P2 + S.part2_0 + i, S.npad, S.nblk, (int64_t)d * S.npad, gv);
 #pragma unroll
     for (int q = 0; q < kMaxD; ++q)
         if (q < d)
-            gv[q] = S.Cg * ordered_strided_sum(w.P2 + S.part2_0 + (int64_t)q * S.npad + i, S.nblk,
-                                               (int64_t)d * S.npad);
+            gv[q] *= S.Cg;
     if (w.set_flags[s] & 2) {
         const PairFp64 k(S);
         const double tm = w.t64[r];
@@ -367,40 +367,48 @@ __device__ __forceinline__ void finalize_grad_row(const Work &w, const SetDesc &
 }
 
 // Own gradient of a flagged row, in FP64 over all events (Appendix A in its
-// ordered form), summed by the first nt threads of the CTA in a fixed order
-// (every thread of the CTA must call; thread 0 stores).
+// ordered form), one pass over the events for every coordinate, summed by
+// the first nt threads of the CTA in a fixed order (every thread of the CTA
+// must call; thread 0 stores).
 __device__ __forceinline__ void fixup_grad_row(const Work &w, const SetDesc &S, int s, int i, double *out_grad,
                                                double *g_sorted, double *sh, int nt)
 {
     const PairFp64 k(S);
     const int64_t R0 = S.row0, r = R0 + i;
+    const int d = S.d;
     const double tn = w.t64[r], wn = __ldcg(&w.w64[r]);
     const bool zero_rate = (w.set_flags[s] & 1) != 0;
     const int src = w.perm[r];
-    for (int q = 0; q < S.d; ++q) {
-        Nsum acc;
-        for (int m = threadIdx.x; m < S.n && (int)threadIdx.x < nt; m += nt) {
-            const double tm = w.t64[R0 + m];
-            if (tm == tn)
-                continue;
-            double r2 = 0.0;
-            for (int q2 = 0; q2 < S.d; ++q2) {
-                const double df = w.x64[r * kMaxD + q2] - w.x64[(R0 + m) * kMaxD + q2];
-                r2 += df * df;
-            }
-            const double dt = tn - tm;
-            const double wm = __ldcg(&w.w64[R0 + m]);
-            const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
-            const double xi = k.Cxi * exp(-(k.omega * fabs(dt) + r2 * k.c));
-            const double coef = mu * (wn + wm) * k.itx2 + xi * (tm < tn ? wn : wm) * k.ih2;
-            acc.add(coef * (w.x64[(R0 + m) * kMaxD + q] - w.x64[r * kMaxD + q]));
+    Nsum acc[kMaxD];
+    for (int m = threadIdx.x; m < S.n && (int)threadIdx.x < nt; m += nt) {
+        const double tm = w.t64[R0 + m];
+        if (tm == tn)
+            continue;
+        double r2 = 0.0;
+        for (int q2 = 0; q2 < d; ++q2) {
+            const double df = w.x64[r * kMaxD + q2] - w.x64[(R0 + m) * kMaxD + q2];
+            r2 += df * df;
         }
-        double gq = cta_sum(acc.value(), sh, nt);
+        const double dt = tn - tm;
+        const double wm = __ldcg(&w.w64[R0 + m]);
+        const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+        const double xi = k.Cxi * exp(-(k.omega * fabs(dt) + r2 * k.c));
+        const double coef = mu * (wn + wm) * k.itx2 + xi * (tm < tn ? wn : wm) * k.ih2;
+#pragma unroll
+        for (int q = 0; q < kMaxD; ++q)
+            if (q < d)
+                acc[q].add(coef * (w.x64[(R0 + m) * kMaxD + q] - w.x64[r * kMaxD + q]));
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxD; ++q) {
+        if (q >= d)
+            break;
+        double gq = cta_sum(acc[q].value(), sh, nt);
         if (zero_rate)
             gq = nan("");
         if (threadIdx.x == 0) {
             if (out_grad)
-                out_grad[S.x0 + (int64_t)src * S.d + q] = gq;
+                out_grad[S.x0 + (int64_t)src * d + q] = gq;
             if (g_sorted)
                 g_sorted[r * kMaxD + q] = gq;
         }

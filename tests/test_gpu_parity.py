@@ -209,6 +209,24 @@ def test_isolated_events_take_the_fp64_fixup(ctx):
     assert_close(ctx, w2, "fp64")
 
 
+@pytest.mark.parametrize("n,d,extent", [(600, 8, 40.0), (2000, 6, 60.0), (400, 4, 100.0), (1000, 5, 80.0)])
+def test_most_rows_take_the_fp64_fixup(ctx, n, d, extent):
+    """Events spread so far apart (bandwidths small against the spacing) that
+    nearly every rate underflows the FP32 kernel values: those rows are
+    recomputed in FP64, their work dealt over several CTAs per segment at
+    these sizes, and the location gradient takes their FP64 terms."""
+    rng = np.random.default_rng(100 + d)
+    t = np.sort(rng.uniform(0.0, 365.0, size=n))
+    X = rng.uniform(0.0, extent, size=(n, d))
+    P = {"mu0": 0.5, "tau_x": 1.0, "tau_t": 14.0, "theta": 0.5, "omega": 0.5, "h": 0.1}
+    w = synth.Workload("spread_out", t, X, X, None, None, P)
+    lam = oracle.rates(t, X, P)
+    Pmu = P["mu0"] / (P["tau_x"] ** d * P["tau_t"] * (2 * math.pi) ** (d / 2 + 0.5))
+    assert np.mean(lam / Pmu < 2.0 ** -76) > 0.9  # rows below the FP32 threshold
+    assert_close(ctx, w, "mixed")
+    assert_close(ctx, w, "fp64")
+
+
 def test_invalid_data_is_reported(ctx):
     import torch
 
