@@ -455,6 +455,12 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
     ctx.sync_status()
     pairs = float(sum(n * n for n in sizes))
     m = statistics.median(ms)
+    # the same batch with every dimension in one persistent launch per pass
+    ctx.set_option("one_launch", 1)
+    m_one = timed_calls(lambda: hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, check=False), stream, l2,
+                        reps=10, warm=2)
+    ctx.sync_status()
+    ctx.set_option("one_launch", 0)
     # the same batch in FP64 (every operation in double), as the accuracy reference
     hawkes_batch_loglik_grad(ctx, sizes, dims, t, X, params, precision="fp64", check=False)
     torch.cuda.synchronize()
@@ -476,6 +482,7 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
                          "roofline": eval_roofline(1e3 / m, c4_work, sms, clock_mhz, "calls/s",
                                                    "sum over the 64 sets of N(N-1)/2 x (6D+19)/FMA-rate SM-cycles "
                                                    f"(the FP32 bound at D = 2, 4, 8), {clock_mhz:.0f} MHz"),
+                         "one_launch_ms_per_call": m_one,
                          "fp64_ms_per_call": m64, "fp64_pairs_per_s": pairs / (m64 * 1e-3)}
     ctx.close()
 
@@ -531,7 +538,13 @@ def other_workloads(dev, stream, l2, fma_rate: float, ex2_rate: float, clock_mhz
         ms.append(a.elapsed_time(b))
     ctx.sync_status()
     m = statistics.median(ms)
+    ctx.set_option("one_launch", 1)
+    m_one = timed_calls(lambda: hawkes_batch_hmc_trajectory(ctx, sizes, dims, t, X, p0, params, eps, 20, log_u,
+                                                            check=False), stream, l2, reps=5, warm=2)
+    ctx.sync_status()
+    ctx.set_option("one_launch", 0)
     out["batched_hmc_c4"] = {"sets": len(sets), "events": sum(sizes), "leapfrog_steps": 20, "ms_per_call": m,
+                             "one_launch_ms_per_call": m_one,
                              "set_trajectories_per_s": len(sets) * 1e3 / m,
                              "roofline": eval_roofline(1e3 / m, 21 * c4_work, sms, clock_mhz, "calls/s",
                                                        "21 evaluations of every set per call, bound as batched_c4")}

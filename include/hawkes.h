@@ -134,7 +134,16 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            when the symmetric kernels' partial slots, one
  *                            per 256-row block and row, would pass 16 GiB);
  *                            0 (default): each unordered pair once, with a
- *                            table-driven FP64 exp2 (Tang's method)         */
+ *                            table-driven FP64 exp2 (Tang's method)
+ *   HAWKES_OPT_ONE_LAUNCH    1: a batch whose sets have several dimensions
+ *                            runs each mixed pair pass as one persistent
+ *                            launch over every set's pair blocks (each block
+ *                            dispatched on its set's dimension; one shape and
+ *                            the largest register count of all dimensions);
+ *                            0 (default): one persistent launch per
+ *                            dimension, the launches on forked streams so
+ *                            that they overlap; results are the same within
+ *                            the mixed tolerances (block sizes may differ)  */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,
@@ -143,7 +152,8 @@ enum {
     HAWKES_OPT_MIXED_FIXUP_EXP = 5,
     HAWKES_OPT_SKIP_FAR_BLOCKS = 6,
     HAWKES_OPT_FP64_ORDERED = 7,
-    HAWKES_OPT_COL_GROUPS = 8
+    HAWKES_OPT_COL_GROUPS = 8,
+    HAWKES_OPT_ONE_LAUNCH = 9
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 

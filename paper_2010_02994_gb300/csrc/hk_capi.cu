@@ -75,6 +75,7 @@ struct Plan {
     int32_t total_segs = 0, max_fsplit = 1;
     int64_t max_ftiles = 1;
     bool fp64_sym = false;  // FP64 passes: symmetric kernels over the work items
+    bool one_launch = false;  // mixed rate and gradient passes: one launch over every dimension
     double pairs = 0.0;  // unordered pairs over all sets
 };
 
@@ -97,7 +98,8 @@ struct hawkes_ctx {
     DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
     // options
     int opt_warps = 0, opt_cols = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
-    int opt_fp64_ordered = 0;
+    int opt_fp64_ordered = 0, opt_one_launch = 0;
+    int occ_any[3][4] = {};  // CTAs per SM of the one-launch pair kernels: [pass 1..2][log2 warps]
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
     double prof_ms[kStages] = {};
@@ -303,11 +305,27 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
     std::vector<int64_t> nmax_by_d(kMaxD + 1, 0);
     for (int s = 0; s < nsets; ++s)
         nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
+    int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
         if (nmax_by_d[d] > 0) {
+            ++ndims;
             choose_shape(ctx, nmax_by_d[d], d, theta, pl.wr_by_d[d], pl.wc_by_d[d]);
             ctx->cur_ctas_by_d[d] = ctx->tune_ctas[d][size_bucket(nmax_by_d[d])];
         }
+    // One launch over every dimension (an option): all dimensions take the
+    // row groups of the one with the most pair work, and one column group.
+    pl.one_launch = !fp64 && !theta && !xi && ctx->opt_one_launch && ndims > 1;
+    if (pl.one_launch) {
+        std::vector<double> work_by_d(kMaxD + 1, 0.0);
+        for (int s = 0; s < nsets; ++s)
+            work_by_d[dims[s]] += (double)ev_counts[s] * (double)ev_counts[s] * (6 * dims[s] + 19);
+        const int heavy = (int)(std::max_element(work_by_d.begin(), work_by_d.end()) - work_by_d.begin());
+        for (int d = 1; d <= kMaxD; ++d)
+            if (nmax_by_d[d] > 0) {
+                pl.wr_by_d[d] = pl.wr_by_d[heavy];
+                pl.wc_by_d[d] = 1;
+            }
+    }
     // FP64: the symmetric kernels keep one partial slot per row block and
     // row, (6 + d) doubles each; they are used while that stays within
     // kSymSlotBudget, the ordered kernels (a few column splits) beyond it
@@ -380,7 +398,34 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         pl.set_ev0[s] = s < nsets ? pl.sets[s].ev0 : ev;
         pl.set_row0[s] = s < nsets ? pl.sets[s].row0 : row;
     }
-    if (!fp64 || pl.fp64_sym) {
+    if (pl.one_launch) {
+        // one list for the single launch: the dimensions' off-diagonal blocks
+        // in order of decreasing cost per block (B^2 (6D + 19)), then every
+        // diagonal block (half the work), so that the last blocks are small
+        std::vector<int> order;
+        for (int d = 1; d <= kMaxD; ++d)
+            if (nmax_by_d[d] > 0)
+                order.push_back(d);
+        auto block_cost = [&](int d) {
+            const double B = 32.0 * rows_per_lane(d) * pl.wr_by_d[d];
+            return B * B * (6 * d + 19);
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return block_cost(a) > block_cost(b); });
+        for (int pass_diag = 0; pass_diag < 2; ++pass_diag)
+            for (int d : order)
+                for (int s = 0; s < nsets; ++s) {
+                    const SetDesc &S = pl.sets[s];
+                    if (S.d != d)
+                        continue;
+                    for (int I = 0; I < S.nblk; ++I) {
+                        if (pass_diag)
+                            pl.items.push_back({s, I, I, 1});
+                        else
+                            for (int J = I + 1; J < S.nblk; ++J)
+                                pl.items.push_back({s, I, J, 0});
+                    }
+                }
+    } else if (!fp64 || pl.fp64_sym) {
         // work items grouped by dimension; diagonal blocks (half the work) last
         for (int d = 1; d <= kMaxD; ++d) {
             const int first = (int)pl.items.size();
@@ -625,6 +670,22 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
 // into s), so that the GPU fills one dimension's tail with another's blocks.
 hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaStream_t s)
 {
+    if (pl.one_launch && (pass == 1 || pass == 2)) {
+        int warps = 1;
+        for (int d = 1; d <= kMaxD; ++d)
+            if (pl.item_range_by_d[d].second > 0 || pl.wr_by_d[d] > 0)
+                warps = std::max(warps, pl.wr_by_d[d]);
+        int per_sm = ctx->occ_any[pass][ilog2_small(warps)];
+        if (ctx->opt_ctas > 0)
+            per_sm = std::min(per_sm, ctx->opt_ctas);
+        const int nitems = (int)pl.items.size();
+        const int grid = std::max(1, std::min(nitems, std::max(per_sm, 1) * ctx->sm_count));
+        Work wd = ctx->w;
+        wd.pair_ctr = ctx->ctl + kCtlDimCounters;  // the slot of dimension 0 (unused otherwise)
+        HK_TRY(launch_pair_pass_any_d(pass, wd, ctx->d_items, nitems, grid, warps, s),
+               pass == 2 ? "gradient pass" : "rate pass");
+        return HAWKES_OK;
+    }
     int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
         ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
@@ -714,7 +775,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
     int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
         ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
-    const int pass_launches = fp64 ? fp64_pass_launches(pl) : ndims;
+    const int pass_launches = fp64 ? fp64_pass_launches(pl) : (pl.one_launch ? 1 : ndims);
     ctx->launches_own += (want_grad ? 2 : 1) * (pass_launches + 1) + (theta ? 2 : 0);
     hawkes_status st;
     {
@@ -854,6 +915,9 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
             for (int a = 0; a < 4; ++a)
                 for (int b = 0; b < 4; ++b)
                     ctx->occ[d][pass][a][b] = (1 << (a + b)) <= 8 ? pass_max_ctas_per_sm(d, pass, 1 << a, 1 << b) : 0;
+    for (int pass = 1; pass <= 2; ++pass)
+        for (int a = 0; a < 4; ++a)
+            ctx->occ_any[pass][a] = pass_any_d_max_ctas_per_sm(pass, 1 << a);
     Plan pl;
     hawkes_params p{1, 1, 1, 1, 1, 1};
     const int64_t n64 = max_n;
@@ -961,6 +1025,9 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
         return HAWKES_OK;
     case HAWKES_OPT_FP64_ORDERED:
         ctx->opt_fp64_ordered = value ? 1 : 0;
+        return HAWKES_OK;
+    case HAWKES_OPT_ONE_LAUNCH:
+        ctx->opt_one_launch = value ? 1 : 0;
         return HAWKES_OK;
     case HAWKES_OPT_MIXED_FIXUP_EXP:
         if (value < -120 || value > 0)

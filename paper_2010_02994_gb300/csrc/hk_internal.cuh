@@ -147,6 +147,11 @@ cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const WorkIte
                                    int wr, int wc, cudaStream_t s);
 size_t pass_smem_bytes(int d, int pass, int wr, int wc);
 int pass_max_ctas_per_sm(int d, int pass, int wr, int wc);
+// hk_pairs_mixed_any.cu: the rate (1) or gradient (2) pass over every
+// dimension of a plan in one launch (warps row groups, one column group).
+cudaError_t launch_pair_pass_any_d(int pass, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+                                   int warps, cudaStream_t s);
+int pass_any_d_max_ctas_per_sm(int pass, int warps);
 
 // hk_pairs_fp64.cu
 constexpr int kFp64Rows = 128;  // rows per CTA of the FP64 pair kernels

@@ -228,11 +228,32 @@ constexpr size_t pair_smem_bytes(int W, int WC)
            + (size_t)W * 32 * R * sizeof(int);            // tie ends of each warp's rows
 }
 
-// Persistent pair kernel.  A CTA of W warps takes pair blocks {I, J} from the
-// work list; its warps form W / WC row groups of 32 R rows of block I and WC
-// column groups of B / WC columns of block J, so that at small N a block is
-// swept by more warps (and ends sooner) without making the blocks, and with
-// them the partial slots, smaller.
+// One pair block {I, J} (I <= J) of set wi.set by the whole CTA: its warps
+// form blockDim.x / 32 / WC row groups of 32 R rows of block I and WC column
+// groups of B / WC columns of block J, so that at small N a block is swept
+// by more warps (and ends sooner) without making the blocks, and with them
+// the partial slots, smaller.  smem4 is the kernel's dynamic shared memory.
+template <int KIND, int D, int R, int WC>
+__device__ __forceinline__ void pair_item(const Work &w, const WorkItem wi, float4 *smem4)
+{
+    constexpr int wc = WC;
+    using T = KindTraits<KIND, D>;
+    constexpr int NP = nrec(D), NPP = T::NPP, VR = T::VR, VC = T::VC;
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wr = warps / wc, rg = warp / wc, cg = warp % wc;
+    const int B = 32 * R * wr, CB = B / wc;
+    float4 *priv = smem4 + warp * NPP * 64;
+    float *colpart = reinterpret_cast<float *>(smem4 + warps * NPP * 64);  // [wr][VC][B]
+    float *rowpart = colpart + (size_t)wr * VC * B;                        // [wc][VC][B]
+    int *te_all = reinterpret_cast<int *>(rowpart + (size_t)wc * VC * B);  // [warps][32 R]
+    int *s_te = te_all + warp * 32 * R;
+    const int src_lane = (lane + 1) & 31;
+#include "hk_pair_item.inc"
+}
+
+// Persistent pair kernel of one dimension: CTAs take pair blocks from the
+// work list (an atomic counter) until it is exhausted.
 template <int KIND, int D, int R, int WC>
 __global__ void __launch_bounds__(256)
     pair_kernel(Work w, const WorkItem *__restrict__ items, int nitems)
@@ -252,7 +273,6 @@ __global__ void __launch_bounds__(256)
     int *s_te = te_all + warp * 32 * R;
     __shared__ int s_item;
     const int src_lane = (lane + 1) & 31;
-
     for (;;) {
         if (threadIdx.x == 0)
             s_item = atomicAdd(&w.pair_ctr[0], 1);
@@ -261,190 +281,47 @@ __global__ void __launch_bounds__(256)
         if (it >= nitems)
             break;
         const WorkItem wi = items[it];
-        const SetDesc &S = w.sets[wi.set];
-        const int I = wi.I, J = wi.J, n = S.n, npad = S.npad;
-        const float4 *rec = w.rec + S.rec0;
-        const float *w32 = w.w32 + S.row0;
-        const float *cm32 = w.cm32 + S.row0;
-        const PairConsts kc{S.rho, S.kappa, S.cxi1};
-        float *P = (KIND == kGrad ? w.P2 + S.part2_0 : w.P1 + S.part0);
+#include "hk_pair_item.inc"
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(&w.pair_ctr[1], 1);
+        if (done == (int)gridDim.x - 1) {
+            w.pair_ctr[0] = 0;
+            w.pair_ctr[1] = 0;
+            __threadfence();
+        }
+    }
+}
 
-        // time origin: the middle row of block I
-        float oh, ol;
-        {
-            const int io = min(I * B + B / 2, n - 1);
-            const float4 v = rec[(int64_t)((2 * D) / 4) * npad + io];
-            const float *c = reinterpret_cast<const float *>(&v);
-            oh = c[(2 * D) % 4];
-            ol = c[(2 * D) % 4 + 1];
-        }
-        // Optional skip of a block that is far apart in time: if even its
-        // closest pair has both exponents <= -130, every kernel value of the
-        // block flushes to zero in FP32 and its partials are exactly zero.
-        bool skip = false;
-        if (w.skip_far && I != J) {
-            const int il = min(I * B + B - 1, n - 1), jf = J * B;
-            const float4 vl = rec[(int64_t)((2 * D) / 4) * npad + il];
-            const float4 vf = rec[(int64_t)((2 * D) / 4) * npad + jf];
-            const float *cl = reinterpret_cast<const float *>(&vl);
-            const float *cf0 = reinterpret_cast<const float *>(&vf);
-            const float dtmin = ((cf0[(2 * D) % 4] - oh) + (cf0[(2 * D) % 4 + 1] - ol)) -
-                                ((cl[(2 * D) % 4] - oh) + (cl[(2 * D) % 4 + 1] - ol));
-            const float cmax = KIND == kGrad ? __int_as_float(w.set_cmmax[wi.set]) : kc.cxi;
-            skip = dtmin * dtmin >= 130.0f && cmax - kc.kappa * dtmin <= -130.0f;
-        }
-        if (skip) {
-            for (int c = threadIdx.x; c < B; c += blockDim.x)
-#pragma unroll
-                for (int v = 0; v < VC; ++v) {
-                    P[((int64_t)J * VC + v) * npad + (int64_t)I * B + c] = 0.0f;
-                    P[((int64_t)I * VC + v) * npad + (int64_t)J * B + c] = 0.0f;
-                }
-        } else {
-            // this lane's rows
-            float rx[R][2 * D], rt[R], rw[R], ra[R], part[R][VR], rs[R][VR], rc[R][VR];
-            const int rbase = I * B + rg * 32 * R;
-            int te_min = 0x7fffffff, te_max = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int row = rbase + 32 * r + lane;
-                float f[4 * NP];
-                load_rec<D>(rec, npad, row, f);
-#pragma unroll
-                for (int q = 0; q < 2 * D; ++q)
-                    rx[r][q] = f[q];
-                rt[r] = (f[2 * D] - oh) + (f[2 * D + 1] - ol);
-                rw[r] = KIND == kGrad ? w32[row] : 0.0f;
-                ra[r] = KIND == kGrad ? kt_plus_c(S.kappa, S.kappa_lo, rt[r], 0.0f, 0.0f)
-                                      : kt_plus_c(S.kappa, S.kappa_lo, rt[r], S.cxi1, S.cxi1_lo);
-                const int te = w.tie_end[S.row0 + row];
-                s_te[32 * r + lane] = te;
-                te_min = min(te_min, te);
-                te_max = max(te_max, te);
-#pragma unroll
-                for (int v = 0; v < VR; ++v) {
-                    rs[r][v] = 0.0f;
-                    rc[r][v] = 0.0f;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                te_min = min(te_min, __shfl_xor_sync(0xffffffffu, te_min, o));
-                te_max = max(te_max, __shfl_xor_sync(0xffffffffu, te_max, o));
-            }
-            const int cbase = J * B + cg * CB;
-            // prefetch the first chunk's record for this lane
-            float pf[4 * NP], pw = 0.0f, pc = 0.0f;
-            {
-                const int64_t col = (int64_t)cbase + lane;
-                load_rec<D>(rec, npad, col, pf);
-                if (KIND == kGrad) {
-                    pw = w32[col];
-                    pc = cm32[col];
-                }
-            }
-            for (int c0 = 0; c0 < CB; c0 += 32) {
-                // stage this chunk's records twice: entries lane and lane + 32
-                {
-                    float f[4 * NPP];
-#pragma unroll
-                    for (int q = 0; q < 4 * NPP; ++q)
-                        f[q] = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < 2 * D; ++q)
-                        f[q] = pf[q];
-                    f[2 * D] = (pf[2 * D] - oh) + (pf[2 * D + 1] - ol);
-                    if (KIND == kGrad) {
-                        f[2 * D + 1] = pw;
-                        f[2 * D + 2] = kt_plus_c(S.kappa, S.kappa_lo, f[2 * D], -pc, 0.0f);
-                    } else {
-                        f[2 * D + 1] = kt_plus_c(S.kappa, S.kappa_lo, f[2 * D], 0.0f, 0.0f);
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int p = 0; p < NPP; ++p) {
-                        const float4 v = make_float4(f[4 * p], f[4 * p + 1], f[4 * p + 2], f[4 * p + 3]);
-                        priv[p * 64 + lane] = v;
-                        priv[p * 64 + lane + 32] = v;
-                    }
-                    __syncwarp();
-                }
-                if (c0 + 32 < CB) {
-                    const int64_t col = (int64_t)cbase + c0 + 32 + lane;
-                    load_rec<D>(rec, npad, col, pf);
-                    if (KIND == kGrad) {
-                        pw = w32[col];
-                        pc = cm32[col];
-                    }
-                }
-                const int m0 = cbase + c0;
-                float *cp = colpart + (size_t)(rg * VC) * B + cg * CB + c0;
-                if (m0 + 32 <= te_min) {  // every pair of this chunk is masked
-#pragma unroll
-                    for (int v = 0; v < VC; ++v)
-                        cp[(size_t)v * B + lane] = 0.0f;
-                    continue;
-                }
-                float acc[VC];
-#pragma unroll
-                for (int v = 0; v < VC; ++v)
-                    acc[v] = 0.0f;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int v = 0; v < VR; ++v)
-                        part[r][v] = 0.0f;
-                if (m0 < te_max)
-                    chunk_steps<KIND, D, R, true>(priv + lane, src_lane, lane, m0, s_te, rx, rt, rw, ra, kc, part,
-                                                  acc);
-                else
-                    chunk_steps<KIND, D, R, false>(priv + lane, src_lane, lane, m0, s_te, rx, rt, rw, ra, kc, part,
-                                                   acc);
-                // lane L now holds the total of column c0 + L
-#pragma unroll
-                for (int v = 0; v < VC; ++v)
-                    cp[(size_t)v * B + lane] = acc[v];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int v = 0; v < VR; ++v) {  // Kahan, once per chunk
-                        const float y = part[r][v] - rc[r][v];
-                        const float t = rs[r][v] + y;
-                        rc[r][v] = (t - rs[r][v]) - y;
-                        rs[r][v] = t;
-                    }
-            }
-            // this column group's row totals, in the column-plane numbering
-            float *rp = rowpart + (size_t)(cg * VC) * B;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int rr = rg * 32 * R + 32 * r + lane;
-#pragma unroll
-                for (int v = 0; v < VC; ++v)
-                    rp[(size_t)v * B + rr] = 0.0f;
-#pragma unroll
-                for (int v = 0; v < VR; ++v)
-                    rp[(size_t)row_plane<KIND>(v) * B + rr] = rs[r][v] - rc[r][v];
-            }
-            __syncthreads();
-            // column totals over the row groups, row totals over the column
-            // groups, both in group order
-            for (int c = threadIdx.x; c < B; c += blockDim.x) {
-#pragma unroll
-                for (int v = 0; v < VC; ++v) {
-                    float tot = 0.0f, rowv = 0.0f;
-                    for (int q = 0; q < wr; ++q)
-                        tot += colpart[((size_t)q * VC + v) * B + c];
-                    for (int q = 0; q < wc; ++q)
-                        rowv += rowpart[((size_t)q * VC + v) * B + c];
-                    if (I != J) {
-                        P[((int64_t)J * VC + v) * npad + (int64_t)I * B + c] = rowv;
-                        P[((int64_t)I * VC + v) * npad + (int64_t)J * B + c] = tot;
-                    } else {
-                        P[((int64_t)I * VC + v) * npad + (int64_t)I * B + c] = rowv + tot;
-                    }
-                }
-            }
+// The same over the work items of every dimension in one persistent launch:
+// each item is dispatched on its set's dimension (one column group; every
+// dimension's blocks are 32 rows_per_lane(d) x blockDim.x / 32 rows).  The
+// kernel's register count is the largest any dimension needs.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+    pair_kernel_any_d(Work w, const WorkItem *__restrict__ items, int nitems)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(&w.pair_ctr[0], 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems)
+            break;
+        const WorkItem wi = items[it];
+        switch (w.sets[wi.set].d) {
+        case 1: pair_item<KIND, 1, rows_per_lane(1), 1>(w, wi, smem4); break;
+        case 2: pair_item<KIND, 2, rows_per_lane(2), 1>(w, wi, smem4); break;
+        case 3: pair_item<KIND, 3, rows_per_lane(3), 1>(w, wi, smem4); break;
+        case 4: pair_item<KIND, 4, rows_per_lane(4), 1>(w, wi, smem4); break;
+        case 5: pair_item<KIND, 5, rows_per_lane(5), 1>(w, wi, smem4); break;
+        case 6: pair_item<KIND, 6, rows_per_lane(6), 1>(w, wi, smem4); break;
+        case 7: pair_item<KIND, 7, rows_per_lane(7), 1>(w, wi, smem4); break;
+        default: pair_item<KIND, 8, rows_per_lane(8), 1>(w, wi, smem4); break;
         }
         __syncthreads();
     }

@@ -49,14 +49,17 @@ def _cat(arrs, dev="cuda"):
     return torch.tensor(np.concatenate([np.asarray(a).reshape(-1) for a in arrs]), device=dev)
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batch_of_64_sets_matches_per_set_oracle(c4, prec):
+@pytest.mark.parametrize("prec,one_launch", [("mixed", 0), ("fp64", 0), ("mixed", 1)])
+def test_batch_of_64_sets_matches_per_set_oracle(c4, prec, one_launch):
+    """Per-dimension launches, and (one_launch) every dimension's pair blocks
+    in one persistent launch per pass."""
     from paper_2010_02994_gb300 import HawkesContext, hawkes_batch_loglik_grad
 
     sets, refs = c4
     sizes = [w.n for w in sets]
     dims = [w.d for w in sets]
     ctx = HawkesContext(device=0, max_n=sum(sizes), max_d=8)
+    ctx.set_option("one_launch", one_launch)
     ell, g = hawkes_batch_loglik_grad(ctx, sizes, dims, _cat([w.t for w in sets]), _cat([w.X for w in sets]),
                                       [w.params for w in sets], precision=prec)
     ell = ell.cpu().numpy()
@@ -73,11 +76,11 @@ def test_batch_of_64_sets_matches_per_set_oracle(c4, prec):
         worst_l, worst_g = max(worst_l, el), max(worst_g, eg)
         assert el <= tl, f"set {i} (n={w.n}, d={w.d}) {prec}: ell rel {el:.2e}"
         assert eg <= tg, f"set {i} (n={w.n}, d={w.d}) {prec}: grad rel-L2 {eg:.2e}"
-    print(f"c4 {prec}: worst ell rel {worst_l:.2e}, worst grad rel-L2 {worst_g:.2e}")
+    print(f"c4 {prec} one_launch={one_launch}: worst ell rel {worst_l:.2e}, worst grad rel-L2 {worst_g:.2e}")
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batched_hmc_over_64_sets_replays_oracle(c4, prec):
+@pytest.mark.parametrize("prec,one_launch", [("mixed", 0), ("fp64", 0), ("mixed", 1)])
+def test_batched_hmc_over_64_sets_replays_oracle(c4, prec, one_launch):
     """One 20-step proposal per set for all 64 sets in one call; the two
     smallest sets of each dimension are replayed by the oracle, and one of
     them gets a log u above its energy gain, so it must be rejected."""
@@ -102,6 +105,7 @@ def test_batched_hmc_over_64_sets_replays_oracle(c4, prec):
     log_u = [-np.inf] * len(sets)
     log_u[reject] = refs[reject]["H0"] - refs[reject]["H1"] + 1.0
     ctx = HawkesContext(device=0, max_n=sum(sizes), max_d=8)
+    ctx.set_option("one_launch", one_launch)
     X = _cat([w.X for w in sets])
     H0, H1, acc = hawkes_batch_hmc_trajectory(ctx, sizes, dims, _cat([w.t for w in sets]), X, _cat(p0s),
                                               [w.params for w in sets], eps, L,
