@@ -33,18 +33,19 @@ MAX_SM_MHZ_NOMINAL = 2070.0  # GB300 maximum SM clock
 CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 
 # DRAM bytes (read + write) per launch of each pair kernel at N=1e5, D=2, from
-# one ncu capture of the kernel source whose SHA-256 is recorded with it;
-# reported as null once the source has changed.
-PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", "hk_pairs_mixed.cuh")
-MEASURED_TRAFFIC = {"source_sha256": "b963b47817d90975d15ea642b2ecf421e43a51e81fd339e9ad3951adbce01c6c",
-                    "pass1_rates": 3767552, "pass2_gradient": 20658944}
+# one ncu capture of the kernel sources whose SHA-256 (of the files in order)
+# is recorded with it; reported as null once the sources have changed.
+PAIR_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", f)
+                       for f in ("hk_pairs_mixed.cuh", "hk_pair_item.inc")]
+MEASURED_TRAFFIC = {"source_sha256": "4149422b98fd6c43cd885fb496b16063efe063bea055000a2f79b6e15c6074d4",
+                    "pass1_rates": 3753216, "pass2_gradient": 21282048}
 
 
 def measured_traffic(kernel: str):
     import hashlib
 
     try:
-        sha = hashlib.sha256(open(PAIR_KERNEL_SOURCE, "rb").read()).hexdigest()
+        sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in PAIR_KERNEL_SOURCES)).hexdigest()
     except OSError:
         return None
     return MEASURED_TRAFFIC.get(kernel) if sha == MEASURED_TRAFFIC["source_sha256"] else None
