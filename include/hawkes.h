@@ -88,9 +88,12 @@ typedef void *hawkes_stream; /* cudaStream_t */
  * mixed-precision problems of up to max_n events (summed over the sets of a
  * batch) in up to max_d <= 8 dimensions.  Larger calls grow the workspace on
  * demand, which allocates device memory at that call; so does the first
- * HAWKES_PREC_FP64 call, whose partial sums take (6 + d) doubles per event
- * and 256-event block (about 2.5 GB at n = 1e5, d = 2).  On success *ctx owns
- * the workspace until hawkes_ctx_destroy. */
+ * HAWKES_PREC_FP64 call.  The workspace is O(n): about 0.5 KB per event in
+ * the arrays kept per event, plus the pair kernels' partial sums, which
+ * take at most max(1 GiB, four slots) where a slot is (vpc + d) floats per
+ * event on the mixed path (vpc = 1, 2 or 6 rate sums) and (6 + d) doubles on
+ * the FP64 path (see HAWKES_OPT_PARTIAL_SLOTS).  On success *ctx owns the
+ * workspace until hawkes_ctx_destroy. */
 hawkes_status hawkes_ctx_create(hawkes_ctx **ctx, int32_t device, int64_t max_n, int32_t max_d);
 
 /* Release a context and its device memory.  The caller must have finished
@@ -130,9 +133,7 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            number of pairs evaluated depends on the data
  *                            (default 0: every pair is evaluated)
  *   HAWKES_OPT_FP64_ORDERED  1: the FP64 path evaluates every ordered pair
- *                            with CUDA's exp() (the layout it falls back to
- *                            when the symmetric kernels' partial slots, one
- *                            per 256-row block and row, would pass 16 GiB);
+ *                            with CUDA's exp() in a few column splits;
  *                            0 (default): each unordered pair once, with a
  *                            table-driven FP64 exp2 (Tang's method)
  *   HAWKES_OPT_ONE_LAUNCH    1: a batch whose sets have several dimensions
@@ -143,7 +144,22 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            0 (default): one persistent launch per
  *                            dimension, the launches on forked streams so
  *                            that they overlap; results are the same within
- *                            the mixed tolerances (block sizes may differ)  */
+ *                            the mixed tolerances (block sizes may differ)
+ *   HAWKES_OPT_PARTIAL_SLOTS the cap G on the partial sums each event keeps
+ *                            between the pair kernels and the finalize
+ *                            kernels.  The pair blocks of a set with nb
+ *                            blocks are dealt out in nb | 1 rounds that touch
+ *                            every block once; the first G rounds store slots
+ *                            0 .. G-1, and each further G rounds ("phase")
+ *                            run as another launch that stores G scratch
+ *                            slots, which a fold kernel adds into the first
+ *                            G: a fixed order, so results stay
+ *                            deterministic.  0 (default): every round its
+ *                            own slot while all slots fit 1 GiB, else as many
+ *                            slots and scratch slots as fit (at least enough
+ *                            for 16 pair blocks per SM in each phase).  A
+ *                            different G changes the order of the sums
+ *                            (results within rounding)  */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,
@@ -153,7 +169,8 @@ enum {
     HAWKES_OPT_SKIP_FAR_BLOCKS = 6,
     HAWKES_OPT_FP64_ORDERED = 7,
     HAWKES_OPT_COL_GROUPS = 8,
-    HAWKES_OPT_ONE_LAUNCH = 9
+    HAWKES_OPT_ONE_LAUNCH = 9,
+    HAWKES_OPT_PARTIAL_SLOTS = 10
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 

@@ -38,6 +38,12 @@ constexpr int kCtlStatus = 0;
 constexpr int kCtlDimCounters = 16;
 constexpr int kCtlSetFlags = 40;
 
+// Partial slots of the symmetric pair kernels: at most this many bytes
+// (unless one slot per row is already more), and a phase of the pair
+// schedule holds at least kMinPhaseItems pair blocks per SM.
+constexpr double kSlotBudget = 1024.0 * 1024.0 * 1024.0;
+constexpr double kMinPhaseItems = 16.0;
+
 struct DeviceBuffer {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -62,13 +68,24 @@ struct ProfEvent {
     double pairs;
 };
 
+// One pair-kernel launch of a pass: runs [run0, run0 + nruns) of the plan's
+// run list, nitems work items in all, of dimension d (0: every dimension),
+// in phase `phase` of the pair schedule.
+struct PairLaunch {
+    int d, phase;
+    int32_t run0, nruns, nitems;
+};
+
 // Host description of one call (a list of sets).
 struct Plan {
     std::vector<SetDesc> sets;
-    std::vector<WorkItem> items;         // grouped by dimension
+    std::vector<ItemRun> runs;           // the pair launches' work lists
+    std::vector<PairLaunch> launches;    // in phase order
     std::vector<int64_t> set_ev0;        // nsets+1
     std::vector<int64_t> set_row0;       // nsets+1
-    std::vector<std::pair<int, int>> item_range_by_d;  // [d] -> (first, count)
+    std::vector<int> dims;               // the dimensions present
+    int32_t slot_cap = 0;                // G: partial slots per row at most
+    int32_t phases = 1;                  // phases of the pair schedule
     std::vector<int> wr_by_d, wc_by_d;  // pair-kernel shape per dimension: row groups, column groups (0 = per pass)
     int64_t n_total = 0, x_total = 0, total_rows = 0, total_rec4 = 0, total_P1 = 0, total_P2 = 0;
     int64_t total_F1 = 0, total_F2 = 0;
@@ -98,7 +115,7 @@ struct hawkes_ctx {
     DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
     // options
     int opt_warps = 0, opt_cols = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
-    int opt_fp64_ordered = 0, opt_one_launch = 0;
+    int opt_fp64_ordered = 0, opt_one_launch = 0, opt_slots = 0;
     int occ_any[3][4] = {};  // CTAs per SM of the one-launch pair kernels: [pass 1..2][log2 warps]
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
@@ -122,7 +139,7 @@ struct hawkes_ctx {
     // workspace views of the current plan
     Work w{};
     SetDesc *d_sets = nullptr;
-    WorkItem *d_items = nullptr;
+    ItemRun *d_runs = nullptr;
     int64_t *d_set_ev0 = nullptr, *d_set_row0 = nullptr;
     double *keys_a = nullptr, *keys_b = nullptr;
     int32_t *vals_a = nullptr, *vals_b = nullptr;
@@ -298,23 +315,21 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
     pl.sets.resize(nsets);
     pl.set_ev0.resize(nsets + 1);
     pl.set_row0.resize(nsets + 1);
-    pl.item_range_by_d.assign(kMaxD + 1, {0, 0});
     pl.wr_by_d.assign(kMaxD + 1, 0);
     pl.wc_by_d.assign(kMaxD + 1, 0);
     // the block size is chosen per dimension from the largest set of that dimension
     std::vector<int64_t> nmax_by_d(kMaxD + 1, 0);
     for (int s = 0; s < nsets; ++s)
         nmax_by_d[dims[s]] = std::max(nmax_by_d[dims[s]], ev_counts[s]);
-    int ndims = 0;
     for (int d = 1; d <= kMaxD; ++d)
         if (nmax_by_d[d] > 0) {
-            ++ndims;
+            pl.dims.push_back(d);
             choose_shape(ctx, nmax_by_d[d], d, theta, pl.wr_by_d[d], pl.wc_by_d[d]);
             ctx->cur_ctas_by_d[d] = ctx->tune_ctas[d][size_bucket(nmax_by_d[d])];
         }
     // One launch over every dimension (an option): all dimensions take the
     // row groups of the one with the most pair work, and one column group.
-    pl.one_launch = !fp64 && !theta && !xi && ctx->opt_one_launch && ndims > 1;
+    pl.one_launch = !fp64 && !theta && !xi && ctx->opt_one_launch && pl.dims.size() > 1;
     if (pl.one_launch) {
         std::vector<double> work_by_d(kMaxD + 1, 0.0);
         for (int s = 0; s < nsets; ++s)
@@ -326,16 +341,37 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
                 pl.wc_by_d[d] = 1;
             }
     }
-    // FP64: the symmetric kernels keep one partial slot per row block and
-    // row, (6 + d) doubles each; they are used while that stays within
-    // kSymSlotBudget, the ordered kernels (a few column splits) beyond it
-    if (fp64) {
-        double sym_bytes = 0.0;
+    pl.fp64_sym = fp64 && ctx->opt_fp64_ordered == 0;
+    const bool sym = !fp64 || pl.fp64_sym;  // the symmetric pair kernels and their schedule
+    auto block_rows = [&](int d) {
+        return fp64 ? (pl.fp64_sym ? kSymRows : kFp64Rows) : 32 * rows_per_lane(d) * pl.wr_by_d[d];
+    };
+    const int vpc = theta ? kPass1ThetaVals : (xi ? kPass1XiVals : kPass1Vals);
+    // Slot cap G of the pair schedule: every round its own slot while all
+    // slots fit kSlotBudget bytes; beyond it as many as fit beside as many
+    // scratch slots, but at least enough that a phase holds kMinPhaseItems
+    // pair blocks per SM.
+    if (sym) {
+        double per_slot = 0.0, full = 0.0, per_round = 0.0;
+        int32_t nt_max = 1;
         for (int s = 0; s < nsets; ++s) {
-            const double nb = (double)((ev_counts[s] + kSymRows - 1) / kSymRows);
-            sym_bytes += nb * nb * kSymRows * (kPass1ThetaVals + dims[s]) * sizeof(double);
+            const int d = dims[s], B = block_rows(d);
+            const int64_t nblk = (ev_counts[s] + B - 1) / B, nt = nblk | 1;
+            const double bytes = (double)(nblk * B) * (fp64 ? (kPass1ThetaVals + d) * 8.0 : (vpc + d) * 4.0);
+            per_slot += bytes;
+            full += (double)nt * bytes;
+            per_round += (double)((nt + 1) / 2);
+            nt_max = std::max<int32_t>(nt_max, (int32_t)nt);
         }
-        pl.fp64_sym = ctx->opt_fp64_ordered == 0 && sym_bytes <= kSymSlotBudget;
+        int64_t G = nt_max;
+        if (ctx->opt_slots > 0) {
+            G = ctx->opt_slots;
+        } else if (full > kSlotBudget) {
+            const int64_t g_fit = (int64_t)(kSlotBudget / std::max(2.0 * per_slot, 1.0));
+            const int64_t g_par = (int64_t)std::ceil(kMinPhaseItems * ctx->sm_count / std::max(per_round, 1.0));
+            G = std::max<int64_t>(1, std::max(g_fit, g_par));
+        }
+        pl.slot_cap = (int32_t)std::min<int64_t>(G, nt_max);
     }
     int64_t ev = 0, x = 0, row = 0, rec4 = 0, p1 = 0, p2 = 0, f1 = 0, f2 = 0;
     int32_t seg = 0;
@@ -348,10 +384,11 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         if (!fp64 && !mixed_range_ok(S))
             return fail(ctx, HAWKES_ERR_INVALID_ARG,
                         "parameters outside the range of the mixed-precision path; use HAWKES_PREC_FP64");
-        const int B = fp64 ? (pl.fp64_sym ? kSymRows : kFp64Rows) : 32 * rows_per_lane(d) * pl.wr_by_d[d];
+        const int B = block_rows(d);
         S.B = B;
         S.nblk = (int32_t)((n + B - 1) / B);
         S.npad = S.nblk * B;
+        S.nslot = sym ? std::min(S.nblk | 1, pl.slot_cap) : 0;
         S.ev0 = ev;
         S.x0 = x;
         S.row0 = row;
@@ -360,14 +397,14 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         S.part2_0 = p2;
         S.fpart0 = f1;
         S.fpart2_0 = f2;
-        S.vpc = theta ? kPass1ThetaVals : (xi ? kPass1XiVals : kPass1Vals);
+        S.vpc = vpc;
         S.seg0 = seg;
         S.nseg = (int32_t)((n + kFinalizeThreads - 1) / kFinalizeThreads);
         // FP64 kernels: enough column splits for about 8 CTAs per SM in total
         const int64_t ftiles = (n + kFp64Rows - 1) / kFp64Rows;
         int64_t fs = std::max<int64_t>(1, (8LL * ctx->sm_count) / std::max<int64_t>(1, ftiles * nsets));
         fs = std::min<int64_t>(fs, ftiles);
-        S.fsplit = pl.fp64_sym ? S.nblk : (int32_t)std::max<int64_t>(1, fs);
+        S.fsplit = pl.fp64_sym ? S.nslot : (int32_t)std::max<int64_t>(1, fs);
         pl.max_fsplit = std::max(pl.max_fsplit, S.fsplit);
         pl.max_ftiles = std::max(pl.max_ftiles, ftiles);
         ev += n;
@@ -375,12 +412,16 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         row += S.npad;
         rec4 += (int64_t)nrec(d) * S.npad;
         // partial slots: FP32 for the mixed path, FP64 for the FP64 path
+        // (with later phases of the pair schedule, nslot scratch slots too)
+        int64_t nalloc = fp64 ? S.fsplit : S.nslot;
+        if (sym && (S.nblk | 1) > S.nslot)
+            nalloc = 2 * S.nslot;
         if (!fp64) {
-            p1 += (int64_t)S.nblk * S.npad * S.vpc;
-            p2 += (int64_t)S.nblk * S.npad * d;
+            p1 += nalloc * S.npad * S.vpc;
+            p2 += nalloc * S.npad * d;
         } else {
-            f1 += (int64_t)S.fsplit * S.npad * kPass1ThetaVals;
-            f2 += (int64_t)S.fsplit * S.npad * d;
+            f1 += nalloc * S.npad * kPass1ThetaVals;
+            f2 += nalloc * S.npad * d;
         }
         seg += S.nseg;
         pl.pairs += 0.5 * (double)n * (double)(n - 1);
@@ -398,55 +439,70 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
         pl.set_ev0[s] = s < nsets ? pl.sets[s].ev0 : ev;
         pl.set_row0[s] = s < nsets ? pl.sets[s].row0 : row;
     }
+    if (!sym)
+        return HAWKES_OK;
+    // Work lists of the pair launches, phase by phase: per dimension (or,
+    // with one launch, over the dimensions in order of decreasing cost per
+    // block, B^2 (6D + 19)), the off-diagonal blocks of every set's rounds
+    // in the phase, then their diagonal blocks (half the work), so that the
+    // last blocks of a launch are small.
+    std::vector<int> order = pl.dims;
     if (pl.one_launch) {
-        // one list for the single launch: the dimensions' off-diagonal blocks
-        // in order of decreasing cost per block (B^2 (6D + 19)), then every
-        // diagonal block (half the work), so that the last blocks are small
-        std::vector<int> order;
-        for (int d = 1; d <= kMaxD; ++d)
-            if (nmax_by_d[d] > 0)
-                order.push_back(d);
         auto block_cost = [&](int d) {
             const double B = 32.0 * rows_per_lane(d) * pl.wr_by_d[d];
             return B * B * (6 * d + 19);
         };
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return block_cost(a) > block_cost(b); });
-        for (int pass_diag = 0; pass_diag < 2; ++pass_diag)
-            for (int d : order)
-                for (int s = 0; s < nsets; ++s) {
-                    const SetDesc &S = pl.sets[s];
-                    if (S.d != d)
-                        continue;
-                    for (int I = 0; I < S.nblk; ++I) {
-                        if (pass_diag)
-                            pl.items.push_back({s, I, I, 1});
-                        else
-                            for (int J = I + 1; J < S.nblk; ++J)
-                                pl.items.push_back({s, I, J, 0});
-                    }
-                }
-    } else if (!fp64 || pl.fp64_sym) {
-        // work items grouped by dimension; diagonal blocks (half the work) last
-        for (int d = 1; d <= kMaxD; ++d) {
-            const int first = (int)pl.items.size();
-            for (int s = 0; s < nsets; ++s) {
-                const SetDesc &S = pl.sets[s];
-                if (S.d != d)
-                    continue;
-                for (int I = 0; I < S.nblk; ++I)
-                    for (int J = I + 1; J < S.nblk; ++J)
-                        pl.items.push_back({s, I, J, 0});
+    }
+    int32_t phases = 0;
+    for (int s = 0; s < nsets; ++s) {
+        const SetDesc &S = pl.sets[s];
+        phases = std::max(phases, ((S.nblk | 1) + S.nslot - 1) / S.nslot);
+    }
+    pl.phases = phases;
+    int64_t first = 0;
+    bool overflow = false;
+    auto add_runs = [&](int d, int phase, bool diag) {
+        for (int s = 0; s < nsets; ++s) {
+            const SetDesc &S = pl.sets[s];
+            if (S.d != d)
+                continue;
+            const int nt = S.nblk | 1;
+            const int r0 = phase * S.nslot;
+            const int r1 = std::min(r0 + S.nslot, diag ? S.nblk : nt);
+            const int per = diag ? 1 : (nt - 1) / 2;
+            if (r1 <= r0 || per == 0)
+                continue;
+            pl.runs.push_back({s, r0, r1 - r0, diag ? 1 : 0, (int32_t)first, 0});
+            first += (int64_t)(r1 - r0) * per;
+            overflow = overflow || first > INT32_MAX;
+        }
+    };
+    auto close_launch = [&](int d, int phase, size_t run0) {
+        if (first > 0)
+            pl.launches.push_back({d, phase, (int32_t)run0, (int32_t)(pl.runs.size() - run0), (int32_t)first});
+        else
+            pl.runs.resize(run0);
+        first = 0;
+    };
+    for (int p = 0; p < phases; ++p) {
+        if (pl.one_launch) {
+            const size_t run0 = pl.runs.size();
+            for (int diag = 0; diag < 2; ++diag)
+                for (int d : order)
+                    add_runs(d, p, diag != 0);
+            close_launch(0, p, run0);
+        } else {
+            for (int d : order) {
+                const size_t run0 = pl.runs.size();
+                add_runs(d, p, false);
+                add_runs(d, p, true);
+                close_launch(d, p, run0);
             }
-            for (int s = 0; s < nsets; ++s) {
-                const SetDesc &S = pl.sets[s];
-                if (S.d != d)
-                    continue;
-                for (int I = 0; I < S.nblk; ++I)
-                    pl.items.push_back({s, I, I, 1});
-            }
-            pl.item_range_by_d[d] = {first, (int)pl.items.size() - first};
         }
     }
+    if (overflow)
+        return fail(ctx, HAWKES_ERR_INVALID_ARG, "too many pair blocks in one launch");
     return HAWKES_OK;
 }
 
@@ -455,7 +511,7 @@ size_t plan_bytes(const Plan &pl, size_t sort_bytes)
     Carve c{nullptr};
     const size_t ns = pl.sets.size();
     c.take<SetDesc>(ns);
-    c.take<WorkItem>(std::max<size_t>(1, pl.items.size()));
+    c.take<ItemRun>(std::max<size_t>(1, pl.runs.size()));
     c.take<int64_t>(ns + 1);
     c.take<int64_t>(ns + 1);
     c.take<float4>(pl.total_rec4);
@@ -526,7 +582,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     Carve c{reinterpret_cast<char *>(ctx->ws.ptr)};
     Work &w = ctx->w;
     ctx->d_sets = c.take<SetDesc>(ns);
-    ctx->d_items = c.take<WorkItem>(std::max<size_t>(1, pl.items.size()));
+    ctx->d_runs = c.take<ItemRun>(std::max<size_t>(1, pl.runs.size()));
     ctx->d_set_ev0 = c.take<int64_t>(ns + 1);
     ctx->d_set_row0 = c.take<int64_t>(ns + 1);
     w.sets = ctx->d_sets;
@@ -581,7 +637,7 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     append(&ctx->ws_generation, sizeof(ctx->ws_generation));
     append(&ctx->ws.ptr, sizeof(void *));
     append(pl.sets.data(), sizeof(SetDesc) * ns);
-    append(pl.items.data(), sizeof(WorkItem) * pl.items.size());
+    append(pl.runs.data(), sizeof(ItemRun) * pl.runs.size());
     append(pl.set_ev0.data(), sizeof(int64_t) * (ns + 1));
     append(pl.set_row0.data(), sizeof(int64_t) * (ns + 1));
     if (bytes == ctx->uploaded)
@@ -592,10 +648,10 @@ hawkes_status bind_plan(hawkes_ctx *ctx, const Plan &pl, cudaStream_t stream)
     HK_TRY(cudaMemsetAsync(w.set_done, 0, sizeof(int32_t) * ns, stream), "clear tickets");
     HK_TRY(cudaMemcpyAsync(ctx->d_sets, pl.sets.data(), sizeof(SetDesc) * ns, cudaMemcpyHostToDevice, stream),
            "upload set descriptors");
-    if (!pl.items.empty())
-        HK_TRY(cudaMemcpyAsync(ctx->d_items, pl.items.data(), sizeof(WorkItem) * pl.items.size(),
+    if (!pl.runs.empty())
+        HK_TRY(cudaMemcpyAsync(ctx->d_runs, pl.runs.data(), sizeof(ItemRun) * pl.runs.size(),
                                cudaMemcpyHostToDevice, stream),
-               "upload work items");
+               "upload work lists");
     HK_TRY(cudaMemcpyAsync(ctx->d_set_ev0, pl.set_ev0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice,
                            stream),
            "upload set offsets");
@@ -658,38 +714,48 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
                "time sort");
     }
     HK_TRY(launch_pack_rows(w, X, ctx->keys_b, ctx->vals_b, pl.total_rows, ctx->d_set_row0, s), "pack");
+    // a pair schedule with later phases starts with cleared scratch slots
+    // (each fold clears them again)
+    if (pl.phases > 1) {
+        HK_TRY(cudaMemsetAsync(w.P1, 0, sizeof(float) * pl.total_P1, s), "clear slots");
+        HK_TRY(cudaMemsetAsync(w.P2, 0, sizeof(float) * pl.total_P2, s), "clear slots");
+        HK_TRY(cudaMemsetAsync(w.F1, 0, sizeof(double) * pl.total_F1, s), "clear slots");
+        HK_TRY(cudaMemsetAsync(w.F2, 0, sizeof(double) * pl.total_F2, s), "clear slots");
+    }
     if (ctx->opt_profile)
         prof_end(ctx, s, pe);
     return HAWKES_OK;
 }
 
 // One pair pass (1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with
-// the self-excitation sums apart) over every dimension of the plan.  Each
-// dimension is one persistent launch with its own work counter; with several
-// dimensions the launches run concurrently on forked streams (joined back
-// into s), so that the GPU fills one dimension's tail with another's blocks.
+// the self-excitation sums apart) over every dimension of the plan: the
+// plan's pair launches in phase order, each of a later phase followed by a
+// fold of its scratch slots.  Each pair launch is persistent with its own
+// work counter; with several dimensions each dimension's launches run on its
+// own forked stream (joined back into s), so that the GPU fills one
+// dimension's tail with another's blocks, while its phases stay in order.
 hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaStream_t s)
 {
+    const int fold_part = pass == 2 ? 1 : 0;
     if (pl.one_launch && (pass == 1 || pass == 2)) {
         int warps = 1;
-        for (int d = 1; d <= kMaxD; ++d)
-            if (pl.item_range_by_d[d].second > 0 || pl.wr_by_d[d] > 0)
-                warps = std::max(warps, pl.wr_by_d[d]);
+        for (int d : pl.dims)
+            warps = std::max(warps, pl.wr_by_d[d]);
         int per_sm = ctx->occ_any[pass][ilog2_small(warps)];
         if (ctx->opt_ctas > 0)
             per_sm = std::min(per_sm, ctx->opt_ctas);
-        const int nitems = (int)pl.items.size();
-        const int grid = std::max(1, std::min(nitems, std::max(per_sm, 1) * ctx->sm_count));
         Work wd = ctx->w;
         wd.pair_ctr = ctx->ctl + kCtlDimCounters;  // the slot of dimension 0 (unused otherwise)
-        HK_TRY(launch_pair_pass_any_d(pass, wd, ctx->d_items, nitems, grid, warps, s),
-               pass == 2 ? "gradient pass" : "rate pass");
+        for (const PairLaunch &L : pl.launches) {
+            const Sched sc{ctx->d_runs + L.run0, L.nruns, L.nitems};
+            const int grid = std::max(1, std::min(L.nitems, std::max(per_sm, 1) * ctx->sm_count));
+            HK_TRY(launch_pair_pass_any_d(pass, wd, sc, grid, warps, s), pass == 2 ? "gradient pass" : "rate pass");
+            if (L.phase > 0)
+                HK_TRY(launch_fold_slots(ctx->w, sc, fold_part, s), "fold slots");
+        }
         return HAWKES_OK;
     }
-    int ndims = 0;
-    for (int d = 1; d <= kMaxD; ++d)
-        ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
-    const bool fork = ndims > 1;
+    const bool fork = pl.dims.size() > 1;
     if (fork) {
         if (!ctx->fork_ev) {
             HK_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
@@ -699,47 +765,47 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
             }
         }
         HK_TRY(cudaEventRecord(ctx->fork_ev, s), "fork");
+        for (int d : pl.dims)
+            HK_TRY(cudaStreamWaitEvent(ctx->side[d], ctx->fork_ev, 0), "fork wait");
     }
-    for (int d = 1; d <= kMaxD; ++d) {
-        const auto rg = pl.item_range_by_d[d];
-        if (rg.second == 0)
-            continue;
+    for (const PairLaunch &L : pl.launches) {
+        const int d = L.d;
         const int wr = pl.wr_by_d[d];
-        const int wc = (pass == 1 || pass == 2) && pl.wc_by_d[d] > 0 ? pl.wc_by_d[d] : pass_cols(ctx, d, pass, wr, rg.second);
-        const int grid = persistent_grid(ctx, d, pass, wr, wc, rg.second);
+        const int wc = (pass == 1 || pass == 2) && pl.wc_by_d[d] > 0 ? pl.wc_by_d[d]
+                                                                      : pass_cols(ctx, d, pass, wr, L.nitems);
+        const int grid = persistent_grid(ctx, d, pass, wr, wc, L.nitems);
         Work wd = ctx->w;
         wd.pair_ctr = ctx->ctl + kCtlDimCounters + 2 * d;  // [0] work taken, [1] CTAs done
-        cudaStream_t ls = s;
-        if (fork) {
-            ls = ctx->side[d];
-            HK_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev, 0), "fork wait");
-        }
-        const WorkItem *items = ctx->d_items + rg.first;
-        HK_TRY(launch_pair_pass_mixed(pass, d, wd, items, rg.second, grid, wr, wc, ls),
-               pass == 2 ? "gradient pass" : "rate pass");
-        if (fork) {
-            HK_TRY(cudaEventRecord(ctx->join_ev[d], ls), "join");
+        const Sched sc{ctx->d_runs + L.run0, L.nruns, L.nitems};
+        cudaStream_t ls = fork ? ctx->side[d] : s;
+        HK_TRY(launch_pair_pass_mixed(pass, d, wd, sc, grid, wr, wc, ls), pass == 2 ? "gradient pass" : "rate pass");
+        if (L.phase > 0)
+            HK_TRY(launch_fold_slots(ctx->w, sc, fold_part, ls), "fold slots");
+    }
+    if (fork)
+        for (int d : pl.dims) {
+            HK_TRY(cudaEventRecord(ctx->join_ev[d], ctx->side[d]), "join");
             HK_TRY(cudaStreamWaitEvent(s, ctx->join_ev[d], 0), "join wait");
         }
-    }
     return HAWKES_OK;
 }
 
-// Kernel launches one FP64 pair pass makes: one per dimension for the
-// symmetric kernels, one for the ordered kernels.
-int fp64_pass_launches(const Plan &pl)
+// Kernel launches one pair pass makes: the plan's pair launches and a fold
+// after each of a later phase (the symmetric kernels), or one (the ordered
+// FP64 kernels).
+int pass_launches(const Plan &pl)
 {
-    if (!pl.fp64_sym)
+    if (pl.launches.empty())
         return 1;
     int k = 0;
-    for (int d = 1; d <= kMaxD; ++d)
-        k += pl.item_range_by_d[d].second > 0 ? 1 : 0;
+    for (const PairLaunch &L : pl.launches)
+        k += L.phase > 0 ? 2 : 1;
     return k;
 }
 
 // One FP64 pair pass (1: rates, with the Theta sums when theta; 2: gradient):
-// the symmetric kernels over the plan's work items of each dimension, or the
-// ordered kernels over all sets.
+// the symmetric kernels over the plan's pair launches (with the folds of the
+// later phases), or the ordered kernels over all sets.
 hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool theta, cudaStream_t s)
 {
     const Work &w = ctx->w;
@@ -751,14 +817,14 @@ hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool 
             HK_TRY(launch_pass2_fp64(w, 0, ns, pl.max_fsplit, pl.max_ftiles, s), "FP64 gradient pass");
         return HAWKES_OK;
     }
-    for (int d = 1; d <= kMaxD; ++d) {
-        const int first = pl.item_range_by_d[d].first, count = pl.item_range_by_d[d].second;
-        if (count == 0)
-            continue;
+    for (const PairLaunch &L : pl.launches) {
+        const Sched sc{ctx->d_runs + L.run0, L.nruns, L.nitems};
         if (pass == 1)
-            HK_TRY(launch_pass1_fp64_sym(d, w, ctx->d_items + first, count, theta, s), "FP64 rate pass");
+            HK_TRY(launch_pass1_fp64_sym(L.d, w, sc, theta, s), "FP64 rate pass");
         else
-            HK_TRY(launch_pass2_fp64_sym(d, w, ctx->d_items + first, count, s), "FP64 gradient pass");
+            HK_TRY(launch_pass2_fp64_sym(L.d, w, sc, s), "FP64 gradient pass");
+        if (L.phase > 0)
+            HK_TRY(launch_fold_slots(w, sc, pass == 2 ? 4 : (theta ? 3 : 2), s), "fold slots");
     }
     return HAWKES_OK;
 }
@@ -772,11 +838,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
 {
     const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
-    int ndims = 0;
-    for (int d = 1; d <= kMaxD; ++d)
-        ndims += pl.item_range_by_d[d].second > 0 ? 1 : 0;
-    const int pass_launches = fp64 ? fp64_pass_launches(pl) : (pl.one_launch ? 1 : ndims);
-    ctx->launches_own += (want_grad ? 2 : 1) * (pass_launches + 1) + (theta ? 2 : 0);
+    ctx->launches_own += (want_grad ? 2 : 1) * (pass_launches(pl) + 1) + (theta ? 2 : 0);
     hawkes_status st;
     {
         ProfEvent pe{};
@@ -1029,6 +1091,11 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
     case HAWKES_OPT_ONE_LAUNCH:
         ctx->opt_one_launch = value ? 1 : 0;
         return HAWKES_OK;
+    case HAWKES_OPT_PARTIAL_SLOTS:
+        if (value < 0 || value > (int64_t)1 << 30)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "partial slots must be in [0, 2^30]");
+        ctx->opt_slots = (int)value;
+        return HAWKES_OK;
     case HAWKES_OPT_MIXED_FIXUP_EXP:
         if (value < -120 || value > 0)
             return fail(ctx, HAWKES_ERR_INVALID_ARG, "fixup exponent must be in [-120, 0]");
@@ -1182,7 +1249,7 @@ hawkes_status hawkes_self_excitation_prob(hawkes_ctx *ctx, const double *t, cons
         HK_TRY(launch_finalize_rows(ctx->w, pl.total_segs, false, kSumsXi, nullptr, s), "finalize rows");
     }
     HK_TRY(launch_self_excitation(ctx->w, pl.total_segs, out_prob, s), "self-excitation");
-    ctx->launches_own += 3 + (fp64 ? fp64_pass_launches(pl) - 1 : 0);
+    ctx->launches_own += 2 + pass_launches(pl);
     return enqueue_nan_on_invalid(ctx, out_prob, n, nullptr, 0, s);
 }
 

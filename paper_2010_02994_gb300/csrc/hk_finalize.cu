@@ -90,10 +90,10 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
         if (!fp64) {
             double v[kMaxD];
             if (sums == kSumsXi)
-                ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nslot,
                                                    (int64_t)kPass1XiVals * S.npad, v);
             else
-                ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nslot,
                                                       (int64_t)kPass1ThetaVals * S.npad, v);
             flagged = !(v[0] + v[1] >= S.s_min);
         }
@@ -123,10 +123,10 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
         } else {
             double v[kMaxD];
             if (sums == kSumsXi)
-                ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                ordered_strided_sums<kPass1XiVals>(w.P1 + S.part0 + i, S.npad, S.nslot,
                                                    (int64_t)kPass1XiVals * S.npad, v);
             else
-                ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nblk,
+                ordered_strided_sums<kPass1ThetaVals>(w.P1 + S.part0 + i, S.npad, S.nslot,
                                                       (int64_t)kPass1ThetaVals * S.npad, v);
             const double sum = v[0] + v[1];
             flagged = !(sum >= S.s_min);
@@ -330,6 +330,43 @@ __global__ void self_excitation_kernel(Work w, double *out)
     out[S.ev0 + w.perm[r]] = lam > 0.0 ? w.theta_rows[r * kPass1ThetaVals + 1] / lam : nan("");
 }
 
+// The partial slots of a set that a fold adds into: part 0 P1, 1 P2 (FP32),
+// 2 F1, 3 F1 with the Theta sums, 4 F2 (FP64); V values per slot.
+__device__ __forceinline__ float *fold_base(const Work &w, const SetDesc &S, int part, int &V, float *)
+{
+    V = part == 0 ? S.vpc : S.d;
+    return part == 0 ? w.P1 + S.part0 : w.P2 + S.part2_0;
+}
+
+__device__ __forceinline__ double *fold_base(const Work &w, const SetDesc &S, int part, int &V, double *)
+{
+    V = part == 2 ? 1 : (part == 3 ? kPass1ThetaVals : S.d);
+    return part == 4 ? w.F2 + S.fpart2_0 : w.F1 + S.fpart0;
+}
+
+// After a later phase of the pair schedule: each off-diagonal run of the
+// launch's work list is one set and the nr rounds it had in the phase, whose
+// partials went to the scratch slots nslot .. nslot + nr - 1; slot j < nr
+// gets scratch slot nslot + j added, which is then cleared for the next
+// phase.  Both are contiguous ranges of nr V npad values (blockIdx.y: the
+// run).
+template <typename T>
+__global__ void __launch_bounds__(256) fold_slots_kernel(Work w, Sched sc, int part)
+{
+    const ItemRun ru = sc.runs[blockIdx.y];
+    if (ru.diag)
+        return;
+    const SetDesc &S = w.sets[ru.set];
+    int V;
+    T *dst = fold_base(w, S, part, V, (T *)nullptr);
+    T *src = dst + (int64_t)S.nslot * V * S.npad;
+    const int64_t len = (int64_t)ru.nr * V * S.npad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        dst[i] += src[i];
+        src[i] = T(0);
+    }
+}
+
 }  // namespace
 
 // CTAs per segment: enough for about four CTAs per SM in all (mixed path;
@@ -340,6 +377,18 @@ static int ctas_per_segment(const Work &w, int32_t total_segs, bool fp64)
         return 1;
     const int64_t want = 4LL * std::max(1, w.sm_count);
     return (int)std::min<int64_t>(32, std::max<int64_t>(1, (want + total_segs - 1) / total_segs));
+}
+
+cudaError_t launch_fold_slots(const Work &w, const Sched &sc, int part, cudaStream_t s)
+{
+    if (sc.nruns <= 0)
+        return cudaSuccess;
+    const dim3 grid((unsigned)std::max(1, (4 * std::max(1, w.sm_count) + sc.nruns - 1) / sc.nruns), (unsigned)sc.nruns);
+    if (part <= 1)
+        fold_slots_kernel<float><<<grid, 256, 0, s>>>(w, sc, part);
+    else
+        fold_slots_kernel<double><<<grid, 256, 0, s>>>(w, sc, part);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,

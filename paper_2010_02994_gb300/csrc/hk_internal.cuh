@@ -16,14 +16,28 @@
 //   t64, x64  FP64 sorted times and coordinates (x64 row stride kMaxD).
 //   P1    pass-1 partial row sums, slot-major: P1[part0 + (slot*vpc + v)*npad + i]
 //   P2    pass-2 partial gradients: P2[part2_0 + (slot*D + k)*npad + i]
-//   A row n of block I receives its partial from the pair block {I, J} in
-//   slot J; each slot has exactly one writer, so every sum below is taken
-//   in a fixed order and the results are deterministic.
 //   F1, F2  the FP64 path's partials, FP64, in the same slot-major layout
 //         (F1[fpart0 + (slot*V + v)*npad + i], V = 6 with the Theta sums,
-//         else 1; F2[fpart2_0 + (slot*D + k)*npad + i]), fsplit slots: one
-//         per row block for the symmetric kernels, a few column splits for
-//         the ordered ones.  A plan holds P1/P2 or F1/F2, not both.
+//         else 1; F2[fpart2_0 + (slot*D + k)*npad + i]), fsplit slots: nslot
+//         for the symmetric kernels, a few column splits for the ordered
+//         ones.  A plan holds P1/P2 or F1/F2, not both.
+//
+// Pair schedule.  The pair blocks {I, J} (I <= J) of a set with nblk row
+// blocks are dealt out in rounds by the circle method over nt = nblk | 1
+// "teams" (one empty team nblk when nblk is even): in round r the team r
+// sits out and plays its diagonal block {r, r}, and the pairs {r + j, r - j}
+// (mod nt), j = 1 .. (nt - 1) / 2, meet.  Every row block is touched exactly
+// once per round, by an off-diagonal block, its diagonal, or a pair with the
+// empty team (whose only effect is a zero partial).  With nslot = min(nt, G)
+// for the plan's slot cap G, rounds [0, nslot) ("phase 0") store a row's
+// partial in slot r; the rounds of a later phase (nslot each) store theirs
+// in the scratch slot nslot + (r mod nslot), and a fold kernel then adds
+// those into slots [0, nslot) and clears them (a pass starts with cleared
+// scratch slots, so a block with zero partials need not store them there).
+// Each slot has one writer per launch and the launches run in order, so
+// every sum is taken in a fixed order and the results are deterministic;
+// the slots take nslot (2 nslot with later phases) x npad values per set,
+// which the cap keeps within a byte budget.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -71,7 +85,7 @@ struct SetDesc {
     int32_t seg0;           // first finalize segment of the set
     int32_t nseg;           // finalize segments of the set (kSegRows rows each)
     int32_t fsplit;         // column splits of the FP64 pair kernels
-    int32_t pad_;
+    int32_t nslot;          // partial slots per row of the symmetric pair kernels (+ nslot scratch with phases)
     // mixed-path exponent constants (base 2; see the pass kernels)
     float rho, kappa, cxi1, cxi2;
     float kappa_lo, cxi1_lo;  // low words: kappa + kappa_lo and cxi1 + cxi1_lo are the FP64 values
@@ -85,9 +99,63 @@ struct SetDesc {
     double mu0, tau_x, tau_t, theta, omega, h;
 };
 
+// One pair block of a launch: set, blocks I <= J (J == nblk: the empty
+// team), and kind = diagonal | scratch << 1 | slot << 2 (the slot its
+// partials are stored in; scratch: a scratch slot of a later phase).
 struct WorkItem {
-    int32_t set, I, J, kind;  // kind 0: off-diagonal pair block, 1: diagonal
+    int32_t set, I, J, kind;
 };
+
+// A run of work items of one launch: rounds [r0, r0 + nr) of set `set`,
+// either the off-diagonal blocks of each round ((nt - 1) / 2 per round, in
+// order j = 1, 2, ...) or its diagonal blocks (one per round).  first: index
+// of the run's first item within the launch.
+struct ItemRun {
+    int32_t set, r0, nr, diag, first, pad_;
+};
+
+// The work list of one pair launch: nruns runs (first increasing), nitems
+// items in all.
+struct Sched {
+    const ItemRun *runs;
+    int32_t nruns, nitems;
+};
+
+#ifdef __CUDACC__
+// Item k of a launch (0 <= k < sc.nitems): its run by binary search, then
+// its round and blocks by the circle method.
+__device__ __forceinline__ WorkItem decode_item(const SetDesc *sets, const Sched &sc, int k)
+{
+    int lo = 0, hi = sc.nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sc.runs[mid].first <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ItemRun ru = sc.runs[lo];
+    const int nt = sets[ru.set].nblk | 1, nslot = sets[ru.set].nslot;
+    const int local = k - ru.first;
+    int r, I, J;
+    if (ru.diag) {
+        r = ru.r0 + local;
+        I = J = r;
+    } else {
+        const int per = (nt - 1) >> 1;
+        r = ru.r0 + local / per;
+        const int j = local % per + 1;
+        int a = r + j, b = r - j;
+        a = a >= nt ? a - nt : a;
+        b = b < 0 ? b + nt : b;
+        I = min(a, b);
+        J = max(a, b);
+    }
+    const int slot = r < nslot ? r : nslot + r % nslot;
+    const int kind = (I == J ? 1 : 0) | (r >= nslot ? 2 : 0) | (slot << 2);
+    return WorkItem{ru.set, I, J, kind};
+}
+#endif
 
 // Device workspace views handed to the kernels.
 struct Work {
@@ -143,13 +211,13 @@ cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_
 // hk_pairs_mixed_*.cu.  pass: 1 rates, 2 gradient, 3 rates with Theta
 // sums, 4 rates with the self-excitation sums apart.  Shape: wr row groups
 // (block size 32 rows_per_lane(d) wr) and wc column groups of warps.
-cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const Sched &sc, int grid,
                                    int wr, int wc, cudaStream_t s);
 size_t pass_smem_bytes(int d, int pass, int wr, int wc);
 int pass_max_ctas_per_sm(int d, int pass, int wr, int wc);
 // hk_pairs_mixed_any.cu: the rate (1) or gradient (2) pass over every
 // dimension of a plan in one launch (warps row groups, one column group).
-cudaError_t launch_pair_pass_any_d(int pass, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+cudaError_t launch_pair_pass_any_d(int pass, const Work &w, const Sched &sc, int grid,
                                    int warps, cudaStream_t s);
 int pass_any_d_max_ctas_per_sm(int pass, int warps);
 
@@ -161,15 +229,19 @@ cudaError_t launch_pass2_fp64(const Work &w, int32_t set_lo, int32_t set_hi, int
                               cudaStream_t s);
 
 // hk_pairs_fp64_sym.cu: one CTA per pair block {I, J} (I <= J) of kSymRows
-// rows, dimension d; slot K of a row of block R holds block K's terms, so a
-// set's FP64 partials take nblk slots (fsplit = nblk).
+// rows, dimension d, over the items of one launch of the pair schedule
+// (fsplit = nslot slots).
 constexpr int kSymRows = 256;
-constexpr double kSymSlotBudget = 16.0 * 1024.0 * 1024.0 * 1024.0;  // bytes of partial slots
-cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, bool theta,
+cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const Sched &sc, bool theta,
                                   cudaStream_t s);
-cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, cudaStream_t s);
+cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const Sched &sc, cudaStream_t s);
 
 // hk_finalize.cu
+// After a later phase of the pair schedule: add the scratch slots of every
+// set of the launch's work list (its off-diagonal runs) into its slots and
+// clear them.  part: 0 P1 (vpc values per slot), 1 P2 (d), 2 F1 (1), 3 F1
+// with the Theta sums (6), 4 F2 (d).
+cudaError_t launch_fold_slots(const Work &w, const Sched &sc, int part, cudaStream_t s);
 // Rates, ell per set (out_loglik, nullable) and the FP64 recompute of the
 // flagged rows, one CTA per segment; sums: the rate pass's extra row sums.
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,

@@ -12,9 +12,10 @@
 // running sums travel one lane down per step (a systolic shuffle), so after
 // 32 steps lane l holds its own column's sums over the warp's 32 rows.  The
 // round schedule gives every chunk one writer per round and a fixed order of
-// warps.  A row of block R receives block K's contribution in slot K; the
-// diagonal block {R, R} adds both directions into slot R.  Every slot has
-// one writer and the finalize kernels add the slots in a fixed order.
+// warps.  Both blocks' rows receive the pair block's contribution in the
+// slot of its round of the pair schedule (the diagonal block adds both
+// directions into it): one writer per slot and launch, launches in order,
+// and the fold and finalize kernels add the slots in a fixed order.
 //
 // Cost model.  On this GPU the FP64 pipe completes about 1.7 operations
 // per SM per clock (DFMA, DADD and DMUL alike), some 70 times fewer than
@@ -168,7 +169,7 @@ __device__ __forceinline__ void chunk_pairs(const ChunkIn<D> &in, const double (
 
 // KIND 0: rates, 1: rates with the parameter-gradient sums, 2: gradient.
 template <int KIND, int D>
-__global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__restrict__ items, double one, double mz)
+__global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, Sched sc, double one, double mz)
 {
     constexpr int VR = SymVals<KIND, D>::R;
     constexpr int VC = SymVals<KIND, D>::C;
@@ -178,13 +179,37 @@ __global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__
     __shared__ double cA[KIND == 2 ? kB : 1];
     __shared__ int cte[kB];
     __shared__ double csum[VC][kB];
+    __shared__ WorkItem s_it;
 
-    const WorkItem it = items[blockIdx.x];
+    if (threadIdx.x == 0)
+        s_it = decode_item(w.sets, sc, blockIdx.x);
+    __syncthreads();
+    const WorkItem it = s_it;
     const SetDesc &S = w.sets[it.set];
     const int E = it.I, L = it.J;
     const bool diag = E == L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t R0 = S.row0;
+    // the block's slot (from its round of the pair schedule; a scratch slot
+    // in a later phase)
+    const int64_t slot = it.kind >> 2;
+    if (L >= S.nblk) {
+        // a pair with the schedule's empty team: block E's rows get a zero
+        // partial, stored in a slot of phase 0 (a scratch slot is zero
+        // already)
+        const int m = E * kB + tid;
+        if (!(it.kind & 2) && m < S.n) {
+            if (KIND == 2)
+#pragma unroll
+                for (int q = 0; q < D; ++q)
+                    w.F2[S.fpart2_0 + (slot * D + q) * S.npad + m] = 0.0;
+            else
+#pragma unroll
+                for (int v = 0; v < (KIND == 1 ? kPass1ThetaVals : 1); ++v)
+                    w.F1[S.fpart0 + (slot * (KIND == 1 ? kPass1ThetaVals : 1) + v) * S.npad + m] = 0.0;
+        }
+        return;
+    }
 
     // exponent constants (base 2) and prefactors
     const double ap = 0.5 * kLog2eSym / (S.tau_x * S.tau_x);
@@ -276,18 +301,18 @@ __global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__
         __syncthreads();
     }
 
-    // slot writes: rows of L get slot E, columns of E get slot L (the
-    // diagonal block adds both directions into one slot)
+    // slot writes: the rows of L and the columns of E, both in the block's
+    // slot (the diagonal block adds both directions into it)
     const int m = E * kB + tid;
     if (KIND == 0) {
-        const int64_t stride = (int64_t)1 * S.npad;  // one value per slot
+        double *f = w.F1 + S.fpart0 + slot * S.npad;  // one value per slot
         double rv = Cmu * racc[0] + Cxi * racc[1];
         if (diag)
             rv += Cmu * csum[0][tid];
         if (row_ok)
-            w.F1[S.fpart0 + (int64_t)E * stride + n] = rv;
+            f[n] = rv;
         if (!diag && m < S.n)
-            w.F1[S.fpart0 + (int64_t)L * stride + m] = Cmu * csum[0][tid];
+            f[m] = Cmu * csum[0][tid];
     } else if (KIND == 1) {
         double rv[6] = {Cmu * racc[0], Cxi * racc[1], Cmu * racc[2], Cmu * racc[3], Cxi * racc[4], Cxi * racc[5]};
         const double cv[6] = {Cmu * csum[0][tid], 0.0, Cmu * csum[1][tid], Cmu * csum[2][tid], 0.0, 0.0};
@@ -295,47 +320,49 @@ __global__ void __launch_bounds__(kB) sym_fp64_kernel(Work w, const WorkItem *__
 #pragma unroll
             for (int v = 0; v < 6; ++v)
                 rv[v] += cv[v];
+        double *f = w.F1 + S.fpart0 + slot * kPass1ThetaVals * S.npad;
         if (row_ok)
 #pragma unroll
             for (int v = 0; v < 6; ++v)
-                w.F1[S.fpart0 + ((int64_t)E * kPass1ThetaVals + v) * S.npad + n] = rv[v];
+                f[(int64_t)v * S.npad + n] = rv[v];
         if (!diag && m < S.n)
 #pragma unroll
             for (int v = 0; v < 6; ++v)
-                w.F1[S.fpart0 + ((int64_t)L * kPass1ThetaVals + v) * S.npad + m] = cv[v];
+                f[(int64_t)v * S.npad + m] = cv[v];
     } else {
         if (diag)
 #pragma unroll
             for (int q = 0; q < D; ++q)
                 racc[q] += csum[q][tid];
+        double *f = w.F2 + S.fpart2_0 + slot * D * S.npad;
         if (row_ok)
 #pragma unroll
             for (int q = 0; q < D; ++q)
-                w.F2[S.fpart2_0 + ((int64_t)E * D + q) * S.npad + n] = racc[q];
+                f[(int64_t)q * S.npad + n] = racc[q];
         if (!diag && m < S.n)
 #pragma unroll
             for (int q = 0; q < D; ++q)
-                w.F2[S.fpart2_0 + ((int64_t)L * D + q) * S.npad + m] = csum[q][tid];
+                f[(int64_t)q * S.npad + m] = csum[q][tid];
     }
 }
 
 template <int KIND>
-cudaError_t launch_kind(int d, const Work &w, const WorkItem *items, int32_t nitems, cudaStream_t s)
+cudaError_t launch_kind(int d, const Work &w, const Sched &sc, cudaStream_t s)
 {
-    if (nitems <= 0)
+    if (sc.nitems <= 0)
         return cudaSuccess;
-    const dim3 grid((unsigned)nitems);
+    const dim3 grid((unsigned)sc.nitems);
     // passed at run time so that the compiler keeps the fused forms
     const double one = 1.0, mz = -0.0;
     switch (d) {
-    case 1: sym_fp64_kernel<KIND, 1><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 2: sym_fp64_kernel<KIND, 2><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 3: sym_fp64_kernel<KIND, 3><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 4: sym_fp64_kernel<KIND, 4><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 5: sym_fp64_kernel<KIND, 5><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 6: sym_fp64_kernel<KIND, 6><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 7: sym_fp64_kernel<KIND, 7><<<grid, kB, 0, s>>>(w, items, one, mz); break;
-    case 8: sym_fp64_kernel<KIND, 8><<<grid, kB, 0, s>>>(w, items, one, mz); break;
+    case 1: sym_fp64_kernel<KIND, 1><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 2: sym_fp64_kernel<KIND, 2><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 3: sym_fp64_kernel<KIND, 3><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 4: sym_fp64_kernel<KIND, 4><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 5: sym_fp64_kernel<KIND, 5><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 6: sym_fp64_kernel<KIND, 6><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 7: sym_fp64_kernel<KIND, 7><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
+    case 8: sym_fp64_kernel<KIND, 8><<<grid, kB, 0, s>>>(w, sc, one, mz); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -343,15 +370,14 @@ cudaError_t launch_kind(int d, const Work &w, const WorkItem *items, int32_t nit
 
 }  // namespace
 
-cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, bool theta,
-                                  cudaStream_t s)
+cudaError_t launch_pass1_fp64_sym(int d, const Work &w, const Sched &sc, bool theta, cudaStream_t s)
 {
-    return theta ? launch_kind<1>(d, w, items, nitems, s) : launch_kind<0>(d, w, items, nitems, s);
+    return theta ? launch_kind<1>(d, w, sc, s) : launch_kind<0>(d, w, sc, s);
 }
 
-cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const WorkItem *items, int32_t nitems, cudaStream_t s)
+cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const Sched &sc, cudaStream_t s)
 {
-    return launch_kind<2>(d, w, items, nitems, s);
+    return launch_kind<2>(d, w, sc, s);
 }
 
 }  // namespace hk

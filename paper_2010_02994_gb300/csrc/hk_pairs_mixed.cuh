@@ -253,10 +253,11 @@ __device__ __forceinline__ void pair_item(const Work &w, const WorkItem wi, floa
 }
 
 // Persistent pair kernel of one dimension: CTAs take pair blocks from the
-// work list (an atomic counter) until it is exhausted.
+// work list (an atomic counter; every thread decodes the block pair) until
+// it is exhausted.
 template <int KIND, int D, int R, int WC>
 __global__ void __launch_bounds__(256)
-    pair_kernel(Work w, const WorkItem *__restrict__ items, int nitems)
+    pair_kernel(Work w, Sched sc)
 {
     constexpr int wc = WC;
     using T = KindTraits<KIND, D>;
@@ -278,9 +279,9 @@ __global__ void __launch_bounds__(256)
             s_item = atomicAdd(&w.pair_ctr[0], 1);
         __syncthreads();
         const int it = s_item;
-        if (it >= nitems)
+        if (it >= sc.nitems)
             break;
-        const WorkItem wi = items[it];
+        const WorkItem wi = decode_item(w.sets, sc, it);
 #include "hk_pair_item.inc"
         __syncthreads();
     }
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(256)
 // kernel's register count is the largest any dimension needs.
 template <int KIND>
 __global__ void __launch_bounds__(256)
-    pair_kernel_any_d(Work w, const WorkItem *__restrict__ items, int nitems)
+    pair_kernel_any_d(Work w, Sched sc)
 {
     extern __shared__ float4 smem4[];
     __shared__ int s_item;
@@ -310,9 +311,9 @@ __global__ void __launch_bounds__(256)
             s_item = atomicAdd(&w.pair_ctr[0], 1);
         __syncthreads();
         const int it = s_item;
-        if (it >= nitems)
+        if (it >= sc.nitems)
             break;
-        const WorkItem wi = items[it];
+        const WorkItem wi = decode_item(w.sets, sc, it);
         switch (w.sets[wi.set].d) {
         case 1: pair_item<KIND, 1, rows_per_lane(1), 1>(w, wi, smem4); break;
         case 2: pair_item<KIND, 2, rows_per_lane(2), 1>(w, wi, smem4); break;

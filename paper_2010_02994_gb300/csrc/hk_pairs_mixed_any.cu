@@ -46,15 +46,15 @@ int any_occupancy(int warps)
 
 }  // namespace
 
-cudaError_t launch_pair_pass_any_d(int pass, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+cudaError_t launch_pair_pass_any_d(int pass, const Work &w, const Sched &sc, int grid,
                                    int warps, cudaStream_t s)
 {
     if (pass == 1) {
-        pair_kernel_any_d<kRate><<<grid, warps * 32, any_smem<kRate>(warps), s>>>(w, items, nitems);
+        pair_kernel_any_d<kRate><<<grid, warps * 32, any_smem<kRate>(warps), s>>>(w, sc);
         return cudaGetLastError();
     }
     if (pass == 2) {
-        pair_kernel_any_d<kGrad><<<grid, warps * 32, any_smem<kGrad>(warps), s>>>(w, items, nitems);
+        pair_kernel_any_d<kGrad><<<grid, warps * 32, any_smem<kGrad>(warps), s>>>(w, sc);
         return cudaGetLastError();
     }
     return cudaErrorInvalidValue;

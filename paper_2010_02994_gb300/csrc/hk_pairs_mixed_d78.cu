@@ -6,7 +6,7 @@ HK_INSTANTIATE_MIXED(7)
 HK_INSTANTIATE_MIXED(8)
 
 #define HK_EXTERN_MIXED(D)                                                                                      \
-    extern template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, int,      \
+    extern template cudaError_t launch_pass_t<D>(int, const Work &, const Sched &, int, int, int,      \
                                                  cudaStream_t);                                                \
     extern template size_t smem_t<D>(int, int, int);                                                            \
     extern template int occupancy_t<D>(int, int, int);
@@ -30,10 +30,10 @@ HK_EXTERN_MIXED(6)
     default: break;                                                                                            \
     }
 
-cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const WorkItem *items, int32_t nitems, int grid,
+cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const Sched &sc, int grid,
                                    int wr, int wc, cudaStream_t s)
 {
-    HK_SWITCH_D(d, launch_pass_t<D>(pass, w, items, nitems, grid, wr, wc, s))
+    HK_SWITCH_D(d, launch_pass_t<D>(pass, w, sc, grid, wr, wc, s))
     return cudaErrorInvalidValue;
 }
 

@@ -21,38 +21,38 @@ constexpr bool kind_splits_columns()
 }
 
 template <int KIND, int D, int WC>
-cudaError_t launch_wc_t(const Work &w, const WorkItem *items, int nitems, int grid, int wr, cudaStream_t s)
+cudaError_t launch_wc_t(const Work &w, const Sched &sc, int grid, int wr, cudaStream_t s)
 {
     constexpr int R = rows_per_lane(D);
     const size_t smem = pair_smem_bytes<KIND, D, R>(wr * WC, WC);
-    pair_kernel<KIND, D, R, WC><<<grid, wr * WC * 32, smem, s>>>(w, items, nitems);
+    pair_kernel<KIND, D, R, WC><<<grid, wr * WC * 32, smem, s>>>(w, sc);
     return cudaGetLastError();
 }
 
 template <int KIND, int D>
-cudaError_t launch_kind_t(const Work &w, const WorkItem *items, int nitems, int grid, int wr, int wc,
+cudaError_t launch_kind_t(const Work &w, const Sched &sc, int grid, int wr, int wc,
                           cudaStream_t s)
 {
     if (!kind_splits_columns<KIND>() || wc == 1)
-        return launch_wc_t<KIND, D, 1>(w, items, nitems, grid, wr, s);
+        return launch_wc_t<KIND, D, 1>(w, sc, grid, wr, s);
     if (wc == 2)
-        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 2 : 1>(w, items, nitems, grid, wr, s);
+        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 2 : 1>(w, sc, grid, wr, s);
     if (wc == 4)
-        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 4 : 1>(w, items, nitems, grid, wr, s);
+        return launch_wc_t<KIND, D, kind_splits_columns<KIND>() ? 4 : 1>(w, sc, grid, wr, s);
     return cudaErrorInvalidValue;
 }
 
 template <int D>
-cudaError_t launch_pass_t(int pass, const Work &w, const WorkItem *items, int nitems, int grid, int wr, int wc,
+cudaError_t launch_pass_t(int pass, const Work &w, const Sched &sc, int grid, int wr, int wc,
                           cudaStream_t s)
 {
     if (pass == 1)
-        return launch_kind_t<kRate, D>(w, items, nitems, grid, wr, wc, s);
+        return launch_kind_t<kRate, D>(w, sc, grid, wr, wc, s);
     if (pass == 2)
-        return launch_kind_t<kGrad, D>(w, items, nitems, grid, wr, wc, s);
+        return launch_kind_t<kGrad, D>(w, sc, grid, wr, wc, s);
     if (pass == 4)
-        return launch_kind_t<kRateXi, D>(w, items, nitems, grid, wr, 1, s);
-    return launch_kind_t<kRateTheta, D>(w, items, nitems, grid, wr, 1, s);
+        return launch_kind_t<kRateXi, D>(w, sc, grid, wr, 1, s);
+    return launch_kind_t<kRateTheta, D>(w, sc, grid, wr, 1, s);
 }
 
 template <int D>
@@ -120,7 +120,7 @@ int occupancy_t(int pass, int wr, int wc)
 }
 
 #define HK_INSTANTIATE_MIXED(D)                                                                                \
-    template cudaError_t launch_pass_t<D>(int, const Work &, const WorkItem *, int, int, int, int, cudaStream_t); \
+    template cudaError_t launch_pass_t<D>(int, const Work &, const Sched &, int, int, int, cudaStream_t); \
     template size_t smem_t<D>(int, int, int);                                                                    \
     template int occupancy_t<D>(int, int, int);
 

@@ -181,7 +181,7 @@ struct RowRate {
 __device__ __forceinline__ RowRate finalize_rate_row(const Work &w, const SetDesc &S, int s, int i, bool write)
 {
     const int64_t r = S.row0 + i;
-    const double sum = ordered_strided_sum(w.P1 + S.part0 + i, S.nblk, S.npad);
+    const double sum = ordered_strided_sum(w.P1 + S.part0 + i, S.nslot, S.npad);
     RowRate out{!(sum >= S.s_min), 0.0};
     if (!write)
         return out;
@@ -310,7 +310,7 @@ __device__ __forceinline__ void finalize_grad_row(const Work &w, const SetDesc &
     const int64_t r = S.row0 + i;
     double gv[kMaxD];
     // all coordinates together: eight slots of each in flight per round trip
-    ordered_strided_sums_d(d, w.P2 + S.part2_0 + i, S.npad, S.nblk, (int64_t)d * S.npad, gv);
+    ordered_strided_sums_d(d, w.P2 + S.part2_0 + i, S.npad, S.nslot, (int64_t)d * S.npad, gv);
 #pragma unroll
     for (int q = 0; q < kMaxD; ++q)
         if (q < d)
