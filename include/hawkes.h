@@ -159,7 +159,17 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            slots and scratch slots as fit (at least enough
  *                            for 16 pair blocks per SM in each phase).  A
  *                            different G changes the order of the sums
- *                            (results within rounding)  */
+ *                            (results within rounding)
+ *   HAWKES_OPT_BMDS_FUSED    1: a mixed-precision BMDS-Hawkes HMC
+ *                            trajectory evaluates the BMDS gradient inside
+ *                            the Hawkes gradient pass (one pair loop for both
+ *                            terms, from a time-ordered FP32 copy of Y that
+ *                            the call makes: 4 npad^2 bytes of device
+ *                            memory) and runs the BMDS kernels only for
+ *                            ell_B at the trajectory's two ends; 0: the BMDS
+ *                            kernels run beside every Hawkes evaluation on a
+ *                            second stream; 2 (default): 1 from 8,192 events
+ *                            on, else 0 (the faster on GB300 at D = 6)  */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,
@@ -170,7 +180,8 @@ enum {
     HAWKES_OPT_FP64_ORDERED = 7,
     HAWKES_OPT_COL_GROUPS = 8,
     HAWKES_OPT_ONE_LAUNCH = 9,
-    HAWKES_OPT_PARTIAL_SLOTS = 10
+    HAWKES_OPT_PARTIAL_SLOTS = 10,
+    HAWKES_OPT_BMDS_FUSED = 11
 };
 hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t value);
 

@@ -24,7 +24,7 @@ STATUS_NAMES = {
 PREC = {"mixed": 0, "fp64": 1}
 OPTIONS = {"block_warps": 1, "ctas_per_sm": 2, "profile": 3, "times_sorted": 4, "mixed_fixup_exp": 5,
            "skip_far_blocks": 6, "fp64_ordered": 7, "col_groups": 8, "one_launch": 9,
-           "partial_slots": 10}
+           "partial_slots": 10, "bmds_fused": 11}
 
 # every function declared in include/hawkes.h
 EXPORTED = (

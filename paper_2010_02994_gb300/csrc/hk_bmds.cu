@@ -231,6 +231,36 @@ Layout layout(int64_t n, int d, bool fp64)
 
 }  // namespace
 
+namespace {
+
+__global__ void sort_y_kernel(const void *__restrict__ Y, int y_f32, const int32_t *__restrict__ perm, int64_t n,
+                              int64_t npad, float *__restrict__ Ys)
+{
+    const int64_t i = blockIdx.x;
+    const int64_t a = i < n ? perm[i] : -1;
+    for (int64_t j = threadIdx.x; j < npad; j += blockDim.x) {
+        float v = 0.0f;
+        if (a >= 0 && j < n && j != i) {
+            const int64_t b = perm[j];
+            const int64_t hi = a > b ? a : b, lo = a > b ? b : a;
+            v = y_f32 ? static_cast<const float *>(Y)[hi * n + lo]
+                      : __double2float_rn(static_cast<const double *>(Y)[hi * n + lo]);
+        }
+        Ys[i * npad + j] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bmds_sort_y(const void *Y, bool y_f32, const int32_t *perm, int64_t n, int64_t npad, float *Ys,
+                               cudaStream_t s)
+{
+    if (npad <= 0)
+        return cudaSuccess;
+    sort_y_kernel<<<(unsigned)npad, 256, 0, s>>>(Y, y_f32 ? 1 : 0, perm, n, npad, Ys);
+    return cudaGetLastError();
+}
+
 size_t bmds_workspace_bytes(int64_t n, int d, bool fp64) { return layout(n, d, fp64).bytes; }
 
 

@@ -137,6 +137,26 @@ __device__ __forceinline__ void pair_terms(float q, float y, const Consts<float>
     coef = (ratio * k.inv_sigma - e * k.inv_s2) * inv_delta;
 }
 
+// The gradient coefficient alone (coef above) in FP32, for the pair loop of
+// the Hawkes gradient pass that also carries this term (the BMDS-Hawkes
+// potential of Section 3): the same steps without log Phi and the value and
+// variance sums.
+__device__ __forceinline__ float grad_coef(float q, float y, float inv_sigma, float inv_s2)
+{
+    const float inv_delta = q > 0.0f ? rsqrtf(q) : 0.0f;
+    const float delta = q * inv_delta;
+    const float z = delta * inv_sigma;
+    const float E = ex2_approx(z * (z * -0.72134752044448170f));
+    const float zc = fminf(z, 14.0f);
+    const float P = fmaf(fmaf(fmaf(fmaf(kTailP[4], zc, kTailP[3]), zc, kTailP[2]), zc, kTailP[1]), zc, kTailP[0]);
+    const float B =
+        fmaf(fmaf(fmaf(fmaf(fmaf(kTailB[5], zc, kTailB[4]), zc, kTailB[3]), zc, kTailB[2]), zc, kTailB[1]), zc,
+             kTailB[0]);
+    const float D = B - E * P;
+    const float ratio = (0.39894228040143268f * E) * (B * rcp_approx(D));  // phi(z) / Phi(z)
+    return (ratio * inv_sigma - (y - delta) * inv_s2) * inv_delta;
+}
+
 // The same terms with every operation in FP64.
 __device__ __forceinline__ void pair_terms(double q, double y, const Consts<double> &k, double &val, double &ssum,
                                            double &coef)

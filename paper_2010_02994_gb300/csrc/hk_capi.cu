@@ -44,6 +44,11 @@ constexpr int kCtlSetFlags = 40;
 constexpr double kSlotBudget = 1024.0 * 1024.0 * 1024.0;
 constexpr double kMinPhaseItems = 16.0;
 
+// BMDS-Hawkes HMC: the BMDS term rides in the gradient pass from this many
+// events on (GB300, D = 6, 20 steps: 3.00 against 2.88 ms per trajectory at
+// N = 4,733, 7.95 against 8.51 at 10,000, 27.9 against 28.8 at 20,000).
+constexpr int64_t kFusedBmdsMinN = 8192;
+
 struct DeviceBuffer {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -113,9 +118,10 @@ struct hawkes_ctx {
     size_t ws_generation = 0;
     DeviceBuffer bmds_ws;  // BMDS partial-sum slots
     DeviceBuffer bmds_hmc;  // BMDS-Hawkes HMC: locations and BMDS gradient in the caller's order, ell_B
+    DeviceBuffer bmds_ys;   // BMDS-Hawkes HMC with the fused gradient pass: Y in time order (FP32)
     // options
     int opt_warps = 0, opt_cols = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
-    int opt_fp64_ordered = 0, opt_one_launch = 0, opt_slots = 0;
+    int opt_fp64_ordered = 0, opt_one_launch = 0, opt_slots = 0, opt_bmds_fused = 2;
     int occ_any[3][4] = {};  // CTAs per SM of the one-launch pair kernels: [pass 1..2][log2 warps]
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
@@ -128,8 +134,8 @@ struct hawkes_ctx {
     cudaEvent_t fork_ev = nullptr, join_ev[kMaxD + 1] = {};
     cudaStream_t bmds_side = nullptr;  // the BMDS branch of a BMDS-Hawkes leapfrog step
     cudaEvent_t bmds_fork = nullptr, bmds_join = nullptr;
-    // CTAs per SM of the pair kernels: [d][pass 1..4][log2 wr][log2 wc] (-1: not yet asked)
-    int occ[kMaxD + 1][5][4][4];
+    // CTAs per SM of the pair kernels: [d][pass 1..5][log2 wr][log2 wc] (-1: not yet asked)
+    int occ[kMaxD + 1][6][4][4];
     static constexpr int kBuckets = 32;
     int tune_warps[kMaxD + 1][kBuckets] = {};  // row groups; 0: no entry
     int tune_cols[kMaxD + 1][kBuckets] = {};   // column groups
@@ -296,6 +302,8 @@ void describe_set(SetDesc &S, int64_t n, int d, const hawkes_params &p, double f
     S.kappa_lo = (float)(kappa - (double)S.kappa);
     S.cxi1 = (float)cxi1;
     S.cxi1_lo = (float)(cxi1 - (double)S.cxi1);
+    S.bq = (float)(1.0 / (S.kx * S.kx));
+    S.bc = (float)(p.tau_x * p.tau_x);
     S.cxi2 = (float)(cxi1 + std::log2(rho));
     S.cxi2_d = cxi1 + std::log2(rho);
     S.s_min = std::ldexp(1.0, (int)fixup_exp);
@@ -736,7 +744,7 @@ hawkes_status enqueue_prep(hawkes_ctx *ctx, const Plan &pl, const double *t, con
 // dimension's tail with another's blocks, while its phases stay in order.
 hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaStream_t s)
 {
-    const int fold_part = pass == 2 ? 1 : 0;
+    const int fold_part = pass == 2 || pass == 5 ? 1 : 0;
     if (pl.one_launch && (pass == 1 || pass == 2)) {
         int warps = 1;
         for (int d : pl.dims)
@@ -778,7 +786,8 @@ hawkes_status enqueue_pair_pass(hawkes_ctx *ctx, const Plan &pl, int pass, cudaS
         wd.pair_ctr = ctx->ctl + kCtlDimCounters + 2 * d;  // [0] work taken, [1] CTAs done
         const Sched sc{ctx->d_runs + L.run0, L.nruns, L.nitems};
         cudaStream_t ls = fork ? ctx->side[d] : s;
-        HK_TRY(launch_pair_pass_mixed(pass, d, wd, sc, grid, wr, wc, ls), pass == 2 ? "gradient pass" : "rate pass");
+        HK_TRY(launch_pair_pass_mixed(pass, d, wd, sc, grid, wr, wc, ls),
+               pass == 2 || pass == 5 ? "gradient pass" : "rate pass");
         if (L.phase > 0)
             HK_TRY(launch_fold_slots(ctx->w, sc, fold_part, ls), "fold slots");
     }
@@ -832,9 +841,10 @@ hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool 
 // Pass 1 .. ell (and pass 2 .. gradient) on packed rows:
 //   rate pass (with the six Theta sums when wanted), finalize rows (rates,
 //   FP64 recompute of flagged rows, ell per set), Theta gradient, gradient
-//   pass, finalize gradient.
+//   pass (grad_pass 5: with the BMDS term), finalize gradient.
 hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
-                           double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr)
+                           double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr,
+                           int grad_pass = 2)
 {
     const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
@@ -867,7 +877,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         ProfEvent pe{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pe, 1, pl.pairs);
-        st = fp64 ? enqueue_fp64_pass(ctx, pl, 2, false, s) : enqueue_pair_pass(ctx, pl, 2, s);
+        st = fp64 ? enqueue_fp64_pass(ctx, pl, 2, false, s) : enqueue_pair_pass(ctx, pl, grad_pass, s);
         if (st != HAWKES_OK)
             return st;
         if (ctx->opt_profile)
@@ -973,7 +983,7 @@ hawkes_status hawkes_ctx_create(hawkes_ctx **out, int32_t device, int64_t max_n,
     // occupancy of every pair-kernel shape, asked now (it also sets each
     // kernel's shared-memory limit) rather than during a stream capture
     for (int d = 1; d <= kMaxD; ++d)
-        for (int pass = 1; pass <= 4; ++pass)
+        for (int pass = 1; pass <= 5; ++pass)
             for (int a = 0; a < 4; ++a)
                 for (int b = 0; b < 4; ++b)
                     ctx->occ[d][pass][a][b] = (1 << (a + b)) <= 8 ? pass_max_ctas_per_sm(d, pass, 1 << a, 1 << b) : 0;
@@ -1022,6 +1032,8 @@ void hawkes_ctx_destroy(hawkes_ctx *ctx)
         cudaFree(ctx->bmds_ws.ptr);
     if (ctx->bmds_hmc.ptr)
         cudaFree(ctx->bmds_hmc.ptr);
+    if (ctx->bmds_ys.ptr)
+        cudaFree(ctx->bmds_ys.ptr);
     if (ctx->ctl)
         cudaFree(ctx->ctl);
     delete ctx;
@@ -1090,6 +1102,11 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
         return HAWKES_OK;
     case HAWKES_OPT_ONE_LAUNCH:
         ctx->opt_one_launch = value ? 1 : 0;
+        return HAWKES_OK;
+    case HAWKES_OPT_BMDS_FUSED:
+        if (value < 0 || value > 2)
+            return fail(ctx, HAWKES_ERR_INVALID_ARG, "BMDS fusion must be 0, 1 or 2");
+        ctx->opt_bmds_fused = (int)value;
         return HAWKES_OK;
     case HAWKES_OPT_PARTIAL_SLOTS:
         if (value < 0 || value > (int64_t)1 << 30)
@@ -1460,6 +1477,23 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
 
     // BMDS term: its workspace and the caller-order buffers exist before any capture
     double *bx = nullptr, *bg = nullptr, *bl = nullptr;
+    // mixed precision: the gradient pass carries the BMDS term (pass 5), from
+    // a time-ordered FP32 copy of Y made here; the BMDS kernels then run only
+    // for ell_B at the two ends of the trajectory.  By default from
+    // kFusedBmdsMinN events on: below it the GPU has room to run the BMDS
+    // kernels beside the Hawkes passes, which was faster.
+    const bool want_fused = ctx->opt_bmds_fused == 1 || (ctx->opt_bmds_fused == 2 && counts[0] >= kFusedBmdsMinN);
+    const bool fused = bmds && !fp64 && want_fused && nsets == 1 &&
+                       occupancy(ctx, dims[0], 5, pl.wr_by_d[dims[0]], 1) > 0;
+    float *ys = nullptr;
+    if (fused) {
+        const int64_t npad = pl.sets[0].npad;
+        if ((st = grow_buffer(ctx, ctx->bmds_ys, sizeof(float) * npad * npad, "time-ordered Y", 0)) != HAWKES_OK)
+            return st;
+        ys = static_cast<float *>(ctx->bmds_ys.ptr);
+        HK_TRY(launch_bmds_sort_y(bmds->Y, bmds->y_f32, w.perm, counts[0], npad, ys, s), "time-ordered Y");
+        ++ctx->launches_own;
+    }
     if (bmds) {
         const int64_t nd = counts[0] * dims[0];
         if ((st = grow_buffer(ctx, ctx->bmds_ws, bmds_workspace_bytes(counts[0], dims[0], fp64), "BMDS workspace",
@@ -1481,11 +1515,25 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
         key.push_back((int64_t)reinterpret_cast<intptr_t>(bmds->Y));
         key.push_back(bmds->y_f32 ? 2 : 1);
         key.push_back(sbits);
+        key.push_back((int64_t)reinterpret_cast<intptr_t>(ys));
     }
     for (int k = 0; k < ns; ++k) {
         key.push_back(counts[k]);
         key.push_back(dims[k]);
         key.push_back(pl.sets[k].B);
+    }
+    // the fused pass's inputs travel in the Work copied into each launch;
+    // later calls must not see them
+    struct ClearBmdsTerm {
+        Work &w;
+        ~ClearBmdsTerm() { w.ysort = nullptr; }
+    } clear_bmds_term{w};
+    if (fused) {
+        w.ysort = ys;
+        w.bmds_inv_sigma_d = 1.0 / std::sqrt(bmds->sigma2);
+        w.bmds_inv_s2_d = 1.0 / bmds->sigma2;
+        w.bmds_inv_sigma = (float)w.bmds_inv_sigma_d;
+        w.bmds_inv_s2 = (float)w.bmds_inv_s2_d;
     }
     if (!ctx->hmc.exec || ctx->hmc.key != key || ctx->opt_profile) {
         if (ctx->hmc.exec) {
@@ -1510,8 +1558,10 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
             HK_TRY(cudaEventCreateWithFlags(&ctx->bmds_fork, cudaEventDisableTiming), "BMDS fork event");
             HK_TRY(cudaEventCreateWithFlags(&ctx->bmds_join, cudaEventDisableTiming), "BMDS join event");
         }
-        auto fork_bmds = [&]() -> hawkes_status {
-            if (!bmds)
+        // the BMDS gradient is carried by the fused gradient pass; ell_B is
+        // needed only for H0 and H1 (the first and last evaluation)
+        auto fork_bmds = [&](bool ends) -> hawkes_status {
+            if (!bmds || (fused && !ends))
                 return HAWKES_OK;
             cudaStream_t bs = ctx->bmds_side;
             HK_TRY(cudaEventRecord(ctx->bmds_fork, es), "BMDS fork");
@@ -1519,30 +1569,32 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
             HK_TRY(launch_to_caller(w, ctx->d_set_row0, w.x64, bx, pl.total_rows, bs), "BMDS locations");
             ++ctx->launches_own;
             HK_TRY(launch_bmds(bmds->Y, bmds->y_f32, bx, counts[0], dims[0], bmds->sigma2, fp64, ctx->bmds_ws.ptr,
-                               reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, bg, nullptr, bs,
-                               &ctx->launches_own),
+                               reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, fused ? nullptr : bg,
+                               nullptr, bs, &ctx->launches_own),
                    "BMDS kernels");
             HK_TRY(cudaEventRecord(ctx->bmds_join, bs), "BMDS join");
             return HAWKES_OK;
         };
-        auto join_bmds = [&]() -> hawkes_status {
-            if (!bmds)
+        auto join_bmds = [&](bool ends) -> hawkes_status {
+            if (!bmds || (fused && !ends))
                 return HAWKES_OK;
             HK_TRY(cudaStreamWaitEvent(es, ctx->bmds_join, 0), "BMDS join wait");
-            HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, bg, ctx->hg, pl.total_rows, bl, es), "BMDS gradient");
+            HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, fused ? nullptr : bg, ctx->hg, pl.total_rows, bl, es),
+                   "BMDS gradient");
             ++ctx->launches_own;
             return HAWKES_OK;
         };
+        const int grad_pass = fused ? 5 : 2;
         auto body = [&]() -> hawkes_status {
             hawkes_status r;
             // the first evaluation follows the prologue, whose reset of the
             // per-evaluation control words precedes the graph; each later one
             // follows a drift kernel that clears them
-            if ((r = fork_bmds()) != HAWKES_OK)
+            if ((r = fork_bmds(true)) != HAWKES_OK)
                 return r;
-            if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+            if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es, nullptr, grad_pass)) != HAWKES_OK)
                 return r;
-            if ((r = join_bmds()) != HAWKES_OK)
+            if ((r = join_bmds(true)) != HAWKES_OK)
                 return r;
             HK_TRY(launch_energy(w, ctx->hp, d_H0, ctx->hscal + 4 * ns, es), "H0");
             for (int32_t k = 0; k < n_steps; ++k) {
@@ -1550,11 +1602,13 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                                          box ? ctx->hhi : nullptr, d_eps, pl.total_rows, k == 0 ? 1 : 2, !fp64,
                                          d_bad, es),
                        "leapfrog drift");
-                if ((r = fork_bmds()) != HAWKES_OK)
+                const bool last = k == n_steps - 1;
+                if ((r = fork_bmds(last)) != HAWKES_OK)
                     return r;
-                if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es)) != HAWKES_OK)
+                if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es, nullptr, grad_pass)) !=
+                    HAWKES_OK)
                     return r;
-                if ((r = join_bmds()) != HAWKES_OK)
+                if ((r = join_bmds(last)) != HAWKES_OK)
                     return r;
             }
             if (n_steps > 0)

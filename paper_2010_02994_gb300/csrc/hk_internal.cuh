@@ -89,6 +89,7 @@ struct SetDesc {
     // mixed-path exponent constants (base 2; see the pass kernels)
     float rho, kappa, cxi1, cxi2;
     float kappa_lo, cxi1_lo;  // low words: kappa + kappa_lo and cxi1 + cxi1_lo are the FP64 values
+    float bq, bc;     // BMDS term of the gradient pass: 1/kx^2 (scaled q -> squared distance), tau_x^2
     double cxi2_d;    // c_xi1 + log2(rho) in FP64
     // FP64 constants
     double kx, kt;    // coordinate scalings sqrt(log2(e)/2)/tau_x and /tau_t
@@ -189,6 +190,12 @@ struct Work {
     unsigned *status;    // sticky device status
     int32_t *set_done;   // finalizing CTAs done per set: the last one writes ell (returns to zero)
     int32_t sm_count;    // SMs of the device
+    // the BMDS term carried by the gradient pass of a BMDS-Hawkes trajectory
+    // (one set; null ysort: none): Y in time order (FP32, npad x npad),
+    // 1/sigma and 1/sigma2 in FP32 (pair kernel) and FP64 (flagged rows)
+    const float *ysort;
+    float bmds_inv_sigma, bmds_inv_s2;
+    double bmds_inv_sigma_d, bmds_inv_s2_d;
 };
 
 // ------------------------------------------------------------ launchers --
@@ -209,8 +216,9 @@ cudaError_t launch_pack_rows(const Work &w, const double *X, const double *keys_
                              int64_t total_rows, const int64_t *set_row0, cudaStream_t s);
 
 // hk_pairs_mixed_*.cu.  pass: 1 rates, 2 gradient, 3 rates with Theta
-// sums, 4 rates with the self-excitation sums apart.  Shape: wr row groups
-// (block size 32 rows_per_lane(d) wr) and wc column groups of warps.
+// sums, 4 rates with the self-excitation sums apart, 5 gradient with the BMDS
+// term.  Shape: wr row groups (block size 32 rows_per_lane(d) wr) and wc
+// column groups of warps.
 cudaError_t launch_pair_pass_mixed(int pass, int d, const Work &w, const Sched &sc, int grid,
                                    int wr, int wc, cudaStream_t s);
 size_t pass_smem_bytes(int d, int pass, int wr, int wc);
@@ -274,6 +282,11 @@ cudaError_t launch_add_caller_term(const Work &w, const int64_t *set_row0, const
 
 // hk_bmds.cu (BMDS likelihood of Eq. (4) and its gradients)
 size_t bmds_workspace_bytes(int64_t n, int d, bool fp64);
+// Y in time order for the gradient pass with the BMDS term: Ys[i npad + j] =
+// Y[perm_i][perm_j] in FP32 (read from the lower triangle), 0 on the
+// diagonal and for padded rows or columns (i or j >= n).
+cudaError_t launch_bmds_sort_y(const void *Y, bool y_f32, const int32_t *perm, int64_t n, int64_t npad, float *Ys,
+                               cudaStream_t s);
 cudaError_t launch_bmds(const void *Y, bool y_f32, const double *X, int64_t n, int d, double sigma2, bool fp64, void *ws,
                         unsigned *status, double *out_loglik, double *out_grad, double *out_grad_sigma2,
                         cudaStream_t s, int64_t *launches);

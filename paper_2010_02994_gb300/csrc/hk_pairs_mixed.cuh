@@ -50,21 +50,32 @@
 // index test only in the chunks that can contain them.
 #pragma once
 
+#include "hk_bmds.cuh"
 #include "hk_internal.cuh"
 
 namespace hk {
 
 // kRateXi: the rate pass that also keeps the self-excitation sum of each row
 // apart (plane 0: background terms, plane 1: self-excitation terms).
-enum PairKind : int { kRate = 0, kRateTheta = 1, kGrad = 2, kRateXi = 3 };
+// kGradB: the gradient pass that also carries the BMDS term of Eq. (4) (the
+// BMDS-Hawkes potential of Section 3): every unordered pair of distinct
+// events adds coef_B (x_m - x_n) to g_n (and the opposite to g_m) beside its
+// Hawkes term, with the observed distance y from a time-ordered copy of Y.
+enum PairKind : int { kRate = 0, kRateTheta = 1, kGrad = 2, kRateXi = 3, kGradB = 4 };
+
+template <int KIND>
+__host__ __device__ constexpr bool grad_kind()
+{
+    return KIND == kGrad || KIND == kGradB;
+}
 
 template <int KIND, int D>
 struct KindTraits {
-    static constexpr int VR = KIND == kGrad ? D : (KIND == kRateTheta ? 3 : 1);   // values per row
-    static constexpr int VC = KIND == kGrad ? D : (KIND == kRateTheta ? 6 : (KIND == kRateXi ? 2 : 1));  // per column
+    static constexpr int VR = grad_kind<KIND>() ? D : (KIND == kRateTheta ? 3 : 1);   // values per row
+    static constexpr int VC = grad_kind<KIND>() ? D : (KIND == kRateTheta ? 6 : (KIND == kRateXi ? 2 : 1));  // per column
     // staged fields: coordinates (hi, lo), time, then b (rate kinds) or
     // w_m and b (gradient)
-    static constexpr int NF = KIND == kGrad ? 2 * D + 3 : 2 * D + 2;
+    static constexpr int NF = grad_kind<KIND>() ? 2 * D + 3 : 2 * D + 2;
     static constexpr int NPP = (NF + 3) / 4;                                       // staged float4 planes
 };
 
@@ -101,6 +112,17 @@ struct PairConsts {
     float rho, kappa, cxi;
 };
 
+// The BMDS term of kGradB: q scale 1/kx^2 (scaled q -> delta^2), coefficient
+// scale tau_x^2 (a BMDS coefficient in the scaled gradient's units),
+// 1/sigma and 1/sigma2; ys: this lane's row of the chunk's Y in shared
+// memory (row r of the lane at ys[1024 r]), row0: the warp's first row, n:
+// events of the set.
+struct BmdsIn {
+    float qscale, cscale, inv_sigma, inv_s2;
+    const float *ys;
+    int row0, n;
+};
+
 // c + k t for the two-word constant k = k_hi + k_lo (and c = c_hi + c_lo),
 // with the error of one FP32 rounding of the result: the product's rounding
 // error is recovered exactly by an FMA and added back with the low words.
@@ -111,11 +133,34 @@ __device__ __forceinline__ float kt_plus_c(float k_hi, float k_lo, float t, floa
     return (c_hi + p) + fmaf(k_lo, t, e + c_lo);
 }
 
+// Asynchronous global -> shared copies (16 bytes each, bypassing L1) for the
+// Y tiles of kGradB: a warp's 32 R rows x 32 columns, row stride ld floats
+// in global memory, 32 in shared memory; lanes 8k .. 8k + 7 copy one row.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int R>
+__device__ __forceinline__ void stage_y_async(float *dst, const float *src, int64_t ld, int lane)
+{
+#pragma unroll 4
+    for (int k = 0; k < R * 8; ++k) {
+        const int v = 32 * k + lane, row = v >> 3, seg = v & 7;
+        cp_async16(dst + 32 * row + 4 * seg, src + (int64_t)row * ld + 4 * seg);
+    }
+}
+
 // One pair: its contributions to the row's values (part) and to the
 // travelling column accumulator (acc).  cf holds the staged column fields.
 template <int KIND, int D>
 __device__ __forceinline__ void pair_update(const float *cf, const float *rx, float rt, float rw, float ra,
-                                            const PairConsts &k, bool valid, float *part, float *acc)
+                                            const PairConsts &k, bool valid, float *part, float *acc,
+                                            const BmdsIn &kb, float y, bool valid_b)
 {
     float dx[D], q;
 #pragma unroll
@@ -169,7 +214,11 @@ __device__ __forceinline__ void pair_update(const float *cf, const float *rx, fl
             mu = 0.0f;
             xw = 0.0f;
         }
-        const float c = fmaf(mu, rw + cf[2 * D + 1], xw);
+        float c = fmaf(mu, rw + cf[2 * D + 1], xw);
+        if (KIND == kGradB) {
+            const float cb = bmds::grad_coef(q * kb.qscale, y, kb.inv_sigma, kb.inv_s2);
+            c = valid_b ? fmaf(cb, kb.cscale, c) : c;
+        }
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             part[d] = fmaf(c, dx[d], part[d]);
@@ -186,7 +235,7 @@ __device__ __forceinline__ void chunk_steps(const float4 *__restrict__ pv, int s
                                             const int *__restrict__ te, const float (&rx)[R][2 * D],
                                             const float (&rt)[R], const float (&rw)[R], const float (&ra)[R],
                                             const PairConsts &k, float (&part)[R][KindTraits<KIND, D>::VR],
-                                            float (&acc)[KindTraits<KIND, D>::VC])
+                                            float (&acc)[KindTraits<KIND, D>::VC], const BmdsIn &kb)
 {
     using T = KindTraits<KIND, D>;
     // unrolled by 16: 1% shorter than 8 for the gradient pass at N = 1e5 on
@@ -206,7 +255,11 @@ __device__ __forceinline__ void chunk_steps(const float4 *__restrict__ pv, int s
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const bool valid = MASKED ? (m >= te[32 * r + lane]) : true;
-            pair_update<KIND, D>(cf, rx[r], rt[r], rw[r], ra[r], k, valid, part[r], acc);
+            // BMDS: every pair of distinct events once (m later in the
+            // order than the row), padded columns excluded
+            const bool valid_b = KIND == kGradB && MASKED ? (m < kb.n && m > kb.row0 + 32 * r + lane) : true;
+            const float y = KIND == kGradB ? kb.ys[32 * 32 * r + ((lane + j) & 31)] : 0.0f;
+            pair_update<KIND, D>(cf, rx[r], rt[r], rw[r], ra[r], k, valid, part[r], acc, kb, y, valid_b);
         }
 #pragma unroll
         for (int v = 0; v < T::VC; ++v)
@@ -225,7 +278,8 @@ constexpr size_t pair_smem_bytes(int W, int WC)
     return (size_t)W * T::NPP * 64 * sizeof(float4)      // staged chunks
            + (size_t)WR * T::VC * B * sizeof(float)       // column totals of each row group
            + (size_t)WC * T::VC * B * sizeof(float)       // row totals of each column group
-           + (size_t)W * 32 * R * sizeof(int);            // tie ends of each warp's rows
+           + (size_t)W * 32 * R * sizeof(int)             // tie ends of each warp's rows
+           + (KIND == kGradB ? (size_t)W * 2 * 32 * R * 32 * sizeof(float) : 0);  // each warp's two Y buffers
 }
 
 // One pair block {I, J} (I <= J) of set wi.set by the whole CTA: its warps
@@ -248,6 +302,7 @@ __device__ __forceinline__ void pair_item(const Work &w, const WorkItem wi, floa
     float *rowpart = colpart + (size_t)wr * VC * B;                        // [wc][VC][B]
     int *te_all = reinterpret_cast<int *>(rowpart + (size_t)wc * VC * B);  // [warps][32 R]
     int *s_te = te_all + warp * 32 * R;
+    float *ysw = reinterpret_cast<float *>(te_all + warps * 32 * R) + (size_t)warp * 2 * 32 * R * 32;  // kGradB
     const int src_lane = (lane + 1) & 31;
 #include "hk_pair_item.inc"
 }
@@ -272,6 +327,7 @@ __global__ void __launch_bounds__(256)
     float *rowpart = colpart + (size_t)wr * VC * B;                        // [wc][VC][B]
     int *te_all = reinterpret_cast<int *>(rowpart + (size_t)wc * VC * B);  // [warps][32 R]
     int *s_te = te_all + warp * 32 * R;
+    float *ysw = reinterpret_cast<float *>(te_all + warps * 32 * R) + (size_t)warp * 2 * 32 * R * 32;  // kGradB
     __shared__ int s_item;
     const int src_lane = (lane + 1) & 31;
     for (;;) {

@@ -1,7 +1,7 @@
 // Launch helpers of the mixed pair kernels, instantiated per dimension by
 // hk_pairs_mixed_lo.cu (D = 1..4) and hk_pairs_mixed_hi.cu (D = 5..8).
 // pass: 1 rates, 2 gradient, 3 rates with Theta sums, 4 rates with the
-// self-excitation sums apart.  A shape is (wr, wc): wr row groups of 32 R
+// self-excitation sums apart, 5 gradient with the BMDS term.  A shape is (wr, wc): wr row groups of 32 R
 // rows (block size B = 32 R wr) and wc column groups, wr * wc <= 8 warps.
 #pragma once
 
@@ -52,6 +52,8 @@ cudaError_t launch_pass_t(int pass, const Work &w, const Sched &sc, int grid, in
         return launch_kind_t<kGrad, D>(w, sc, grid, wr, wc, s);
     if (pass == 4)
         return launch_kind_t<kRateXi, D>(w, sc, grid, wr, 1, s);
+    if (pass == 5)
+        return launch_kind_t<kGradB, D>(w, sc, grid, wr, 1, s);
     return launch_kind_t<kRateTheta, D>(w, sc, grid, wr, 1, s);
 }
 
@@ -65,6 +67,8 @@ size_t smem_t(int pass, int wr, int wc)
         return pair_smem_bytes<kGrad, D, R>(wr * wc, wc);
     if (pass == 4)
         return pair_smem_bytes<kRateXi, D, R>(wr, 1);
+    if (pass == 5)
+        return pair_smem_bytes<kGradB, D, R>(wr, 1);
     return pair_smem_bytes<kRateTheta, D, R>(wr, 1);
 }
 
@@ -116,6 +120,8 @@ int occupancy_t(int pass, int wr, int wc)
         return occupancy_kind<kGrad, D>(wr, wc);
     if (pass == 4)
         return occupancy_kind<kRateXi, D>(wr, 1);
+    if (pass == 5)
+        return occupancy_kind<kGradB, D>(wr, 1);
     return occupancy_kind<kRateTheta, D>(wr, 1);
 }
 

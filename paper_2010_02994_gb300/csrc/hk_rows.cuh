@@ -367,9 +367,10 @@ __device__ __forceinline__ void finalize_grad_row(const Work &w, const SetDesc &
 }
 
 // Own gradient of a flagged row, in FP64 over all events (Appendix A in its
-// ordered form), one pass over the events for every coordinate, summed by
-// the first nt threads of the CTA in a fixed order (every thread of the CTA
-// must call; thread 0 stores).
+// ordered form, plus the BMDS term of Eq. (4) when the gradient pass carried
+// it), one pass over the events for every coordinate, summed by the first nt
+// threads of the CTA in a fixed order (every thread of the CTA must call;
+// thread 0 stores).
 __device__ __forceinline__ void fixup_grad_row(const Work &w, const SetDesc &S, int s, int i, double *out_grad,
                                                double *g_sorted, double *sh, int nt)
 {
@@ -382,18 +383,30 @@ __device__ __forceinline__ void fixup_grad_row(const Work &w, const SetDesc &S, 
     Nsum acc[kMaxD];
     for (int m = threadIdx.x; m < S.n && (int)threadIdx.x < nt; m += nt) {
         const double tm = w.t64[R0 + m];
-        if (tm == tn)
+        if (tm == tn && (w.ysort == nullptr || m == i))
             continue;
         double r2 = 0.0;
         for (int q2 = 0; q2 < d; ++q2) {
             const double df = w.x64[r * kMaxD + q2] - w.x64[(R0 + m) * kMaxD + q2];
             r2 += df * df;
         }
-        const double dt = tn - tm;
-        const double wm = __ldcg(&w.w64[R0 + m]);
-        const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
-        const double xi = k.Cxi * exp(-(k.omega * fabs(dt) + r2 * k.c));
-        const double coef = mu * (wn + wm) * k.itx2 + xi * (tm < tn ? wn : wm) * k.ih2;
+        double coef = 0.0;
+        if (tm != tn) {
+            const double dt = tn - tm;
+            const double wm = __ldcg(&w.w64[R0 + m]);
+            const double mu = k.Cmu * exp(-(r2 * k.a + dt * dt * k.b));
+            const double xi = k.Cxi * exp(-(k.omega * fabs(dt) + r2 * k.c));
+            coef = mu * (wn + wm) * k.itx2 + xi * (tm < tn ? wn : wm) * k.ih2;
+        }
+        if (w.ysort) {
+            // the BMDS term of a BMDS-Hawkes trajectory (every other event,
+            // tied times included), from the same FP32 y as the pair kernel
+            const double y = (double)w.ysort[(int64_t)i * S.npad + m];
+            const double delta = sqrt(r2), inv_delta = r2 > 0.0 ? 1.0 / delta : 0.0;
+            const double z = delta * w.bmds_inv_sigma_d;
+            const double ratio = exp(-0.5 * z * z) * 0.39894228040143267794 / (1.0 - 0.5 * erfc(z * 0.70710678118654752440));
+            coef += (ratio * w.bmds_inv_sigma_d - (y - delta) * w.bmds_inv_s2_d) * inv_delta;
+        }
 #pragma unroll
         for (int q = 0; q < kMaxD; ++q)
             if (q < d)
