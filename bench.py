@@ -37,8 +37,8 @@ CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 # is recorded with it; reported as null once the sources have changed.
 PAIR_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", f)
                        for f in ("hk_pairs_mixed.cuh", "hk_pair_item.inc", "hk_internal.cuh")]
-MEASURED_TRAFFIC = {"source_sha256": "6b92872214be69b064fd06d743cf47cb6cfe3b2925804794f0c6f7d80abc0d08",
-                    "pass1_rates": 3669248, "pass2_gradient": 21959680}
+MEASURED_TRAFFIC = {"source_sha256": "f872e2cd2ba83a37d524e5eb82408cf194fd15615e258eabf6ec0195eb29c83e",
+                    "pass1_rates": 3677440, "pass2_gradient": 21936128}
 
 
 def measured_traffic(kernel: str):
@@ -607,6 +607,19 @@ def run_workload_calls(name: str, calls: int) -> int:
             hawkes_bmds_hmc_trajectory(ctx, t, X, p0, w.params, Y, b.sigma2, 5e-4, 4, -1e30, "mixed", check=False)
         ctx.sync_status()
         ctx.close()
+    elif name == "bmds_hmc_fused_n10000":
+        # one-step BMDS-Hawkes trajectories at N = 10,000, D = 6, with the
+        # BMDS term inside the gradient pass
+        w, b = synth.make_bmds_hawkes(n=10_000)
+        ctx = HawkesContext(device=0, max_n=w.n, max_d=w.d)
+        ctx.set_option("bmds_fused", 1)
+        t, X = torch.tensor(w.t, device=dev), torch.tensor(w.X, device=dev)
+        Y = torch.tensor(b.Y, device=dev).float()
+        p0 = torch.tensor(np.random.default_rng(3).standard_normal(size=w.X.shape), device=dev)
+        for _ in range(calls):
+            hawkes_bmds_hmc_trajectory(ctx, t, X, p0, w.params, Y, b.sigma2, 5e-4, 1, -1e30, "mixed", check=False)
+        ctx.sync_status()
+        ctx.close()
     elif name == "hmc_c2":
         w = synth.make_c2()
         ctx = HawkesContext(device=0, max_n=w.n, max_d=w.d)
@@ -656,7 +669,7 @@ def main():
                     help="only run warmup + steps evaluations (for profiler captures); prints no JSON")
     ap.add_argument("--workload", default=None,
                     choices=["bmds", "bmds_f64y", "mwg1", "mwg32", "mwg32_mixed", "bmds_hmc", "hmc_c2",
-                             "batched_c4", "fp64_c2"],
+                             "batched_c4", "fp64_c2", "bmds_hmc_fused_n10000"],
                     help="with --kernels-only: run warmup + steps calls of that other workload instead "
                          "(for profiler captures); prints no JSON")
     args = ap.parse_args()
