@@ -410,7 +410,7 @@ def bmds_hawkes_hmc_workload(dev, stream, l2, fma_rate: float, ex2_rate: float, 
     m_fused = timed_calls(run, stream, l2, reps=10, warm=2)  # the BMDS term inside the gradient pass
     ctx.set_option("bmds_fused", 0)
     m_two = timed_calls(run, stream, l2, reps=10, warm=2)  # BMDS kernels on a second stream
-    ctx.set_option("bmds_fused", 2)
+    ctx.set_option("bmds_fused", 0)
     ctx.sync_status()
     ctx.close()
     pairs = w.n * (w.n - 1) / 2
@@ -418,7 +418,7 @@ def bmds_hawkes_hmc_workload(dev, stream, l2, fma_rate: float, ex2_rate: float, 
                                   + bmds_bound_cycles(w.d, fma_rate, ex2_rate))
     return {"workload": w.name, "n": w.n, "d": w.d, "leapfrog_steps": steps, "precision": "mixed, FP32 Y",
             "ms_per_trajectory": m, "trajectories_per_s": 1e3 / m, "gradient_evals_per_s": (steps + 1) * 1e3 / m,
-            "gradient": "BMDS kernels beside the Hawkes passes (the default below 8,192 events)",
+            "gradient": "BMDS kernels (gradient alone between the ends) beside the Hawkes passes",
             "fused_ms_per_trajectory": m_fused, "two_stream_ms_per_trajectory": m_two,
             "roofline": eval_roofline(1e3 / m, work, sms, clock_mhz, "trajectories/s",
                                       f"{steps + 1} Hawkes (6D+19 FP32, 4 ex2) and BMDS (4D+40 FP32, 4 MUFU) "

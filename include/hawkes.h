@@ -166,10 +166,11 @@ hawkes_status hawkes_ctx_sync_status(hawkes_ctx *ctx, hawkes_stream stream);
  *                            terms, from a time-ordered FP32 copy of Y that
  *                            the call makes: 4 npad^2 bytes of device
  *                            memory) and runs the BMDS kernels only for
- *                            ell_B at the trajectory's two ends; 0: the BMDS
- *                            kernels run beside every Hawkes evaluation on a
- *                            second stream; 2 (default): 1 from 8,192 events
- *                            on, else 0 (the faster on GB300 at D = 6)  */
+ *                            ell_B at the trajectory's two ends; 0 (default,
+ *                            as fast or faster on GB300 at D = 6 from 4,733
+ *                            to 20,000 events): the BMDS kernels (the
+ *                            gradient alone between the ends) run beside
+ *                            every Hawkes evaluation on a second stream  */
 enum {
     HAWKES_OPT_BLOCK_WARPS = 1,
     HAWKES_OPT_CTAS_PER_SM = 2,

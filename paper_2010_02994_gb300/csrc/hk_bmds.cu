@@ -157,27 +157,32 @@ Consts<F> make_consts(double sigma2)
 }  // namespace bmds
 
 // FP32 pair kernels for D = 1..4 live in hk_bmds_lo.cu.
-cudaError_t launch_bmds_pairs_f32_lo(const bmds::Args<float> &a, bool y_f32, int W, int64_t pairs, cudaStream_t s);
+cudaError_t launch_bmds_pairs_f32_lo(const bmds::Args<float> &a, bool y_f32, bool value, int W, int64_t pairs,
+                                     cudaStream_t s);
 
 namespace {
 
 template <int D, int W>
-void launch_f32(const bmds::Args<float> &a, bool y_f32, int64_t pairs, cudaStream_t s)
+void launch_f32(const bmds::Args<float> &a, bool y_f32, bool value, int64_t pairs, cudaStream_t s)
 {
-    if (y_f32)
-        bmds::pairs_kernel<float, float, D, W><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
+    if (y_f32 && value)
+        bmds::pairs_kernel<float, float, D, W, true><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
+    else if (y_f32)
+        bmds::pairs_kernel<float, float, D, W, false><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
+    else if (value)
+        bmds::pairs_kernel<float, double, D, W, true><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
     else
-        bmds::pairs_kernel<float, double, D, W><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
+        bmds::pairs_kernel<float, double, D, W, false><<<(unsigned)pairs, 32 * W, 0, s>>>(a);
 }
 
-cudaError_t launch_f32_hi(const bmds::Args<float> &a, bool y_f32, int W, int64_t pairs, cudaStream_t s)
+cudaError_t launch_f32_hi(const bmds::Args<float> &a, bool y_f32, bool value, int W, int64_t pairs, cudaStream_t s)
 {
 #define HK_BMDS_CASE(D)                       \
     case D:                                   \
         if (W == 4)                           \
-            launch_f32<D, 4>(a, y_f32, pairs, s); \
+            launch_f32<D, 4>(a, y_f32, value, pairs, s); \
         else                                  \
-            launch_f32<D, 2>(a, y_f32, pairs, s); \
+            launch_f32<D, 2>(a, y_f32, value, pairs, s); \
         break;
     switch (a.d) {
         HK_BMDS_CASE(5)
@@ -266,7 +271,7 @@ size_t bmds_workspace_bytes(int64_t n, int d, bool fp64) { return layout(n, d, f
 
 cudaError_t launch_bmds(const void *Y, bool y_f32, const double *X, int64_t n, int d, double sigma2, bool fp64, void *ws,
                         unsigned *status, double *out_loglik, double *out_grad, double *out_grad_sigma2,
-                        cudaStream_t s, int64_t *launches)
+                        cudaStream_t s, int64_t *launches, bool value)
 {
     const Layout L = layout(n, d, fp64);
     char *base = static_cast<char *>(ws);
@@ -289,7 +294,8 @@ cudaError_t launch_bmds(const void *Y, bool y_f32, const double *X, int64_t n, i
         bmds::Args<float> a{Y, X, n, d, L.T, bmds::make_consts<float>(sigma2),
                             reinterpret_cast<float *>(base + L.off_row), reinterpret_cast<float *>(base + L.off_col),
                             status};
-        e = d <= 4 ? launch_bmds_pairs_f32_lo(a, y_f32, L.W, L.pairs, s) : launch_f32_hi(a, y_f32, L.W, L.pairs, s);
+        e = d <= 4 ? launch_bmds_pairs_f32_lo(a, y_f32, value, L.W, L.pairs, s)
+                   : launch_f32_hi(a, y_f32, value, L.W, L.pairs, s);
         if (e != cudaSuccess)
             return e;
         bmds::finalize_kernel<float><<<L.nblocks, bmds::kFinThreads, 0, s>>>(a, L.KT, sigma2, out_grad, blockpart,

@@ -251,8 +251,9 @@ constexpr unsigned kYBitsMax = 0x7f7fffffu;
 // rotated (entry s is that column), and the column records are stored twice
 // (entries j and j + 32), so step s reads fixed offsets from per-lane bases.
 // MASKED handles ragged rows or columns and the diagonal tile; SYM adds the
-// column side, whose accumulators move one lane down per step.
-template <typename F, int DS, bool MASKED, bool SYM>
+// column side, whose accumulators move one lane down per step; VAL: the
+// value and variance sums too (else the gradient coefficient alone, FP32).
+template <typename F, int DS, bool MASKED, bool SYM, bool VAL>
 __device__ __forceinline__ void sweep(int d, int lane, const F *__restrict__ yrow,
                                       const typename Rec<F>::type *__restrict__ xrec, const F (&xh)[DS],
                                       const F (&xl)[DS], const Consts<F> &k, int64_t row, int64_t c0, int64_t n,
@@ -277,8 +278,11 @@ __device__ __forceinline__ void sweep(int d, int lane, const F *__restrict__ yro
                 dx[2 * i] = dx[2 * i + 1] = F(0);
             }
         }
-        F v, ss, cf;
-        pair_terms(q, yrow[s], k, v, ss, cf);
+        F v = F(0), ss = F(0), cf;
+        if constexpr (VAL)
+            pair_terms(q, yrow[s], k, v, ss, cf);
+        else
+            cf = grad_coef(q, yrow[s], k.inv_sigma, k.inv_s2);
         if (MASKED) {
             const int64_t col = c0 + ((lane + s) & (kCh - 1));
             const bool ok = row_ok && col < n && col != row;
@@ -307,8 +311,10 @@ __device__ __forceinline__ void sweep(int d, int lane, const F *__restrict__ yro
 }
 
 // D > 0: compile-time dimension; D == 0: runtime d (up to kMaxD).
-// YT: element type of Y in memory (double or float).
-template <typename F, typename YT, int D, int W>
+// YT: element type of Y in memory (double or float).  VAL: the value and
+// variance sums as well as the gradient (without them, FP32 only, their
+// slots hold zeros: for callers that need the gradient alone).
+template <typename F, typename YT, int D, int W, bool VAL = true>
 __global__ void __launch_bounds__(32 * W) pairs_kernel(Args<F> a)
 {
     using R = typename Rec<F>::type;
@@ -462,11 +468,11 @@ __global__ void __launch_bounds__(32 * W) pairs_kernel(Args<F> a)
         const R *xrec = sxc + lane;
         const bool full = !diag && full_rows && c0 + kCh <= n;
         if (full)
-            sweep<F, DS, false, true>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
+            sweep<F, DS, false, true, VAL>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
         else if (!diag)
-            sweep<F, DS, true, true>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
+            sweep<F, DS, true, true, VAL>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
         else
-            sweep<F, DS, true, false>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
+            sweep<F, DS, true, false, VAL>(d, lane, yrow, xrec, xh, xl, a.k, row, c0, n, row_ok, gp, vp, sp, colacc);
 #pragma unroll
         for (int c = 0; c < DS; ++c)
             g[c] += gp[c];

@@ -44,11 +44,6 @@ constexpr int kCtlSetFlags = 40;
 constexpr double kSlotBudget = 1024.0 * 1024.0 * 1024.0;
 constexpr double kMinPhaseItems = 16.0;
 
-// BMDS-Hawkes HMC: the BMDS term rides in the gradient pass from this many
-// events on (GB300, D = 6, 20 steps: 3.00 against 2.88 ms per trajectory at
-// N = 4,733, 7.95 against 8.51 at 10,000, 27.9 against 28.8 at 20,000).
-constexpr int64_t kFusedBmdsMinN = 8192;
-
 struct DeviceBuffer {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -121,7 +116,7 @@ struct hawkes_ctx {
     DeviceBuffer bmds_ys;   // BMDS-Hawkes HMC with the fused gradient pass: Y in time order (FP32)
     // options
     int opt_warps = 0, opt_cols = 0, opt_ctas = 0, opt_profile = 0, opt_sorted = 0, opt_fixup_exp = -76, opt_skip = 0;
-    int opt_fp64_ordered = 0, opt_one_launch = 0, opt_slots = 0, opt_bmds_fused = 2;
+    int opt_fp64_ordered = 0, opt_one_launch = 0, opt_slots = 0, opt_bmds_fused = 0;
     int occ_any[3][4] = {};  // CTAs per SM of the one-launch pair kernels: [pass 1..2][log2 warps]
     std::vector<ProfEvent> prof_pending;
     static constexpr int kStages = 5;
@@ -1104,9 +1099,7 @@ hawkes_status hawkes_ctx_set_option(hawkes_ctx *ctx, int32_t option, int64_t val
         ctx->opt_one_launch = value ? 1 : 0;
         return HAWKES_OK;
     case HAWKES_OPT_BMDS_FUSED:
-        if (value < 0 || value > 2)
-            return fail(ctx, HAWKES_ERR_INVALID_ARG, "BMDS fusion must be 0, 1 or 2");
-        ctx->opt_bmds_fused = (int)value;
+        ctx->opt_bmds_fused = value ? 1 : 0;
         return HAWKES_OK;
     case HAWKES_OPT_PARTIAL_SLOTS:
         if (value < 0 || value > (int64_t)1 << 30)
@@ -1477,13 +1470,10 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
 
     // BMDS term: its workspace and the caller-order buffers exist before any capture
     double *bx = nullptr, *bg = nullptr, *bl = nullptr;
-    // mixed precision: the gradient pass carries the BMDS term (pass 5), from
-    // a time-ordered FP32 copy of Y made here; the BMDS kernels then run only
-    // for ell_B at the two ends of the trajectory.  By default from
-    // kFusedBmdsMinN events on: below it the GPU has room to run the BMDS
-    // kernels beside the Hawkes passes, which was faster.
-    const bool want_fused = ctx->opt_bmds_fused == 1 || (ctx->opt_bmds_fused == 2 && counts[0] >= kFusedBmdsMinN);
-    const bool fused = bmds && !fp64 && want_fused && nsets == 1 &&
+    // mixed precision, as an option: the gradient pass carries the BMDS term
+    // (pass 5), from a time-ordered FP32 copy of Y made here; the BMDS kernels
+    // then run only for ell_B at the two ends of the trajectory
+    const bool fused = bmds && !fp64 && ctx->opt_bmds_fused && nsets == 1 &&
                        occupancy(ctx, dims[0], 5, pl.wr_by_d[dims[0]], 1) > 0;
     float *ys = nullptr;
     if (fused) {
@@ -1568,9 +1558,11 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
             HK_TRY(cudaStreamWaitEvent(bs, ctx->bmds_fork, 0), "BMDS fork wait");
             HK_TRY(launch_to_caller(w, ctx->d_set_row0, w.x64, bx, pl.total_rows, bs), "BMDS locations");
             ++ctx->launches_own;
+            // ell_B only where the energy needs it (the first and last
+            // evaluation); the steps in between take the gradient alone
             HK_TRY(launch_bmds(bmds->Y, bmds->y_f32, bx, counts[0], dims[0], bmds->sigma2, fp64, ctx->bmds_ws.ptr,
                                reinterpret_cast<unsigned *>(ctx->ctl + kCtlStatus), bl, fused ? nullptr : bg,
-                               nullptr, bs, &ctx->launches_own),
+                               nullptr, bs, &ctx->launches_own, ends || fp64),
                    "BMDS kernels");
             HK_TRY(cudaEventRecord(ctx->bmds_join, bs), "BMDS join");
             return HAWKES_OK;

@@ -287,8 +287,10 @@ size_t bmds_workspace_bytes(int64_t n, int d, bool fp64);
 // diagonal and for padded rows or columns (i or j >= n).
 cudaError_t launch_bmds_sort_y(const void *Y, bool y_f32, const int32_t *perm, int64_t n, int64_t npad, float *Ys,
                                cudaStream_t s);
+// value = false (mixed precision only): the gradient alone; out_loglik and
+// out_grad_sigma2 then receive meaningless values.
 cudaError_t launch_bmds(const void *Y, bool y_f32, const double *X, int64_t n, int d, double sigma2, bool fp64, void *ws,
                         unsigned *status, double *out_loglik, double *out_grad, double *out_grad_sigma2,
-                        cudaStream_t s, int64_t *launches);
+                        cudaStream_t s, int64_t *launches, bool value = true);
 
 }  // namespace hk

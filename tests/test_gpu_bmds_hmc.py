@@ -91,7 +91,7 @@ def _case_ties(seed, n, d, ties):
     return w, Y, rng.standard_normal(size=w.X.shape)
 
 
-DEFAULTS = {"bmds_fused": 2, "mixed_fixup_exp": -76}
+DEFAULTS = {"bmds_fused": 0, "mixed_fixup_exp": -76}
 
 
 def _with(ctx, opts, fn):
@@ -149,7 +149,7 @@ def test_fused_bmds_influenza_like_trajectory(ctx):
                                                  torch.tensor(p0, device="cuda"), w.params,
                                                  torch.tensor(Y, device="cuda").float(), sigma2, eps, L, -np.inf,
                                                  precision="mixed")
-        ctx.set_option("bmds_fused", 2)
+        ctx.set_option("bmds_fused", 0)
         X = X.cpu().numpy()
         assert int(acc.item()) == ref["accepted"]
         assert abs(H0.item() - ref["H0"]) <= 1e-6 * abs(ref["H0"])
