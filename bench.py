@@ -36,8 +36,8 @@ CPU_SAMPLE_N = 20_000        # events of the bounded CPU-oracle sample
 # one ncu capture of the kernel sources whose SHA-256 (of the files in order)
 # is recorded with it; reported as null once the sources have changed.
 PAIR_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2010_02994_gb300", "csrc", f)
-                       for f in ("hk_pairs_mixed.cuh", "hk_pair_item.inc", "hk_internal.cuh")]
-MEASURED_TRAFFIC = {"source_sha256": "f872e2cd2ba83a37d524e5eb82408cf194fd15615e258eabf6ec0195eb29c83e",
+                       for f in ("hk_pairs_mixed.cuh", "hk_pair_item.inc", "hk_sched.cuh")]
+MEASURED_TRAFFIC = {"source_sha256": "ee35351c374ca03397298cc0d52bed21ed6d53b339c836a093857f7557083cbf",
                     "pass1_rates": 3677440, "pass2_gradient": 21936128}
 
 
