@@ -839,7 +839,7 @@ hawkes_status enqueue_fp64_pass(hawkes_ctx *ctx, const Plan &pl, int pass, bool 
 //   pass (grad_pass 5: with the BMDS term), finalize gradient.
 hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want_grad, double *out_loglik,
                            double *out_grad, double *g_sorted, cudaStream_t s, double *out_grad_params = nullptr,
-                           int grad_pass = 2)
+                           int grad_pass = 2, bool ell = true)
 {
     const bool theta = out_grad_params != nullptr;
     Work &w = ctx->w;
@@ -859,7 +859,7 @@ hawkes_status enqueue_eval(hawkes_ctx *ctx, const Plan &pl, bool fp64, bool want
         ProfEvent pf{};
         if (ctx->opt_profile)
             prof_begin(ctx, s, pf, 3, 0.0);
-        HK_TRY(launch_finalize_rows(w, pl.total_segs, fp64, theta ? kSumsTheta : kSumsNone, out_loglik, s),
+        HK_TRY(launch_finalize_rows(w, pl.total_segs, fp64, theta ? kSumsTheta : kSumsNone, out_loglik, s, ell),
                "finalize rows");
         if (ctx->opt_profile)
             prof_end(ctx, s, pf);
@@ -1571,7 +1571,8 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
             if (!bmds || (fused && !ends))
                 return HAWKES_OK;
             HK_TRY(cudaStreamWaitEvent(es, ctx->bmds_join, 0), "BMDS join wait");
-            HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, fused ? nullptr : bg, ctx->hg, pl.total_rows, bl, es),
+            HK_TRY(launch_add_caller_term(w, ctx->d_set_row0, fused ? nullptr : bg, ctx->hg, pl.total_rows,
+                                          ends ? bl : nullptr, es),
                    "BMDS gradient");
             ++ctx->launches_own;
             return HAWKES_OK;
@@ -1597,7 +1598,8 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
                 const bool last = k == n_steps - 1;
                 if ((r = fork_bmds(last)) != HAWKES_OK)
                     return r;
-                if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es, nullptr, grad_pass)) !=
+                // ell (for H1) from the last evaluation only
+                if ((r = enqueue_eval(ctx, pl, fp64, true, nullptr, nullptr, ctx->hg, es, nullptr, grad_pass, last)) !=
                     HAWKES_OK)
                     return r;
                 if ((r = join_bmds(last)) != HAWKES_OK)

@@ -64,7 +64,7 @@ __device__ void theta_sums_fp64(const Work &w, const SetDesc &S, int i, double *
 // One row per thread.  fp64: the FP64 path's slots; else the mixed path's,
 // with the rate pass's extra row sums (RateSums: none, the six
 // parameter-gradient sums, or the self-excitation sum apart).
-__global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int sums, double *out_loglik)
+__global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int sums, double *out_loglik, int ell)
 {
     __shared__ double s_lnl[kT];
     __shared__ double sh[kT];
@@ -194,7 +194,10 @@ __global__ void __launch_bounds__(kT) finalize_rows_kernel(Work w, int fp64, int
         }
         fixup_rate_row(w, S, s, fi, sh, kT);
     }
-    // the set's last segment writes its ell
+    // the set's last segment writes its ell (when it is wanted: an HMC step
+    // between the trajectory's ends needs only the rates)
+    if (!ell)
+        return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0)
@@ -392,10 +395,10 @@ cudaError_t launch_fold_slots(const Work &w, const Sched &sc, int part, cudaStre
 }
 
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool ell)
 {
     const dim3 grid(total_segs, ctas_per_segment(w, total_segs, fp64));
-    finalize_rows_kernel<<<grid, kT, 0, s>>>(w, fp64 ? 1 : 0, sums, out_loglik);
+    finalize_rows_kernel<<<grid, kT, 0, s>>>(w, fp64 ? 1 : 0, sums, out_loglik, ell ? 1 : 0);
     return cudaGetLastError();
 }
 

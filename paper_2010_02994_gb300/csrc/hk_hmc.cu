@@ -226,13 +226,13 @@ __global__ void to_caller_kernel(Work w, const int64_t *set_row0, const double *
 }
 
 // g_sorted += g (caller order; g null: nothing) and, once, set_loglik[0] +=
-// *ell_add: folds a second potential term (BMDS, evaluated in the caller's
+// *ell_add (ell_add null: nothing): folds a second potential term (BMDS, evaluated in the caller's
 // order) into the Hawkes gradient and log-likelihood that the leapfrog and
 // energy read.
 __global__ void add_caller_term_kernel(Work w, const int64_t *set_row0, const double *__restrict__ g,
                                        double *__restrict__ g_sorted, int64_t total_rows, const double *ell_add)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ell_add)
         w.set_loglik[0] += *ell_add;
     if (g == nullptr)  // the value alone
         return;

@@ -194,10 +194,11 @@ cudaError_t launch_pass2_fp64_sym(int d, const Work &w, const Sched &sc, cudaStr
 // clear them.  part: 0 P1 (vpc values per slot), 1 P2 (d), 2 F1 (1), 3 F1
 // with the Theta sums (6), 4 F2 (d).
 cudaError_t launch_fold_slots(const Work &w, const Sched &sc, int part, cudaStream_t s);
-// Rates, ell per set (out_loglik, nullable) and the FP64 recompute of the
-// flagged rows, one CTA per segment; sums: the rate pass's extra row sums.
+// Rates, ell per set (out_loglik, nullable; not formed when !ell) and the
+// FP64 recompute of the flagged rows, one CTA per segment; sums: the rate
+// pass's extra row sums.
 cudaError_t launch_finalize_rows(const Work &w, int32_t total_segs, bool fp64, int sums, double *out_loglik,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool ell = true);
 cudaError_t launch_theta_grad(const Work &w, int64_t n, double *out6, cudaStream_t s);
 // Gradient rows from the pass-2 slots (with the flagged rows' FP64 terms
 // and own gradients), in the caller's layout and sorted; one CTA per segment.
