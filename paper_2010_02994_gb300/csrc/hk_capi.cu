@@ -470,14 +470,7 @@ hawkes_status build_plan(hawkes_ctx *ctx, Plan &pl, int32_t nsets, const int64_t
             const SetDesc &S = pl.sets[s];
             if (S.d != d)
                 continue;
-            const int nt = S.nblk | 1;
-            const int r0 = phase * S.nslot;
-            const int r1 = std::min(r0 + S.nslot, diag ? S.nblk : nt);
-            const int per = diag ? 1 : (nt - 1) / 2;
-            if (r1 <= r0 || per == 0)
-                continue;
-            pl.runs.push_back({s, r0, r1 - r0, diag ? 1 : 0, (int32_t)first, 0});
-            first += (int64_t)(r1 - r0) * per;
+            append_set_run(s, S.nblk, S.nslot, phase, diag, pl.runs, first);
             overflow = overflow || first > INT32_MAX;
         }
     };

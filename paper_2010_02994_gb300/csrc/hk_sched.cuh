@@ -5,6 +5,8 @@
 
 #include <stdint.h>
 
+#include <vector>
+
 namespace hk {
 
 // One pair block of a launch: set, blocks I <= J (J == nblk: the empty
@@ -29,12 +31,31 @@ struct Sched {
     int32_t nruns, nitems;
 };
 
+// The run of one set's rounds in phase `phase` (rounds [phase nslot,
+// phase nslot + nslot) of its nblk | 1): its off-diagonal blocks or (diag)
+// its diagonal ones, appended to runs with its first item index `first`,
+// which advances by the run's item count.  Nothing when the phase holds no
+// such item for the set.
+inline void append_set_run(int32_t set, int nblk, int nslot, int phase, bool diag, std::vector<ItemRun> &runs,
+                           int64_t &first)
+{
+    const int nt = nblk | 1;
+    const int r0 = phase * nslot;
+    int r1 = r0 + nslot;
+    r1 = r1 < (diag ? nblk : nt) ? r1 : (diag ? nblk : nt);
+    const int per = diag ? 1 : (nt - 1) / 2;
+    if (r1 <= r0 || per == 0)
+        return;
+    runs.push_back({set, r0, r1 - r0, diag ? 1 : 0, (int32_t)first, 0});
+    first += (int64_t)(r1 - r0) * per;
+}
+
 #ifdef __CUDACC__
 // Item k of a launch (0 <= k < sc.nitems): its run by binary search, then
 // its round and blocks by the circle method (sets: the plan's set
-// descriptors, of which nblk and nslot are read).
+// descriptors, of which nblk and nslot are read).  Host and device.
 template <typename Set>
-__device__ __forceinline__ WorkItem decode_item(const Set *sets, const Sched &sc, int k)
+__host__ __device__ __forceinline__ WorkItem decode_item(const Set *sets, const Sched &sc, int k)
 {
     int lo = 0, hi = sc.nruns - 1;
     while (lo < hi) {
