@@ -1505,6 +1505,20 @@ static hawkes_status hmc_common(hawkes_ctx *ctx, int32_t nsets, const int64_t *c
         key.push_back(dims[k]);
         key.push_back(pl.sets[k].B);
     }
+    // the options that shape the captured launches or the Work they copy,
+    // and the pair launches themselves (a replay must not run another plan's
+    // work lists)
+    for (int64_t v : {(int64_t)ctx->opt_warps, (int64_t)ctx->opt_cols, (int64_t)ctx->opt_ctas, (int64_t)ctx->opt_skip,
+                      (int64_t)ctx->opt_one_launch, (int64_t)ctx->opt_slots, (int64_t)ctx->opt_fp64_ordered,
+                      (int64_t)ctx->opt_bmds_fused, (int64_t)pl.slot_cap, (int64_t)pl.phases})
+        key.push_back(v);
+    for (const PairLaunch &L : pl.launches) {
+        key.push_back(L.d);
+        key.push_back(L.phase);
+        key.push_back(L.run0);
+        key.push_back(L.nruns);
+        key.push_back(L.nitems);
+    }
     // the fused pass's inputs travel in the Work copied into each launch;
     // later calls must not see them
     struct ClearBmdsTerm {

@@ -264,3 +264,31 @@ def test_mixed_at_1m_within_slot_budget():
     assert n_a > n_1  # the capped evaluation ran in phases
     assert abs(ell_a - ell_1) <= 1e-6 * abs(ell_1)
     assert rel_l2(g_a, g_1) <= 1e-5
+
+
+def test_hmc_graph_follows_option_changes():
+    """A trajectory's CUDA graph is cached per shape; changing the slot cap
+    (or the far-block skip) between two calls on the same context must run
+    the new plan's launches (its phases and folds), not replay the old ones:
+    both calls follow the oracle's replay."""
+    import torch
+
+    from paper_2010_02994_gb300 import HawkesContext, hmc_leapfrog_trajectory
+
+    w = synth.random_case(13, 2400, 2, shuffle=True)
+    p0 = np.random.default_rng(4).standard_normal(size=w.X.shape)
+    eps, L = 1e-3, 6
+    ref = oracle.hmc_trajectory(w.t, w.X, p0, w.params, eps, L, -np.inf)
+    ctx = HawkesContext(device=0, max_n=20_000, max_d=2)
+    ctx.set_option("block_warps", 2)
+    for opts in ({}, {"partial_slots": 2}, {"partial_slots": 2, "skip_far_blocks": 1}, {}):
+        for k in ("partial_slots", "skip_far_blocks"):
+            ctx.set_option(k, opts.get(k, 0))
+        X = torch.tensor(w.X, device="cuda")
+        H0, H1, acc = hmc_leapfrog_trajectory(ctx, torch.tensor(w.t, device="cuda"), X,
+                                              torch.tensor(p0, device="cuda"), w.params, eps, L, -np.inf,
+                                              precision="mixed")
+        assert int(acc.item()) == 1, opts
+        assert abs(H1.item() - ref["H1"]) <= 1e-6 * abs(ref["H1"]), opts
+        assert np.max(np.abs(X.cpu().numpy() - ref["X"])) <= 1e-6 * max(1.0, float(np.max(np.abs(ref["X"])))), opts
+    ctx.close()
