@@ -427,8 +427,9 @@ hawkes_status hawkes_mwg_sync_status(hawkes_mwg *s, hawkes_stream stream);
  *            H1 finite.
  *   out_H0, out_H1: device [1];  out_accepted: device int32 [1].
  * The L-step trajectory runs as one CUDA graph cached in the context (keyed
- * by n, d, n_steps, precision and the presence of boxes); the first call
- * with a new key captures it. */
+ * by n, d, n_steps, precision, the presence of boxes, the workspace, the
+ * options that shape its launches and the plan's pair launches); the first
+ * call with a new key captures it. */
 hawkes_status hmc_leapfrog_trajectory(hawkes_ctx *ctx, const double *t, double *X_inout, const double *p0,
                                       const double *box_lo, const double *box_hi, int64_t n, int32_t d,
                                       const hawkes_params *params, double eps, int32_t n_steps,
