@@ -1,9 +1,10 @@
 """The pair schedule on the CPU: tests/native/schedule_check.cu compiles the
 library's own run builder and item decoding (csrc/hk_sched.cuh) for the host
-and checks, for block counts 1..130 and several larger ones and slot caps
-from 1 to unlimited, that every pair of blocks is visited exactly once, that
-blocks and slots stay in range, and that no slot is written twice in a
-phase (the invariants the pair kernels' one-writer slots rest on)."""
+and checks, for block counts 1..130 and several larger ones, batches of
+uneven sets sharing a launch, and slot caps from 1 to unlimited, that every
+pair of blocks is visited exactly once, that blocks and slots stay in range,
+and that no slot is written twice in a phase (the invariants the pair
+kernels' one-writer slots rest on)."""
 import os
 import shutil
 import subprocess
